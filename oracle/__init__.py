@@ -1,0 +1,208 @@
+"""FP64 CPU oracle for the state-vector path (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It wraps ``oracle.c`` (plain C, FP64,
+compiled with gcc) through ctypes; it imports nothing from the CUDA package
+and the CUDA package imports nothing from it.
+
+Every function takes and returns numpy arrays; states are ``complex128``
+arrays of length 2**n, qubit q <-> bit q of the index.  The paper passage each
+function follows is cited in ``oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "oracle.c"
+_LIB_DIR = _HERE / "_build"
+_LIB = _LIB_DIR / "liboracle.so"
+_lib = None
+
+
+def build(force: bool = False) -> Path:
+    """Compile ``oracle.c`` into ``oracle/_build/liboracle.so`` with gcc."""
+    _LIB_DIR.mkdir(exist_ok=True)
+    if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = _LIB_DIR / f"liboracle.{os.getpid()}.so"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+             "-o", str(tmp), str(_SRC), "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = C.CDLL(str(_LIB))
+        dp = C.c_void_p
+        i, u64, d = C.c_int, C.c_uint64, C.c_double
+        sig = {
+            "or_philox4x32_10": (None, [dp, dp, dp]),
+            "or_norm2": (d, [dp, i]),
+            "or_init_zero": (None, [dp, i]),
+            "or_init_gaussian": (None, [dp, i, u64]),
+            "or_gaussian_slice": (None, [dp, u64, u64, u64]),
+            "or_apply_gate": (None, [dp, i, i, dp, dp]),
+            "or_apply_controlled": (None, [dp, i, i, dp, i, dp, dp]),
+            "or_apply_mcx": (None, [dp, i, i, dp, i]),
+            "or_qft_dft": (None, [dp, i, i, i, i]),
+            "or_qft_amplitude": (None, [dp, i, i, i, i, u64, dp, dp]),
+            "or_qft_circuit": (None, [dp, i, i, i, i]),
+            "or_add_const": (None, [dp, i, i, dp, u64]),
+            "or_add_const_circuit": (None, [dp, i, i, dp, u64]),
+            "or_expectation": (d, [dp, i, i, dp, dp, dp]),
+            "or_probs": (None, [dp, i, i, dp, dp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _state(psi):
+    a = np.ascontiguousarray(psi, dtype=np.complex128)
+    n = int(a.size).bit_length() - 1
+    if a.ndim != 1 or a.size != (1 << n):
+        raise ValueError("state must be a 1-D array of length 2**n")
+    return a, n
+
+
+def _ints(xs):
+    return np.ascontiguousarray(np.asarray(xs, dtype=np.int32))
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def philox4x32_10(ctr, key):
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
+    out = np.zeros(4, dtype=np.uint32)
+    _load().or_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def zero_state(n):
+    psi = np.empty(1 << n, dtype=np.complex128)
+    _load().or_init_zero(_ptr(psi), n)
+    return psi
+
+
+def gaussian_state(n, seed):
+    psi = np.empty(1 << n, dtype=np.complex128)
+    _load().or_init_gaussian(_ptr(psi), n, seed)
+    return psi
+
+
+def gaussian_slice(seed, i0, count):
+    out = np.empty(count, dtype=np.complex128)
+    _load().or_gaussian_slice(_ptr(out), seed, i0, count)
+    return out
+
+
+def norm2(psi):
+    a, n = _state(psi)
+    return _load().or_norm2(_ptr(a), n)
+
+
+def apply_gate(psi, qubits, matrix):
+    a, n = _state(psi)
+    a = a.copy()
+    q = _ints(qubits)
+    U = np.ascontiguousarray(np.asarray(matrix, dtype=np.complex128))
+    if U.shape != (1 << q.size, 1 << q.size):
+        raise ValueError("matrix shape does not match the number of qubits")
+    _load().or_apply_gate(_ptr(a), n, q.size, _ptr(q), _ptr(U))
+    return a
+
+
+def apply_controlled(psi, controls, targets, matrix):
+    a, n = _state(psi)
+    a = a.copy()
+    c = _ints(controls)
+    t = _ints(targets)
+    U = np.ascontiguousarray(np.asarray(matrix, dtype=np.complex128))
+    _load().or_apply_controlled(_ptr(a), n, c.size, _ptr(c), t.size, _ptr(t), _ptr(U))
+    return a
+
+
+def apply_mcx(psi, controls, target):
+    a, n = _state(psi)
+    a = a.copy()
+    c = _ints(controls)
+    _load().or_apply_mcx(_ptr(a), n, c.size, _ptr(c), int(target))
+    return a
+
+
+def qft_dft(psi, lo, m, inverse=False):
+    a, n = _state(psi)
+    a = a.copy()
+    _load().or_qft_dft(_ptr(a), n, lo, m, int(bool(inverse)))
+    return a
+
+
+def qft_amplitude(psi, lo, m, index, inverse=False):
+    a, n = _state(psi)
+    re, im = C.c_double(), C.c_double()
+    _load().or_qft_amplitude(_ptr(a), n, lo, m, int(bool(inverse)), int(index),
+                             C.byref(re), C.byref(im))
+    return complex(re.value, im.value)
+
+
+def qft_circuit(psi, lo, m, inverse=False):
+    a, n = _state(psi)
+    a = a.copy()
+    _load().or_qft_circuit(_ptr(a), n, lo, m, int(bool(inverse)))
+    return a
+
+
+def add_const(psi, qubits, c):
+    a, n = _state(psi)
+    a = a.copy()
+    q = _ints(qubits)
+    _load().or_add_const(_ptr(a), n, q.size, _ptr(q), int(c) & ((1 << 64) - 1))
+    return a
+
+
+def add_const_circuit(psi, qubits, c):
+    a, n = _state(psi)
+    a = a.copy()
+    q = _ints(qubits)
+    _load().or_add_const_circuit(_ptr(a), n, q.size, _ptr(q), int(c) & ((1 << 64) - 1))
+    return a
+
+
+def expectation(psi, xmask, zmask, coeff):
+    a, n = _state(psi)
+    xm = np.ascontiguousarray(np.asarray(xmask, dtype=np.uint64))
+    zm = np.ascontiguousarray(np.asarray(zmask, dtype=np.uint64))
+    cf = np.ascontiguousarray(np.asarray(coeff, dtype=np.float64))
+    return _load().or_expectation(_ptr(a), n, xm.size, _ptr(xm), _ptr(zm), _ptr(cf))
+
+
+def probs(psi, qubits):
+    a, n = _state(psi)
+    q = _ints(qubits)
+    out = np.empty(1 << q.size, dtype=np.float64)
+    _load().or_probs(_ptr(a), n, q.size, _ptr(q), _ptr(out))
+    return out
+
+
+def fidelity(ref, got):
+    """|<ref|got>|^2 / (<ref|ref><got|got>) in FP64 (max-abs and fidelity are
+    the two error measures every parity test reports)."""
+    r = np.asarray(ref, dtype=np.complex128)
+    g = np.asarray(got, dtype=np.complex128)
+    ov = np.vdot(r, g)
+    return float(abs(ov) ** 2 / (np.vdot(r, r).real * np.vdot(g, g).real))

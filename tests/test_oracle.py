@@ -1,0 +1,370 @@
+"""Pins for the FP64 oracle against facts the paper and mathematics fix.
+
+None of these compares the oracle with itself: each check uses a closed
+form, a library routine the definition reduces to (numpy.kron, tensordot,
+numpy.fft), an invariant, a printed example or brute force on tiny inputs.
+The matrices are deliberately non-symmetric so that a transposed operand,
+a wrong sign or a dropped term fails at least one test.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1604_06460_gb300 import inputs as I
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def kron_list(ms):
+    out = np.array([[1.0 + 0j]])
+    for m in ms:
+        out = np.kron(out, m)
+    return out
+
+
+def dense_1q(n, q, U):
+    """Sec. II construction: Kronecker product of n 2x2 factors, identity
+    except at qubit q; the leftmost factor is the highest qubit."""
+    return kron_list([U if j == q else np.eye(2) for j in reversed(range(n))])
+
+
+def tensordot_apply(psi, n, qubits, U):
+    """Apply U by numpy.tensordot on the (2,)*n tensor; axis n-1-q is qubit q
+    and the matrix index bit j is qubits[j] (so the reshaped U has its
+    most significant axis first, i.e. qubits in reverse order)."""
+    k = len(qubits)
+    T = psi.reshape((2,) * n)
+    Ut = U.reshape((2,) * (2 * k))
+    axes_in = [n - 1 - q for q in reversed(qubits)]
+    out = np.tensordot(Ut, T, axes=(list(range(k, 2 * k)), axes_in))
+    # tensordot puts the k output axes first (in reversed-qubit order)
+    out = np.moveaxis(out, list(range(k)), axes_in)
+    return out.reshape(-1)
+
+
+def rand_unitary(d, rng):
+    z = rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))
+    q, r = np.linalg.qr(z)
+    return q * (np.diag(r) / np.abs(np.diag(r)))[None, :]
+
+
+# --- Philox: the published known-answer vectors ---------------------------
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLD, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = oracle.philox4x32_10(v[0:4], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+# --- Sec. II: qubit order, Kronecker construction ----------------------------
+def test_kron_example_is_not_on_qubit_1():
+    rows = [l.split() for l in open(os.path.join(GOLD, "kron_not_example.txt"))
+            if l.strip() and not l.startswith("#")]
+    M = np.array(rows, dtype=float)
+    cols = []
+    for b in range(4):
+        e = np.zeros(4, complex)
+        e[b] = 1
+        cols.append(oracle.apply_gate(e, [1], I.mat_x()))
+    assert np.array_equal(np.array(cols).T.real, M)
+
+
+def test_x_on_qubit0_maps_zero_to_index1():
+    out = oracle.apply_gate(oracle.zero_state(3), [0], I.mat_x())
+    assert out[1] == 1 and np.count_nonzero(out) == 1
+
+
+@pytest.mark.parametrize("n,q", [(1, 0), (3, 0), (3, 2), (5, 3)])
+def test_1q_gate_vs_kron(n, q):
+    rng = np.random.default_rng(n * 10 + q)
+    U = I.haar_u2(rng)
+    psi = I.random_state(n, 7 + q)
+    ref = dense_1q(n, q, U) @ psi
+    got = oracle.apply_gate(psi, [q], U)
+    assert np.max(np.abs(got - ref)) < 1e-14
+
+
+def test_adjacent_2q_gate_vs_kron():
+    # a 2-qubit gate on (q, q+1): matrix index bit 0 <-> q, bit 1 <-> q+1, so
+    # in Kronecker order the gate's 4x4 block sits at factor position of q+1,q.
+    n, q = 5, 1
+    rng = np.random.default_rng(3)
+    U = rand_unitary(4, rng)
+    psi = I.random_state(n, 11)
+    dense = kron_list([np.eye(2)] * (n - q - 2) + [U] + [np.eye(2)] * q)
+    got = oracle.apply_gate(psi, [q, q + 1], U)
+    assert np.max(np.abs(got - dense @ psi)) < 1e-14
+
+
+@pytest.mark.parametrize("qubits", [[0], [4], [2, 0], [1, 5], [5, 1, 3], [0, 6, 2, 4], [6, 0, 3, 1, 5]])
+def test_kq_gate_vs_tensordot(qubits):
+    n = 7
+    rng = np.random.default_rng(sum(qubits) + len(qubits))
+    U = rand_unitary(1 << len(qubits), rng)
+    psi = I.random_state(n, 5)
+    ref = tensordot_apply(psi, n, qubits, U)
+    got = oracle.apply_gate(psi, qubits, U)
+    assert np.max(np.abs(got - ref)) < 1e-13
+
+
+def test_cnot_truth_table_table1():
+    # Table I CNOT: control is the matrix's high bit; cnot(c, t) flips t iff c.
+    n = 3
+    for b in range(8):
+        e = np.zeros(8, complex)
+        e[b] = 1
+        g = I.cnot(2, 0)
+        out = oracle.apply_gate(e, g.qubits, g.matrix)
+        want = b ^ 1 if (b >> 2) & 1 else b
+        assert out[want] == 1
+
+
+def test_controlled_vs_projector_sum():
+    # C-U = |0><0| (x) 1 + |1><1| (x) U on (control 2, target 0), n = 3
+    rng = np.random.default_rng(1)
+    U = I.haar_u2(rng)
+    P0 = np.diag([1, 0]).astype(complex)
+    P1 = np.diag([0, 1]).astype(complex)
+    dense = kron_list([P0, np.eye(2), np.eye(2)]) + kron_list([P1, np.eye(2), U])
+    psi = I.random_state(3, 2)
+    got = oracle.apply_controlled(psi, [2], [0], U)
+    assert np.max(np.abs(got - dense @ psi)) < 1e-14
+
+
+def test_mcx_truth_table():
+    n = 5
+    for b in range(32):
+        e = np.zeros(32, complex)
+        e[b] = 1
+        out = oracle.apply_mcx(e, [0, 3, 4], 2)
+        want = b ^ 4 if (b & 0b11001) == 0b11001 else b
+        assert out[want] == 1
+
+
+def test_ghz_closed_form():
+    n = 6
+    psi = oracle.zero_state(n)
+    for g in I.ghz_circuit(n):
+        psi = oracle.apply_gate(psi, g.qubits, g.matrix)
+    want = np.zeros(1 << n, complex)
+    want[0] = want[-1] = 1 / np.sqrt(2)
+    assert np.max(np.abs(psi - want)) < 1e-15
+
+
+def test_random_circuit_norm_and_inverse():
+    n = 8
+    gates = I.random_circuit(n, 4, seed=9)
+    psi = oracle.zero_state(n)
+    for g in gates:
+        psi = oracle.apply_gate(psi, g.qubits, g.matrix)
+    assert abs(oracle.norm2(psi) - 1) < 1e-13
+    for g in reversed(gates):
+        psi = oracle.apply_gate(psi, g.qubits, g.matrix.conj().T)
+    assert abs(psi[0] - 1) < 1e-13 and np.max(np.abs(psi[1:])) < 1e-13
+
+
+def test_dense_brute_force_circuit_n6():
+    # whole circuit as the product of dense Kronecker matrices (Sec. II)
+    n = 6
+    rng = np.random.default_rng(4)
+    ops = []
+    psi = I.random_state(n, 3)
+    ref = psi.copy()
+    for _ in range(10):
+        q = int(rng.integers(n))
+        U = I.haar_u2(rng)
+        ops.append((q, U))
+    for q, U in ops:
+        ref = dense_1q(n, q, U) @ ref
+        psi = oracle.apply_gate(psi, [q], U)
+    assert np.max(np.abs(psi - ref)) < 1e-14
+
+
+# --- Sec. III-B: QFT -------------------------------------------------------
+@pytest.mark.parametrize("m", [1, 2, 3, 6])
+def test_qft_dft_equals_numpy_ifft(m):
+    # alpha_l -> 2^{-m/2} sum_k alpha_k e^{+2 pi i k l / 2^m} is numpy's
+    # inverse FFT (sign +, scale 1/N) times sqrt(N).
+    psi = I.random_state(m, m)
+    ref = np.fft.ifft(psi) * np.sqrt(1 << m)
+    assert np.max(np.abs(oracle.qft_dft(psi, 0, m) - ref)) < 1e-14
+    ref_inv = np.fft.fft(psi) / np.sqrt(1 << m)
+    assert np.max(np.abs(oracle.qft_dft(psi, 0, m, inverse=True) - ref_inv)) < 1e-14
+
+
+def test_qft_subregister_batched_vs_numpy():
+    # QFT on qubits [2, 6) of n = 8: independent transforms along axis of stride 4
+    n, lo, m = 8, 2, 4
+    psi = I.random_state(n, 21)
+    T = psi.reshape(1 << (n - lo - m), 1 << m, 1 << lo)
+    ref = (np.fft.ifft(T, axis=1) * np.sqrt(1 << m)).reshape(-1)
+    assert np.max(np.abs(oracle.qft_dft(psi, lo, m) - ref)) < 1e-14
+
+
+@pytest.mark.parametrize("x", [0, 1, 5, 13])
+def test_qft_basis_state_closed_form(x):
+    m = 4
+    e = np.zeros(1 << m, complex)
+    e[x] = 1
+    out = oracle.qft_dft(e, 0, m)
+    l = np.arange(1 << m)
+    want = np.exp(2j * np.pi * ((x * l) % (1 << m)) / (1 << m)) / np.sqrt(1 << m)
+    assert np.max(np.abs(out - want)) < 1e-15
+
+
+@pytest.mark.parametrize("lo,m,inv", [(0, 5, False), (1, 4, False), (2, 3, True), (0, 6, True)])
+def test_qft_circuit_equals_definition(lo, m, inv):
+    n = 7
+    psi = I.random_state(n, lo * 10 + m)
+    a = oracle.qft_dft(psi, lo, m, inverse=inv)
+    b = oracle.qft_circuit(psi, lo, m, inverse=inv)
+    assert np.max(np.abs(a - b)) < 1e-13
+
+
+def test_qft_parseval_square_and_inverse():
+    m = 7
+    psi = I.random_state(m, 77)
+    f = oracle.qft_dft(psi, 0, m)
+    assert abs(oracle.norm2(f) - 1) < 1e-14
+    ff = oracle.qft_dft(f, 0, m)
+    idx = (-np.arange(1 << m)) % (1 << m)   # QFT^2 maps k -> -k mod 2^m
+    assert np.max(np.abs(ff - psi[idx])) < 1e-14
+    back = oracle.qft_dft(f, 0, m, inverse=True)
+    assert np.max(np.abs(back - psi)) < 1e-14
+
+
+def test_qft_single_amplitude_matches_dft():
+    n, lo, m = 9, 1, 6
+    psi = I.random_state(n, 8)
+    full = oracle.qft_dft(psi, lo, m)
+    for idx in [0, 3, 77, 300, 511]:
+        v = oracle.qft_amplitude(psi, lo, m, idx)
+        assert abs(v - full[idx]) < 1e-15
+        vi = oracle.qft_amplitude(psi, lo, m, idx, inverse=True)
+        assert abs(vi - oracle.qft_dft(psi, lo, m, inverse=True)[idx]) < 1e-15
+
+
+# --- Sec. III-A: addition as a permutation ----------------------------------
+def test_add_const_exhaustive_basis_states():
+    n, qubits = 6, [1, 2, 3, 4]
+    m = len(qubits)
+    for c in [0, 1, 7, 15, 9]:
+        for x in range(1 << n):
+            e = np.zeros(1 << n, complex)
+            e[x] = 1
+            out = oracle.add_const(e, qubits, c)
+            r = sum(((x >> q) & 1) << j for j, q in enumerate(qubits))
+            r2 = (r + c) % (1 << m)
+            x2 = x & ~sum(1 << q for q in qubits)
+            x2 |= sum(((r2 >> j) & 1) << q for j, q in enumerate(qubits))
+            assert out[x2] == 1 and np.count_nonzero(out) == 1
+
+
+def test_add_const_permuted_register_order():
+    # register bits listed out of order: bit j of r is qubits[j]
+    n, qubits, c = 5, [3, 0, 4], 5
+    for x in range(32):
+        e = np.zeros(32, complex)
+        e[x] = 1
+        out = oracle.add_const(e, qubits, c)
+        r = ((x >> 3) & 1) | (((x >> 0) & 1) << 1) | (((x >> 4) & 1) << 2)
+        r2 = (r + c) % 8
+        x2 = (x & ~0b11001) | ((r2 & 1) << 3) | (((r2 >> 1) & 1) << 0) | (((r2 >> 2) & 1) << 4)
+        assert out[x2] == 1
+
+
+@pytest.mark.parametrize("qubits,c", [([0, 1, 2, 3, 4], 13), ([2, 3, 4, 5], 11), ([5, 1, 3], 6), ([0, 1, 2, 3, 4, 5, 6], 100)])
+def test_add_const_circuit_equals_permutation_bit_exact(qubits, c):
+    psi = I.random_state(7, c)
+    a = oracle.add_const(psi, qubits, c)
+    b = oracle.add_const_circuit(psi, qubits, c)
+    assert np.array_equal(a, b)
+
+
+def test_add_const_roundtrip_identity():
+    psi = I.random_state(8, 3)
+    q = [0, 1, 2, 3, 4, 5]
+    c = 37
+    out = oracle.add_const(oracle.add_const(psi, q, c), q, (1 << 6) - c)
+    assert np.array_equal(out, psi)
+
+
+# --- Sec. III-D: expectation values and probabilities ----------------------
+def dense_pauli(n, xm, zm):
+    X, Y, Z = I.mat_x(), I.mat_y(), I.mat_z()
+    fs = []
+    for q in reversed(range(n)):
+        xb, zb = (xm >> q) & 1, (zm >> q) & 1
+        fs.append(Y if xb and zb else X if xb else Z if zb else np.eye(2))
+    return kron_list(fs)
+
+
+def test_tfim_closed_forms():
+    n = 6
+    xm, zm, cf = I.tfim_terms(n)
+    assert abs(oracle.expectation(oracle.zero_state(n), xm, zm, cf) - (n - 1)) < 1e-14
+    plus = np.full(1 << n, 1 / np.sqrt(1 << n), complex)
+    assert abs(oracle.expectation(plus, xm, zm, cf) - 0.7 * n) < 1e-13
+
+
+def test_expectation_dense_brute_force():
+    n = 6
+    rng = np.random.default_rng(12)
+    xm = rng.integers(0, 1 << n, size=6).astype(np.uint64)
+    zm = rng.integers(0, 1 << n, size=6).astype(np.uint64)
+    cf = rng.standard_normal(6)
+    psi = I.random_state(n, 13)
+    H = sum(c * dense_pauli(n, int(x), int(z)) for x, z, c in zip(xm, zm, cf))
+    ref = np.vdot(psi, H @ psi).real
+    assert abs(oracle.expectation(psi, xm, zm, cf) - ref) < 1e-13
+
+
+def test_y_eigenstate():
+    # |+i> = (|0> + i|1>)/sqrt 2 is the +1 eigenstate of Y
+    psi = np.array([1, 1j]) / np.sqrt(2)
+    assert abs(oracle.expectation(psi, [1], [1], [1.0]) - 1) < 1e-15
+
+
+def test_probs_ghz_and_product_state():
+    n = 5
+    psi = oracle.zero_state(n)
+    for g in I.ghz_circuit(n):
+        psi = oracle.apply_gate(psi, g.qubits, g.matrix)
+    p = oracle.probs(psi, [0, 3])
+    assert np.allclose(p, [0.5, 0, 0, 0.5], atol=1e-15)
+    # product state RY(a) (x) RY(b): P(bit=1) = sin^2(theta/2)
+    a, b = 0.3, 1.1
+    st = np.kron(I.mat_ry(b) @ [1, 0], I.mat_ry(a) @ [1, 0])
+    p = oracle.probs(st, [0, 1])
+    pa, pb = np.sin(a / 2) ** 2, np.sin(b / 2) ** 2
+    assert np.allclose(p, [(1 - pa) * (1 - pb), pa * (1 - pb), (1 - pa) * pb, pa * pb], atol=1e-15)
+
+
+def test_probs_sum_to_norm_and_order():
+    psi = I.random_state(7, 31)
+    p = oracle.probs(psi, [6, 2, 0])
+    assert abs(p.sum() - 1) < 1e-14
+    # out[r], bit j of r <-> qubits[j]
+    x = 0b1000100  # qubits 6 and 2 set -> r = 0b011
+    e = np.zeros(128, complex)
+    e[x] = 1
+    assert oracle.probs(e, [6, 2, 0])[3] == 1
+
+
+# --- the seeded random state ----------------------------------------------
+def test_gaussian_state_normalised_and_slices():
+    n = 12
+    psi = oracle.gaussian_state(n, 1234)
+    assert abs(oracle.norm2(psi) - 1) < 1e-14
+    raw = oracle.gaussian_slice(1234, 0, 1 << n)
+    scale = np.sqrt(np.vdot(raw, raw).real)
+    assert np.max(np.abs(raw / scale - psi)) < 1e-15
+    # standard complex Gaussian: E re^2 = E im^2 = 1, mean 0
+    big = oracle.gaussian_slice(99, 1 << 40, 1 << 16)
+    assert abs(np.mean(big.real ** 2) - 1) < 0.03 and abs(np.mean(big.imag ** 2) - 1) < 0.03
+    assert abs(np.mean(big.real)) < 0.02 and abs(np.mean(big.imag)) < 0.02
