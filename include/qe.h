@@ -1,0 +1,186 @@
+/*
+ * qe.h -- C ABI of the GB300 state-vector emulator.
+ *
+ * The library updates one state vector of 2^n complex amplitudes resident in
+ * GPU memory (Haener, Steiger, Smelyanskiy, Troyer, "High Performance
+ * Emulation of Quantum Circuits", 2016, Sec. II).  Gates are applied as
+ * dense 2^k x 2^k blocks; whole subroutines are emulated instead of being
+ * simulated gate by gate (Sec. III): the QFT as an FFT (Sec. III-B), the
+ * addition of a classical constant as an amplitude permutation (Sec. III-A),
+ * and expectation values / probabilities computed directly (Sec. III-D).
+ *
+ * Conventions used by every call
+ *   - qubit q is bit q of the amplitude index (little-endian); amplitudes are
+ *     interleaved (re, im) in one contiguous allocation of 2^n elements;
+ *   - QE_C128 stores complex128 (16 B/amplitude, computed to FP64 accuracy),
+ *     QE_C64 stores complex64 (8 B/amplitude, computed in FP32);
+ *   - a k-qubit matrix is 2^k x 2^k complex, row-major, interleaved doubles
+ *     (2 * 4^k values), host memory, whose row/column bit j <-> qubits[j];
+ *   - all device work is enqueued on the state's CUDA stream; calls that
+ *     return host values synchronise that stream; host arrays passed in are
+ *     copied before the call returns, so the caller keeps ownership;
+ *   - every call returns QE_OK (0) or a negative status; no C++ exception
+ *     crosses the ABI; qe_last_error() describes the most recent failure of
+ *     the calling thread.  Invalid arguments return QE_ERR_ARG and leave the
+ *     state untouched.
+ *   - gates may be queued for fusion; qe_flush() (and every call that reads
+ *     or transforms the whole state) applies them first.
+ */
+#ifndef QE_H
+#define QE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qe_state qe_state;
+
+typedef enum { QE_C64 = 0, QE_C128 = 1 } qe_dtype;
+
+typedef enum {
+    QE_OK = 0,
+    QE_ERR_ARG = -1,          /* invalid argument (range, duplicate qubit, NULL) */
+    QE_ERR_OOM = -2,          /* device allocation failed */
+    QE_ERR_CUDA = -3,         /* a CUDA call failed; see qe_last_error() */
+    QE_ERR_TIMEOUT = -4,      /* a bounded device wait gave up */
+    QE_ERR_STATE = -5,        /* handle unusable (freed, failed earlier) */
+    QE_ERR_UNSUPPORTED = -6   /* valid request this build does not implement */
+} qe_status;
+
+/* Planner policy for subroutines that can be emulated or simulated. */
+typedef enum {
+    QE_POLICY_AUTO = 0,       /* learned cost model if loaded, else analytic rule */
+    QE_POLICY_ANALYTIC = 1,   /* analytic cross-over (Sec. III-B performance models) */
+    QE_POLICY_EMULATE = 2,    /* always the classical shortcut */
+    QE_POLICY_SIMULATE = 3    /* always the gate-by-gate circuit */
+} qe_policy;
+
+/* Allocate a state handle for n qubits (1 <= n <= 34) of the given dtype and
+ * initialise it to |0...0>.  dev_ptr == NULL: the library allocates
+ * 2^n * sizeof(amplitude) bytes and frees them in qe_free_state.  Otherwise
+ * dev_ptr is caller-owned device memory of at least that many bytes (e.g. a
+ * torch tensor's storage), 256-byte aligned, which the library borrows for
+ * the handle's lifetime.  stream is a cudaStream_t (NULL = legacy default).
+ * Sec. II: the state is a vector of 2^n amplitudes with sum |alpha_i|^2 = 1. */
+int qe_alloc_state(int n, int dtype, void* dev_ptr, size_t bytes, void* stream,
+                   qe_state** out);
+
+/* Release the handle (and memory the library allocated).  NULL is a no-op. */
+int qe_free_state(qe_state* s);
+
+/* Report n, dtype and the device address of amplitude 0. */
+int qe_state_info(const qe_state* s, int* n, int* dtype, void** dev_ptr);
+
+/* Reset to the basis state |index> (Sec. II): alpha_index = 1, all others 0. */
+int qe_init_basis(qe_state* s, uint64_t index);
+
+/* Fill with i.i.d. standard complex Gaussian amplitudes and normalise by the
+ * compensated FP64 norm.  Amplitude i draws Philox4x32-10 (Salmon et al.,
+ * SC'11) with counter (lo32(i), hi32(i), 0, 0) and key (lo32(seed),
+ * hi32(seed)); words (0,1) give u1 in (0,1], words (2,3) give u2 in [0,1)
+ * (53-bit uniforms); Box-Muller: re + i im = sqrt(-2 ln u1) e^{2 pi i u2}. */
+int qe_init_random(qe_state* s, uint64_t seed);
+
+/* Copy count amplitudes between host memory (in the state's dtype,
+ * interleaved) and the state, starting at amplitude offset.  Pending gates
+ * are applied before a read and before an overwrite. */
+int qe_set_amplitudes(qe_state* s, const void* host, uint64_t offset, uint64_t count);
+int qe_get_amplitudes(qe_state* s, void* host, uint64_t offset, uint64_t count);
+
+/* Apply a k-qubit gate (1 <= k <= 5) given as a dense 2^k x 2^k matrix
+ * (Sec. II; Table I lists the standard ones).  qubits[] are k distinct
+ * qubits < n.  The planner exploits structure (Sec. II): a matrix that acts
+ * as the identity unless some of its qubits are 1 runs as a controlled gate
+ * touching only that fraction of the state; a diagonal matrix with a single
+ * non-unit entry (e.g. CR(theta) = diag(1,1,1,e^{i theta})) touches only the
+ * amplitudes of that entry (a quarter of the state, Sec. III-B); 0/1
+ * permutation matrices (X, CNOT, SWAP) move amplitudes bit-exactly.
+ * Consecutive gates are fused into blocks of up to max_k qubits
+ * (qe_set_policy) and applied at the next flush. */
+int qe_apply_gate(qe_state* s, int k, const int* qubits, const double* matrix);
+
+/* Apply U (2^k x 2^k, 0 <= k <= 2) on targets[] only where every one of the
+ * nc controls[] is 1 (multi-controlled gates such as the Toffoli / MCX used
+ * by reversible arithmetic, Sec. III).  k = 0 multiplies the controlled
+ * amplitudes by the scalar matrix[0]. */
+int qe_apply_controlled(qe_state* s, int nc, const int* controls, int k,
+                        const int* targets, const double* matrix);
+
+/* Quantum Fourier transform on the contiguous register [lo, lo+m)
+ * (Sec. III-B): for every assignment of the other qubits, with register
+ * value k = sum_j bit(lo+j) 2^j,
+ *     alpha_l -> 2^{-m/2} sum_k alpha_k exp(+2 pi i k l / 2^m),
+ * natural output order; inverse != 0 uses the opposite sign.  Emulated as an
+ * in-place FFT, or simulated as m Hadamards, m(m-1)/2 CR gates and the
+ * qubit reversal, as the policy decides. */
+int qe_apply_qft(qe_state* s, int lo, int m, int inverse);
+
+/* Add the classical constant c to the m-qubit register qubits[] (bit j of
+ * the register value <-> qubits[j]), modulo 2^m (Sec. III-A): the amplitude
+ * at x moves to x' whose register value is (r + c) mod 2^m.  Emulated as one
+ * in-place permutation (bit-exact), or simulated as a ripple of
+ * multi-controlled NOTs, as the policy decides.  1 <= m <= n. */
+int qe_apply_add_const(qe_state* s, int m, const int* qubits, uint64_t c);
+
+/* <psi| sum_t coeff[t] P_t |psi> for Pauli strings P_t given by bit masks
+ * over the qubits: (x,z) = (0,0) I, (1,0) X, (0,1) Z, (1,1) Y (Sec. III-D:
+ * the expectation computed in one step instead of by repeated sampling).
+ * Accumulated in FP64 with compensation; *out receives the real value. */
+int qe_expectation(qe_state* s, int nterms, const uint64_t* xmask,
+                   const uint64_t* zmask, const double* coeff, double* out);
+
+/* Marginal probabilities of the m qubits[] (Sec. II, |alpha_i|^2):
+ * out[r] (host, 2^m doubles, 1 <= m <= 16) = sum over x whose bits at
+ * qubits[] spell r of |alpha_x|^2.  FP64 compensated accumulation. */
+int qe_probs(qe_state* s, int m, const int* qubits, double* out);
+
+/* sum_i |alpha_i|^2 in compensated FP64. */
+int qe_norm2(qe_state* s, double* out);
+
+/* Apply queued gates / wait for all work on the state's stream. */
+int qe_flush(qe_state* s);
+int qe_sync(qe_state* s);
+
+/* Choose the emulate-vs-simulate policy and the largest fused block width
+ * (1 <= max_k <= 5) the gate fuser may form. */
+int qe_set_policy(qe_state* s, int policy, int max_k);
+
+/* Counters since the last reset: kernel launches, full-state passes, and the
+ * algorithmic bytes those passes move (reads + writes, see Sec. III-B's
+ * byte count for the controlled phase). */
+typedef struct {
+    uint64_t launches;
+    uint64_t passes;
+    double algorithmic_bytes;
+    uint64_t gates_applied;
+    uint64_t fused_blocks;
+} qe_stats;
+int qe_get_stats(const qe_state* s, qe_stats* out);
+int qe_reset_stats(qe_state* s);
+
+/* Per-kernel timing with CUDA events recorded on the state's stream around
+ * every launch (measurement aid; the events add a few microseconds per
+ * launch).  qe_profile_enable(s, 1) clears earlier records and starts
+ * recording; qe_profile_read synchronises the stream and reports, for each
+ * kernel name, its launches, the summed event time and the algorithmic bytes
+ * those launches move.  *count receives the number of kernel names (at most
+ * max are written). */
+typedef struct {
+    char name[48];
+    uint64_t launches;
+    double total_ms;
+    double bytes;
+} qe_kernel_profile;
+int qe_profile_enable(qe_state* s, int enable);
+int qe_profile_read(qe_state* s, qe_kernel_profile* out, int max, int* count);
+
+/* Human-readable description of the calling thread's last failure. */
+const char* qe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QE_H */

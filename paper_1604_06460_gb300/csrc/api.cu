@@ -1,0 +1,626 @@
+// C ABI (include/qe.h) and the host-side planner: argument checking, the
+// gate queue, gate fusion, structure detection and the choice between
+// emulating and simulating a subroutine (Sec. III).
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <exception>
+#include <string>
+#include <vector>
+
+#include "qe_internal.h"
+#include "qe_plan.h"
+
+namespace {
+thread_local std::string g_last_error = "";
+
+int set_error(int status, const std::string& msg) {
+    g_last_error = msg;
+    return status;
+}
+}  // namespace
+
+#define QE_API_BEGIN try {
+#define QE_API_END                                                              \
+    return QE_OK;                                                               \
+    }                                                                           \
+    catch (const qe::Error& e) { return set_error(e.status, e.msg); }           \
+    catch (const std::bad_alloc&) { return set_error(QE_ERR_OOM, "host out of memory"); } \
+    catch (const std::exception& e) { return set_error(QE_ERR_CUDA, e.what()); } \
+    catch (...) { return set_error(QE_ERR_CUDA, "unknown error"); }
+
+namespace qe {
+
+static void check_state(const qe_state* s) {
+    if (!s || s->magic != 0x51E57A7E) fail(QE_ERR_STATE, "invalid state handle");
+}
+
+static void check_qubits(const qe_state* s, int k, const int* q, uint64_t* mask_out) {
+    if (k > 0 && !q) fail(QE_ERR_ARG, "qubit list is NULL");
+    uint64_t mask = 0;
+    for (int j = 0; j < k; ++j) {
+        if (q[j] < 0 || q[j] >= s->n) fail(QE_ERR_ARG, "qubit index out of range");
+        if ((mask >> q[j]) & 1ull) fail(QE_ERR_ARG, "duplicate qubit");
+        mask |= 1ull << q[j];
+    }
+    if (mask_out) *mask_out = mask;
+}
+
+// ---------------------------------------------------------------- apply
+// One block (possibly fused) through the structure-aware dispatch (Sec. II).
+void apply_block(qe_state* s, int k, const int* qubits, const std::vector<cd>& U, uint64_t cmask) {
+    s->stats.blocks += 1;
+    const uint64_t cmask_in = cmask;
+    const int D = 1 << k;
+    // identity: nothing to do
+    bool ident = true;
+    for (int r = 0; r < D && ident; ++r)
+        for (int c = 0; c < D; ++c)
+            if (U[r * D + c] != (r == c ? cd(1.0) : cd(0.0))) { ident = false; break; }
+    if (ident) return;
+    // strip qubits that act as controls: U is the identity wherever that bit is 0
+    std::vector<int> q(qubits, qubits + k);
+    std::vector<cd> M = U;
+    int kk = k;
+    for (int j = kk - 1; j >= 0; --j) {
+        const int Dk = 1 << kk;
+        bool ctrl = true;
+        for (int r = 0; r < Dk && ctrl; ++r)
+            for (int c = 0; c < Dk; ++c) {
+                if (((r >> j) & 1) && ((c >> j) & 1)) continue;
+                cd want = (r == c) ? cd(1.0) : cd(0.0);
+                if (M[r * Dk + c] != want) { ctrl = false; break; }
+            }
+        if (!ctrl) continue;
+        // keep the block where bit j = 1
+        const int Dn = Dk / 2;
+        std::vector<cd> R(Dn * Dn);
+        auto ins = [j](int v) { return ((v >> j) << (j + 1)) | (1 << j) | (v & ((1 << j) - 1)); };
+        for (int r = 0; r < Dn; ++r)
+            for (int c = 0; c < Dn; ++c) R[r * Dn + c] = M[ins(r) * Dk + ins(c)];
+        cmask |= 1ull << q[j];
+        q.erase(q.begin() + j);
+        M.swap(R);
+        --kk;
+    }
+    const int Dk = 1 << kk;
+    if (kk == 0) {
+        launch_phase_pattern(s, cmask, cmask, M[0]);
+        return;
+    }
+    bool diag = true;
+    int nonunit = 0, where = -1;
+    for (int r = 0; r < Dk; ++r)
+        for (int c = 0; c < Dk; ++c) {
+            if (r != c && M[r * Dk + c] != cd(0.0)) diag = false;
+            if (r == c && M[r * Dk + c] != cd(1.0)) { ++nonunit; where = r; }
+        }
+    if (diag && nonunit == 1) {
+        uint64_t mask = cmask, value = cmask;
+        for (int j = 0; j < kk; ++j) {
+            mask |= 1ull << q[j];
+            if ((where >> j) & 1) value |= 1ull << q[j];
+        }
+        launch_phase_pattern(s, mask, value, M[where * Dk + where]);
+        return;
+    }
+    if (diag && cmask == 0) {
+        std::vector<cd> d(Dk);
+        for (int r = 0; r < Dk; ++r) d[r] = M[r * Dk + r];
+        launch_gate_diag(s, kk, q.data(), d.data());
+        return;
+    }
+    // 0/1 permutation matrix: move amplitudes without arithmetic
+    bool perm = kk <= 2;
+    std::vector<int> p(Dk, -1);
+    for (int r = 0; r < Dk && perm; ++r)
+        for (int c = 0; c < Dk; ++c) {
+            cd v = M[r * Dk + c];
+            if (v == cd(1.0)) {
+                if (p[r] >= 0) perm = false;
+                p[r] = c;
+            } else if (v != cd(0.0)) {
+                perm = false;
+            }
+        }
+    for (int r = 0; r < Dk && perm; ++r) perm = p[r] >= 0;
+    if (perm) {
+        launch_permute(s, cmask, kk, q.data(), p.data());
+        return;
+    }
+    if (cmask != 0 && kk <= 2) {
+        launch_controlled(s, cmask, kk, q.data(), M.data());
+        return;
+    }
+    if (cmask != 0) {
+        // controls found inside a dense block of more than two other qubits:
+        // the full matrix already encodes them
+        if (cmask_in != 0) fail(QE_ERR_UNSUPPORTED, "controlled gate with more than two targets");
+        launch_gate_dense(s, k, qubits, U.data());
+        return;
+    }
+    launch_gate_dense(s, kk, q.data(), M.data());
+}
+
+// ----------------------------------------------------------------- fusion
+namespace {
+struct Block {
+    std::vector<int> q;      // matrix bit j <-> q[j]
+    std::vector<cd> U;       // 2^|q| x 2^|q|
+    uint64_t mask = 0;
+    int gates = 0;
+};
+
+// U_block <- G (on qubits gq, embedded) * U_block, where gq is a subset of b.q
+void left_multiply(Block& b, int gk, const int* gq, const std::vector<cd>& G) {
+    const int k = (int)b.q.size(), D = 1 << k, Dg = 1 << gk;
+    int pos[5];
+    for (int j = 0; j < gk; ++j)
+        pos[j] = (int)(std::find(b.q.begin(), b.q.end(), gq[j]) - b.q.begin());
+    int gmask = 0;
+    for (int j = 0; j < gk; ++j) gmask |= 1 << pos[j];
+    std::vector<cd> out(D * D);
+    std::vector<int> dep(Dg);
+    for (int c = 0; c < Dg; ++c) {
+        int o = 0;
+        for (int j = 0; j < gk; ++j)
+            if ((c >> j) & 1) o |= 1 << pos[j];
+        dep[c] = o;
+    }
+    for (int col = 0; col < D; ++col)
+        for (int r = 0; r < D; ++r) {
+            int gr = 0;
+            for (int j = 0; j < gk; ++j) gr |= ((r >> pos[j]) & 1) << j;
+            const int base = r & ~gmask;
+            cd acc = 0.0;
+            for (int c = 0; c < Dg; ++c) acc += G[gr * Dg + c] * b.U[(base | dep[c]) * D + col];
+            out[r * D + col] = acc;
+        }
+    b.U.swap(out);
+}
+
+// Grow block b to also cover qubits extra (identity on them).
+void extend(Block& b, const std::vector<int>& extra) {
+    for (int qn : extra) {
+        const int k = (int)b.q.size(), D = 1 << k;
+        std::vector<cd> out(4 * D * D, 0.0);
+        // new bit k is qn: U' = I_2 (x) U (block diagonal over the new bit)
+        for (int hb = 0; hb < 2; ++hb)
+            for (int r = 0; r < D; ++r)
+                for (int c = 0; c < D; ++c) out[(r | (hb << k)) * (2 * D) + (c | (hb << k))] = b.U[r * D + c];
+        b.U.swap(out);
+        b.q.push_back(qn);
+        b.mask |= 1ull << qn;
+    }
+}
+
+// Merge block o into b (disjoint qubit sets; the two commute).
+void merge_into(Block& b, const Block& o) {
+    std::vector<int> extra;
+    for (int qn : o.q)
+        if (!((b.mask >> qn) & 1ull)) extra.push_back(qn);
+    extend(b, extra);
+    left_multiply(b, (int)o.q.size(), o.q.data(), o.U);
+    b.gates += o.gates;
+}
+}  // namespace
+
+void flush(qe_state* s) {
+    if (s->queue.empty()) return;
+    std::vector<PendingGate> q;
+    q.swap(s->queue);
+    const int max_k = s->max_k;
+    if (max_k <= 1) {
+        for (auto& g : q) {
+            apply_block(s, g.k, g.q, g.U, g.cmask);
+            s->stats.gates += 1;
+        }
+        return;
+    }
+    std::vector<Block> open;
+    auto close_if = [&](uint64_t touch) {
+        std::vector<Block> keep;
+        for (auto& b : open) {
+            if (b.mask & touch) apply_block(s, (int)b.q.size(), b.q.data(), b.U, 0);
+            else keep.push_back(std::move(b));
+        }
+        open.swap(keep);
+    };
+    for (auto& g : q) {
+        s->stats.gates += 1;
+        uint64_t gmask = 0;
+        for (int j = 0; j < g.k; ++j) gmask |= 1ull << g.q[j];
+        if (g.cmask != 0 || g.k > max_k) {
+            close_if(gmask | g.cmask);
+            apply_block(s, g.k, g.q, g.U, g.cmask);
+            continue;
+        }
+        uint64_t uni = gmask;
+        for (auto& b : open)
+            if (b.mask & gmask) uni |= b.mask;
+        if (__builtin_popcountll(uni) <= max_k) {
+            Block nb;
+            nb.q.assign(g.q, g.q + g.k);
+            nb.U = g.U;
+            nb.mask = gmask;
+            nb.gates = 1;
+            // earlier blocks touching the gate act first
+            Block merged;
+            bool first = true;
+            std::vector<Block> keep;
+            for (auto& b : open) {
+                if (b.mask & gmask) {
+                    if (first) { merged = std::move(b); first = false; }
+                    else merge_into(merged, b);
+                } else {
+                    keep.push_back(std::move(b));
+                }
+            }
+            if (first) {
+                keep.push_back(std::move(nb));
+            } else {
+                merge_into(merged, nb);
+                keep.push_back(std::move(merged));
+            }
+            open.swap(keep);
+        } else {
+            close_if(gmask);
+            Block nb;
+            nb.q.assign(g.q, g.q + g.k);
+            nb.U = g.U;
+            nb.mask = gmask;
+            nb.gates = 1;
+            open.push_back(std::move(nb));
+        }
+    }
+    close_if(~0ull);
+}
+
+// ------------------------------------------------------------ subroutines
+static void qft_simulated(qe_state* s, int lo, int m, int inverse) {
+    const double r2 = 1.0 / std::sqrt(2.0);
+    std::vector<cd> H = {r2, r2, r2, -r2};
+    // CR(theta) = diag(1, 1, 1, e^{i theta}) on (target, control) (Table I)
+    auto cr = [&](int c, int t, double th) {
+        std::vector<cd> D(16, 0.0);
+        D[0] = 1.0;
+        D[5] = 1.0;
+        D[10] = 1.0;
+        D[15] = std::polar(1.0, th);
+        int qq[2] = {t, c};
+        apply_block(s, 2, qq, D, 0);
+    };
+    if (!inverse) {
+        for (int j = m - 1; j >= 0; --j) {
+            int qj = lo + j;
+            apply_block(s, 1, &qj, H, 0);
+            for (int l = j - 1; l >= 0; --l) cr(lo + l, lo + j, M_PI / std::ldexp(1.0, j - l));
+        }
+        launch_bitrev(s, lo, m);
+    } else {
+        launch_bitrev(s, lo, m);
+        for (int j = 0; j < m; ++j) {
+            for (int l = 0; l < j; ++l) cr(lo + l, lo + j, -M_PI / std::ldexp(1.0, j - l));
+            int qj = lo + j;
+            apply_block(s, 1, &qj, H, 0);
+        }
+    }
+    s->stats.gates += (uint64_t)m + (uint64_t)m * (m - 1) / 2;
+}
+
+static void add_simulated(qe_state* s, int m, const int* qubits, uint64_t c) {
+    // ripple of multi-controlled NOTs: adding 2^j increments (qubits[j..m-1])
+    for (int j = 0; j < m; ++j) {
+        if (!((c >> j) & 1ull)) continue;
+        for (int i = m - 1; i >= j; --i) {
+            uint64_t cm = 0;
+            for (int l = j; l < i; ++l) cm |= 1ull << qubits[l];
+            int t = qubits[i];
+            int perm[2] = {1, 0};
+            launch_permute(s, cm, 1, &t, perm);
+            s->stats.gates += 1;
+        }
+    }
+}
+
+}  // namespace qe
+
+// =================================================================== C ABI
+using namespace qe;
+
+extern "C" {
+
+const char* qe_last_error(void) { return g_last_error.c_str(); }
+
+int qe_alloc_state(int n, int dtype, void* dev_ptr, size_t bytes, void* stream, qe_state** out) {
+    QE_API_BEGIN
+    if (!out) fail(QE_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > 34) fail(QE_ERR_ARG, "n must be in [1, 34]");
+    if (dtype != QE_C64 && dtype != QE_C128) fail(QE_ERR_ARG, "unknown dtype");
+    const size_t need = (size_t)(dtype == QE_C128 ? 16 : 8) << n;
+    auto* s = new qe_state();
+    s->n = n;
+    s->dtype = dtype;
+    s->stream = (cudaStream_t)stream;
+    s->max_k = dtype == QE_C128 ? 2 : 4;
+    const char* ar = std::getenv("QE_C128_ARITH");
+    s->c128_native = (ar && std::strcmp(ar, "f64") == 0) ? 1 : 0;
+    try {
+        if (dev_ptr) {
+            if (bytes < need) fail(QE_ERR_ARG, "borrowed buffer too small");
+            if (((uintptr_t)dev_ptr) & 255u) fail(QE_ERR_ARG, "borrowed buffer not 256-byte aligned");
+            s->d = dev_ptr;
+            s->owned = false;
+        } else {
+            cudaError_t e = cudaMalloc(&s->d, need);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                fail(QE_ERR_OOM, std::string("cudaMalloc of the state failed: ") + cudaGetErrorString(e));
+            }
+            s->owned = true;
+        }
+        s->bytes = need;
+        launch_init_basis(s, 0);
+        QE_CUDA(cudaStreamSynchronize(s->stream));
+    } catch (...) {
+        if (s->owned && s->d) cudaFree(s->d);
+        delete s;
+        throw;
+    }
+    *out = s;
+    QE_API_END
+}
+
+int qe_free_state(qe_state* s) {
+    QE_API_BEGIN
+    if (!s) return QE_OK;
+    check_state(s);
+    cudaStreamSynchronize(s->stream);
+    if (s->owned && s->d) cudaFree(s->d);
+    if (s->scratch) cudaFree(s->scratch);
+    profile_clear(s);
+    for (auto e : s->event_pool) cudaEventDestroy(e);
+    s->magic = 0;
+    delete s;
+    QE_API_END
+}
+
+int qe_state_info(const qe_state* s, int* n, int* dtype, void** dev_ptr) {
+    QE_API_BEGIN
+    check_state(s);
+    if (n) *n = s->n;
+    if (dtype) *dtype = s->dtype;
+    if (dev_ptr) *dev_ptr = s->d;
+    QE_API_END
+}
+
+int qe_init_basis(qe_state* s, uint64_t index) {
+    QE_API_BEGIN
+    check_state(s);
+    if (index >= dim(s)) fail(QE_ERR_ARG, "basis index out of range");
+    s->queue.clear();
+    launch_init_basis(s, index);
+    QE_API_END
+}
+
+int qe_init_random(qe_state* s, uint64_t seed) {
+    QE_API_BEGIN
+    check_state(s);
+    s->queue.clear();
+    launch_init_random(s, seed);
+    QE_API_END
+}
+
+int qe_set_amplitudes(qe_state* s, const void* host, uint64_t offset, uint64_t count) {
+    QE_API_BEGIN
+    check_state(s);
+    if (!host && count) fail(QE_ERR_ARG, "host is NULL");
+    if (offset > dim(s) || count > dim(s) - offset) fail(QE_ERR_ARG, "range out of bounds");
+    flush(s);
+    QE_CUDA(cudaMemcpyAsync((char*)s->d + offset * amp_bytes(s), host, count * amp_bytes(s),
+                            cudaMemcpyHostToDevice, s->stream));
+    QE_CUDA(cudaStreamSynchronize(s->stream));
+    QE_API_END
+}
+
+int qe_get_amplitudes(qe_state* s, void* host, uint64_t offset, uint64_t count) {
+    QE_API_BEGIN
+    check_state(s);
+    if (!host && count) fail(QE_ERR_ARG, "host is NULL");
+    if (offset > dim(s) || count > dim(s) - offset) fail(QE_ERR_ARG, "range out of bounds");
+    flush(s);
+    QE_CUDA(cudaMemcpyAsync(host, (const char*)s->d + offset * amp_bytes(s), count * amp_bytes(s),
+                            cudaMemcpyDeviceToHost, s->stream));
+    QE_CUDA(cudaStreamSynchronize(s->stream));
+    QE_API_END
+}
+
+int qe_apply_gate(qe_state* s, int k, const int* qubits, const double* matrix) {
+    QE_API_BEGIN
+    check_state(s);
+    if (k < 1 || k > 5) fail(QE_ERR_ARG, "k must be in [1, 5]");
+    check_qubits(s, k, qubits, nullptr);
+    if (!matrix) fail(QE_ERR_ARG, "matrix is NULL");
+    PendingGate g;
+    g.k = k;
+    for (int j = 0; j < k; ++j) g.q[j] = qubits[j];
+    const int D = 1 << k;
+    g.U.resize(D * D);
+    for (int i = 0; i < D * D; ++i) {
+        if (!std::isfinite(matrix[2 * i]) || !std::isfinite(matrix[2 * i + 1]))
+            fail(QE_ERR_ARG, "matrix has a non-finite entry");
+        g.U[i] = cd(matrix[2 * i], matrix[2 * i + 1]);
+    }
+    s->queue.push_back(std::move(g));
+    QE_API_END
+}
+
+int qe_apply_controlled(qe_state* s, int nc, const int* controls, int k, const int* targets,
+                        const double* matrix) {
+    QE_API_BEGIN
+    check_state(s);
+    if (nc < 0 || k < 0 || k > 2) fail(QE_ERR_ARG, "need nc >= 0 and 0 <= k <= 2");
+    uint64_t cm = 0, tm = 0;
+    check_qubits(s, nc, controls, &cm);
+    check_qubits(s, k, targets, &tm);
+    if (cm & tm) fail(QE_ERR_ARG, "a qubit is both control and target");
+    if (!matrix) fail(QE_ERR_ARG, "matrix is NULL");
+    PendingGate g;
+    g.k = k;
+    for (int j = 0; j < k; ++j) g.q[j] = targets[j];
+    g.cmask = cm;
+    const int D = 1 << k;
+    g.U.resize(D * D);
+    for (int i = 0; i < D * D; ++i) g.U[i] = cd(matrix[2 * i], matrix[2 * i + 1]);
+    if (k == 0 && cm == 0) fail(QE_ERR_ARG, "a global phase needs at least one control");
+    if (k == 0) {
+        flush(s);
+        launch_phase_pattern(s, cm, cm, g.U[0]);
+        s->stats.gates += 1;
+    } else {
+        s->queue.push_back(std::move(g));
+    }
+    QE_API_END
+}
+
+int qe_apply_qft(qe_state* s, int lo, int m, int inverse) {
+    QE_API_BEGIN
+    check_state(s);
+    if (m < 1 || lo < 0 || lo + m > s->n) fail(QE_ERR_ARG, "register [lo, lo+m) out of range");
+    flush(s);
+    if (choose_emulate_qft(s, lo, m)) launch_qft_fft(s, lo, m, inverse);
+    else qft_simulated(s, lo, m, inverse);
+    QE_API_END
+}
+
+int qe_apply_add_const(qe_state* s, int m, const int* qubits, uint64_t c) {
+    QE_API_BEGIN
+    check_state(s);
+    if (m < 1 || m > s->n) fail(QE_ERR_ARG, "m out of range");
+    check_qubits(s, m, qubits, nullptr);
+    flush(s);
+    if (choose_emulate_add(s, m, qubits, c)) launch_add_const(s, m, qubits, c);
+    else add_simulated(s, m, qubits, c);
+    QE_API_END
+}
+
+int qe_expectation(qe_state* s, int nterms, const uint64_t* xmask, const uint64_t* zmask,
+                   const double* coeff, double* out) {
+    QE_API_BEGIN
+    check_state(s);
+    if (nterms < 0 || (nterms && (!xmask || !zmask || !coeff)) || !out) fail(QE_ERR_ARG, "bad term arrays");
+    const uint64_t valid = (s->n >= 64) ? ~0ull : ((1ull << s->n) - 1ull);
+    for (int t = 0; t < nterms; ++t) {
+        if ((xmask[t] | zmask[t]) & ~valid) fail(QE_ERR_ARG, "Pauli mask names a qubit >= n");
+        if (!std::isfinite(coeff[t])) fail(QE_ERR_ARG, "non-finite coefficient");
+    }
+    flush(s);
+    *out = reduce_expectation(s, nterms, xmask, zmask, coeff);
+    QE_API_END
+}
+
+int qe_probs(qe_state* s, int m, const int* qubits, double* out) {
+    QE_API_BEGIN
+    check_state(s);
+    if (m < 1 || m > 16 || m > s->n) fail(QE_ERR_ARG, "m must be in [1, min(16, n)]");
+    check_qubits(s, m, qubits, nullptr);
+    if (!out) fail(QE_ERR_ARG, "out is NULL");
+    flush(s);
+    reduce_probs(s, m, qubits, out);
+    QE_API_END
+}
+
+int qe_norm2(qe_state* s, double* out) {
+    QE_API_BEGIN
+    check_state(s);
+    if (!out) fail(QE_ERR_ARG, "out is NULL");
+    flush(s);
+    *out = reduce_norm2(s);
+    QE_API_END
+}
+
+int qe_flush(qe_state* s) {
+    QE_API_BEGIN
+    check_state(s);
+    flush(s);
+    QE_API_END
+}
+
+int qe_sync(qe_state* s) {
+    QE_API_BEGIN
+    check_state(s);
+    flush(s);
+    QE_CUDA(cudaStreamSynchronize(s->stream));
+    QE_API_END
+}
+
+int qe_set_policy(qe_state* s, int policy, int max_k) {
+    QE_API_BEGIN
+    check_state(s);
+    if (policy < QE_POLICY_AUTO || policy > QE_POLICY_SIMULATE) fail(QE_ERR_ARG, "unknown policy");
+    if (max_k < 1 || max_k > 5) fail(QE_ERR_ARG, "max_k must be in [1, 5]");
+    flush(s);
+    s->policy = policy;
+    s->max_k = max_k;
+    QE_API_END
+}
+
+int qe_get_stats(const qe_state* s, qe_stats* out) {
+    QE_API_BEGIN
+    check_state(s);
+    if (!out) fail(QE_ERR_ARG, "out is NULL");
+    out->launches = s->stats.launches;
+    out->passes = s->stats.passes;
+    out->algorithmic_bytes = s->stats.bytes;
+    out->gates_applied = s->stats.gates;
+    out->fused_blocks = s->stats.blocks;
+    QE_API_END
+}
+
+int qe_profile_enable(qe_state* s, int enable) {
+    QE_API_BEGIN
+    check_state(s);
+    flush(s);
+    QE_CUDA(cudaStreamSynchronize(s->stream));
+    profile_clear(s);
+    s->profile = enable != 0;
+    QE_API_END
+}
+
+int qe_profile_read(qe_state* s, qe_kernel_profile* out, int max, int* count) {
+    QE_API_BEGIN
+    check_state(s);
+    if (!count || (max > 0 && !out)) fail(QE_ERR_ARG, "NULL output");
+    flush(s);
+    QE_CUDA(cudaStreamSynchronize(s->stream));
+    std::vector<std::string> names;
+    std::vector<qe_kernel_profile> acc;
+    for (auto& r : s->prof) {
+        float ms = 0.f;
+        QE_CUDA(cudaEventElapsedTime(&ms, r.start, r.stop));
+        size_t i = std::find(names.begin(), names.end(), std::string(r.tag)) - names.begin();
+        if (i == names.size()) {
+            names.push_back(r.tag);
+            qe_kernel_profile p{};
+            std::strncpy(p.name, r.tag, sizeof(p.name) - 1);
+            acc.push_back(p);
+        }
+        acc[i].launches += 1;
+        acc[i].total_ms += ms;
+        acc[i].bytes += r.bytes;
+    }
+    *count = (int)acc.size();
+    for (int i = 0; i < (int)acc.size() && i < max; ++i) out[i] = acc[i];
+    QE_API_END
+}
+
+int qe_reset_stats(qe_state* s) {
+    QE_API_BEGIN
+    check_state(s);
+    s->stats = Stats();
+    QE_API_END
+}
+
+}  // extern "C"

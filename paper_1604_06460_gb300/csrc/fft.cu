@@ -1,0 +1,374 @@
+// Emulated QFT (Sec. III-B): the QFT of a register [lo, lo+m) equals, for
+// every assignment of the other qubits, the length-2^m discrete Fourier
+// transform with kernel exp(+2 pi i k l / 2^m) and scale 2^{-m/2}.  The
+// emulator computes it as an in-place FFT instead of m(m+1)/2 gates.
+//
+// Decomposition: radix-2^r passes from the top register bits down
+// (decimation in frequency).  A pass loads tiles that hold whole groups of
+// 2^r elements strided along its r bits into shared memory, runs r radix-2
+// DIF stages there, multiplies every element by the inter-pass twiddle
+// exp(s 2 pi i j2 k1 / 2^(b0+r)) (j2: the register bits below the pass, k1:
+// the pass's output digit), and writes the tile back in place.  After the
+// last pass the register holds the transform in bit-reversed order; a
+// separate in-place tiled pass reverses it.  A register that fits in one
+// tile is transformed in a single pass with the reversal done in shared
+// memory.  Twiddles come from two tables of FP64-generated roots (fine and
+// coarse, 2^ceil(m/2) + 2^floor(m/2) entries) stored in the policy's type.
+#include <algorithm>
+#include <cmath>
+#include <map>
+
+#include "qe_arith.cuh"
+#include "qe_internal.h"
+
+namespace qe {
+
+namespace {
+
+constexpr int kFftThreads = 512;
+
+template <class P>
+__global__ void k_twiddles(typename P::M* fine, typename P::M* coarse, int m, int h, int sign) {
+    const uint64_t nf = 1ull << h, nc = 1ull << (m - h);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nf + nc;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t e = i < nf ? i : ((i - nf) << h);
+        // exp(sign * 2 pi i e / 2^m): the angle in units of pi is exact
+        const double x = scalbn((double)e, 1 - m);
+        double sn, cs;
+        sincospi(x, &sn, &cs);
+        typename P::M w = P::from_d(cs, sign > 0 ? sn : -sn);
+        if (i < nf) fine[i] = w;
+        else coarse[i - nf] = w;
+    }
+}
+
+template <class P>
+struct FftArgs {
+    typename P::S* x;
+    const typename P::M* fine;
+    const typename P::M* coarse;
+    uint64_t ntiles;
+    int L, T, kh;
+    uint8_t hq[16];
+    int P0;       // tile-local position of the lowest pass bit
+    int r;        // bits in this pass
+    int b0;       // lowest register bit of this pass (register-relative)
+    int lo, m, h; // register placement, size, fine-table bits
+    int twiddle;  // multiply by the inter-pass twiddle
+    int natural;  // single pass: undo the bit reversal inside the tile
+    int scale_on;
+    typename P::M scale;
+};
+
+template <class P>
+__device__ __forceinline__ typename P::M root(const FftArgs<P>& a, uint64_t e) {
+    return P::cmul(a.coarse[e >> a.h], a.fine[e & ((1ull << a.h) - 1ull)]);
+}
+
+template <class P>
+__global__ void __launch_bounds__(kFftThreads) k_fft_pass(const __grid_constant__ FftArgs<P> a) {
+    using V = typename P::V;
+    using M = typename P::M;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* tile = reinterpret_cast<V*>(smem_raw);
+    M* roots = reinterpret_cast<M*>(tile + (1 << a.T));
+    __shared__ uint64_t offA[64], offB[64];
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int R = 1 << a.r;
+    // per-stage tables: roots[2^s - 1 + p] = exp(sign 2 pi i p / 2^(s+1)), p < 2^s,
+    // so that lanes with consecutive p read consecutive entries
+    for (int e = tid; e < R - 1; e += nth) {
+        const int s = 31 - __clz(e + 1);
+        const uint64_t p = (uint64_t)(e + 1 - (1 << s));
+        roots[e] = root(a, p << (a.m - s - 1));
+    }
+    if (tid < 64) {
+        uint64_t oa = 0, ob = 0;
+        for (int j = 0; j < 6 && j < a.kh; ++j)
+            if ((tid >> j) & 1) oa |= 1ull << a.hq[j];
+        for (int j = 6; j < a.kh; ++j)
+            if ((tid >> (j - 6)) & 1) ob |= 1ull << a.hq[j];
+        offA[tid] = oa;
+        offB[tid] = ob;
+    }
+    __syncthreads();
+    const int Tn = 1 << a.T;
+    const uint32_t lowmask = (1u << a.L) - 1u;
+    const uint64_t j2mask = (1ull << a.b0) - 1ull;
+    const uint64_t emask = (1ull << (a.b0 + a.r)) - 1ull;
+    for (uint64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const uint64_t base = insert_zero_bits(t << a.L, a.hq, a.kh);
+        for (int i = tid; i < Tn; i += nth) {
+            const uint32_t hi = (uint32_t)i >> a.L;
+            tile[i] = P::load(a.x[base + (i & lowmask) + offA[hi & 63] + offB[hi >> 6]]);
+        }
+        __syncthreads();
+        for (int s = a.r - 1; s >= 0; --s) {
+            const int bitpos = a.P0 + s;
+            const uint32_t below = (1u << bitpos) - 1u;
+            for (int beta = tid; beta < Tn / 2; beta += nth) {
+                const uint32_t u = (((uint32_t)beta & ~below) << 1) | ((uint32_t)beta & below);
+                const uint32_t v = u | (1u << bitpos);
+                const uint32_t p = (u >> a.P0) & ((1u << s) - 1u);
+                const M w = roots[(1 << s) - 1 + p];
+                const V U = tile[u], W = tile[v];
+                tile[u] = P::add(U, W);
+                tile[v] = P::cmul(w, P::sub(U, W));
+            }
+            __syncthreads();
+        }
+        for (int i = tid; i < Tn; i += nth) {
+            const uint32_t hi = (uint32_t)i >> a.L;
+            const uint64_t G = base + (i & lowmask) + offA[hi & 63] + offB[hi >> 6];
+            const uint32_t gp = ((uint32_t)i >> a.P0) & (uint32_t)(R - 1);
+            const uint32_t rev = (a.r > 0) ? (__brev(gp) >> (32 - a.r)) : 0u;
+            V v;
+            if (a.natural) {
+                // position gp receives the element whose in-group index is rev(gp)
+                const uint32_t src = ((uint32_t)i & ~((uint32_t)(R - 1) << a.P0)) | (rev << a.P0);
+                v = tile[src];
+            } else {
+                v = tile[i];
+            }
+            if (a.twiddle) {
+                const uint64_t j2 = (G >> a.lo) & j2mask;
+                const uint64_t e = ((j2 * (uint64_t)rev) & emask) << (a.m - a.b0 - a.r);
+                v = P::cmul(root(a, e), v);
+            }
+            if (a.scale_on) v = P::cmul(a.scale, v);
+            a.x[G] = P::store(v);
+        }
+        __syncthreads();
+    }
+}
+
+// --------------------------------------------------------------- bitrev
+// In-place reversal of the register value's bits.  Work item = (outer bits,
+// middle value Mv <= rev(Mv)); tiles X(Mv) and Y(rev Mv) hold elements
+// [b][a][w] (b: top c register bits, a: bottom c register bits, w: the lo
+// qubits below the register) and are exchanged transposed and reversed.
+template <class P>
+struct RevArgs {
+    typename P::S* x;
+    uint64_t items;
+    int lo, m, c;
+};
+
+template <class P>
+__global__ void __launch_bounds__(256) k_bitrev(const __grid_constant__ RevArgs<P> a) {
+    using S = typename P::S;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int C = 1 << a.c, W = 1 << a.lo;
+    const int row = C * W + 1;   // odd stride in elements: conflict-free 16-byte accesses
+    S* X = reinterpret_cast<S*>(smem_raw);
+    S* Y = X + C * row;
+    const int mid_bits = a.m - 2 * a.c;
+    const uint64_t nmid = 1ull << mid_bits;
+    for (uint64_t item = blockIdx.x; item < a.items; item += gridDim.x) {
+        const uint64_t mv = item & (nmid - 1ull);
+        const uint64_t outer = item >> mid_bits;
+        const uint64_t mr = mid_bits > 0 ? (__brevll(mv) >> (64 - mid_bits)) : 0ull;
+        if (mv > mr) continue;
+        const bool self = (mv == mr);
+        const uint64_t obase = outer << (a.lo + a.m);
+        const uint64_t bx = obase | (mv << (a.lo + a.c));
+        const uint64_t by = obase | (mr << (a.lo + a.c));
+        const int shb = a.lo + a.m - a.c;
+        const int n = C * C * W;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int b = i / (C * W), aw = i % (C * W);
+            const uint64_t off = ((uint64_t)b << shb) | (uint64_t)aw;
+            X[b * row + aw] = a.x[bx + off];
+            if (!self) Y[b * row + aw] = a.x[by + off];
+        }
+        __syncthreads();
+        const S* srcX = self ? X : Y;   // destination tile X(mv) receives from Y
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int b2 = i / (C * W), aw = i % (C * W);
+            const int a2 = aw / W, w = aw % W;
+            const int rb = (int)(__brev((uint32_t)a2) >> (32 - a.c));   // source b
+            const int ra = (int)(__brev((uint32_t)b2) >> (32 - a.c));   // source a
+            const uint64_t off = ((uint64_t)b2 << shb) | (uint64_t)aw;
+            a.x[bx + off] = srcX[rb * row + ra * W + w];
+            if (!self) a.x[by + off] = X[rb * row + ra * W + w];
+        }
+        __syncthreads();
+    }
+}
+
+struct TableKey {
+    int m, sign, policy;
+    bool operator<(const TableKey& o) const {
+        return m != o.m ? m < o.m : sign != o.sign ? sign < o.sign : policy < o.policy;
+    }
+};
+struct Table {
+    void* fine = nullptr;
+    void* coarse = nullptr;
+};
+std::map<std::pair<int, TableKey>, Table> g_tables;   // (device, key) -> table
+
+template <class P>
+Table get_tables(qe_state* s, int m, int sign, int pol) {
+    int dev = 0;
+    QE_CUDA(cudaGetDevice(&dev));
+    auto key = std::make_pair(dev, TableKey{m, sign, pol});
+    auto it = g_tables.find(key);
+    if (it != g_tables.end()) return it->second;
+    const int h = (m + 1) / 2;
+    Table t;
+    QE_CUDA(cudaMalloc(&t.fine, sizeof(typename P::M) << h));
+    QE_CUDA(cudaMalloc(&t.coarse, sizeof(typename P::M) << (m - h)));
+    uint64_t total = (1ull << h) + (1ull << (m - h));
+    unsigned grid = (unsigned)std::min<uint64_t>((total + 255) / 256, 4096);
+    Launch L(s, "fft_twiddles", 0.0, false);
+    k_twiddles<P><<<grid, 256, 0, s->stream>>>((typename P::M*)t.fine, (typename P::M*)t.coarse, m, h, sign);
+    QE_CUDA(cudaGetLastError());
+    g_tables[key] = t;
+    return t;
+}
+
+struct Geom {
+    int T = 0, L = 0, kh = 0;
+    uint8_t hq[16] = {0};
+};
+// Tile of at most 2^Tt elements containing the register bits [g0, g0+r).
+Geom pass_geom(int n, int g0, int r, int Tt) {
+    Tt = std::min(Tt, n);
+    for (int L = Tt; L >= 0; --L) {
+        int kh = 0;
+        for (int q = g0; q < g0 + r; ++q) kh += q >= L;
+        if (L + kh <= Tt) {
+            Geom g;
+            g.L = L;
+            g.kh = kh;
+            g.T = L + kh;
+            int j = 0;
+            for (int q = g0; q < g0 + r; ++q)
+                if (q >= L) g.hq[j++] = (uint8_t)q;
+            return g;
+        }
+    }
+    fail(QE_ERR_ARG, "no FFT tile geometry");
+}
+
+template <class P>
+void fft_impl(qe_state* s, int lo, int m, int inverse, int pol) {
+    const int sign = inverse ? -1 : 1;
+    Table tb = get_tables<P>(s, m, sign, pol);
+    const int Tmax = (sizeof(typename P::V) >= 16) ? 11 : 12;
+    const int Lmin = (sizeof(typename P::V) >= 16) ? 3 : 4;   // >= 128-byte chunks
+    const int rb_max = Tmax - std::min(lo, Lmin);
+    std::vector<std::pair<int, int>> passes;   // (b0, r), top first
+    if (m <= rb_max) {
+        passes.push_back({0, m});
+    } else {
+        const int ru_max = Tmax - Lmin;
+        const int rest = m - rb_max;
+        const int nup = (rest + ru_max - 1) / ru_max;
+        int top = m;
+        for (int p = 0; p < nup; ++p) {
+            int r = rest / nup + (p < rest % nup ? 1 : 0);
+            passes.push_back({top - r, r});
+            top -= r;
+        }
+        passes.push_back({0, top});
+    }
+    static thread_local FftArgs<P> a;
+    a.x = reinterpret_cast<typename P::S*>(s->d);
+    a.fine = (const typename P::M*)tb.fine;
+    a.coarse = (const typename P::M*)tb.coarse;
+    a.lo = lo;
+    a.m = m;
+    a.h = (m + 1) / 2;
+    const double scale = std::pow(2.0, -0.5 * m);
+    a.scale = P::mat(scale, 0.0);
+    const bool single = passes.size() == 1;
+    for (size_t p = 0; p < passes.size(); ++p) {
+        const int b0 = passes[p].first, r = passes[p].second;
+        Geom g = pass_geom(s->n, lo + b0, r, Tmax);
+        a.L = g.L;
+        a.T = g.T;
+        a.kh = g.kh;
+        for (int j = 0; j < 16; ++j) a.hq[j] = g.hq[j];
+        a.P0 = std::min(lo + b0, g.L);
+        a.r = r;
+        a.b0 = b0;
+        a.ntiles = 1ull << (s->n - g.T);
+        a.twiddle = b0 > 0;
+        a.natural = single;
+        a.scale_on = (p + 1 == passes.size());
+        size_t smem = sizeof(typename P::V) * ((size_t)1 << g.T) +
+                      sizeof(typename P::M) * ((size_t)1 << r);
+        auto fn = k_fft_pass<P>;
+        QE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int occ = 0;
+        QE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kFftThreads, smem));
+        uint64_t grid = std::min<uint64_t>(a.ntiles, (uint64_t)num_sms() * std::max(occ, 1));
+        Launch L(s, "fft_pass", 2.0 * dim(s) * amp_bytes(s));
+        fn<<<(unsigned)grid, kFftThreads, smem, s->stream>>>(a);
+        QE_CUDA(cudaGetLastError());
+    }
+    if (!single) launch_bitrev(s, lo, m);
+}
+
+template <class S>
+__global__ void __launch_bounds__(256) k_bitrev_chunks(S* __restrict__ x, uint64_t count, int lo, int m) {
+    const uint64_t rmask = ((1ull << m) - 1ull) << lo;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = (i & rmask) >> lo;
+        const uint64_t kr = __brevll(k) >> (64 - m);
+        if (k < kr) {
+            const uint64_t j = (i & ~rmask) | (kr << lo);
+            S t = x[i];
+            x[i] = x[j];
+            x[j] = t;
+        }
+    }
+}
+
+template <class P>
+void bitrev_impl(qe_state* s, int lo, int m) {
+    if (m <= 1) return;
+    using S = typename P::S;
+    Launch L(s, "bitrev", 2.0 * dim(s) * amp_bytes(s));
+    if (lo >= 5) {
+        // chunks of >= 32 contiguous amplitudes move as units: coalesced pair swaps
+        const uint64_t count = dim(s);
+        unsigned grid = (unsigned)std::min<uint64_t>((count + 255) / 256, (uint64_t)num_sms() * 8);
+        k_bitrev_chunks<S><<<grid, 256, 0, s->stream>>>(reinterpret_cast<S*>(s->d), count, lo, m);
+    } else {
+        static thread_local RevArgs<P> a;
+        a.x = reinterpret_cast<S*>(s->d);
+        a.lo = lo;
+        a.m = m;
+        a.c = std::min(m / 2, (11 - lo) / 2);
+        a.items = (1ull << (s->n - lo - m)) << (m - 2 * a.c);
+        const int C = 1 << a.c, W = 1 << lo;
+        size_t smem = sizeof(S) * 2 * (size_t)C * (C * W + 1);
+        auto fn = k_bitrev<P>;
+        QE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int occ = 0;
+        QE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, smem));
+        uint64_t grid = std::min<uint64_t>(a.items, (uint64_t)num_sms() * std::max(occ, 1));
+        fn<<<(unsigned)grid, 256, smem, s->stream>>>(a);
+    }
+    QE_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+void launch_qft_fft(qe_state* s, int lo, int m, int inverse) {
+    if (s->dtype == QE_C64) fft_impl<F32>(s, lo, m, inverse, 0);
+    else if (s->c128_native) fft_impl<F64>(s, lo, m, inverse, 1);
+    else fft_impl<DF>(s, lo, m, inverse, 2);
+}
+
+void launch_bitrev(qe_state* s, int lo, int m) {
+    if (s->dtype == QE_C64) bitrev_impl<F32>(s, lo, m);
+    else bitrev_impl<F64>(s, lo, m);   // pure data movement: storage type only
+}
+
+}  // namespace qe

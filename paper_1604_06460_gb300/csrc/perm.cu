@@ -1,0 +1,244 @@
+// Emulated arithmetic (Sec. III-A): adding a classical constant c to an
+// m-qubit register is a permutation of the amplitudes, x -> x' where the
+// register value r becomes (r + c) mod 2^m.  The emulator performs it as one
+// in-place permutation: every amplitude is read once and written once, and
+// the bits are moved unchanged (no arithmetic touches the values).
+//
+// For a fixed assignment of the non-register qubits (a "column") the map is a
+// rotation by c of 2^m entries, which splits into g = gcd(c, 2^m) cycles of
+// length 2^m / g.  Three in-place strategies:
+//   slice   - register [lo, lo+m) whose slice of 2^(lo+m) contiguous
+//             amplitudes fits one CTA's shared memory: load, write rotated;
+//   cluster - slices up to 8x larger: eight CTAs of a thread-block cluster
+//             each stage 1/8 of the slice and read the rotated source from
+//             the owner's shared memory (distributed shared memory);
+//   walk    - otherwise every thread follows one cycle of one column,
+//             prefetching several positions ahead (coalesced when the
+//             lowest non-register qubits vary across the warp).
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "qe_arith.cuh"
+#include "qe_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace qe {
+
+namespace {
+
+template <class S>
+struct WalkArgs {
+    S* x;
+    uint64_t columns;     // 2^(n-m)
+    uint64_t g;           // cycles per column: gcd(c, 2^m)
+    uint64_t nseg;        // segments per cycle
+    uint64_t seg_len;     // cycle positions per segment
+    uint64_t items;       // columns * g * nseg
+    S* scratch;           // one saved element per item
+    uint64_t c;           // constant mod 2^m
+    uint64_t mmask;       // 2^m - 1
+    uint64_t cycle_len;   // 2^m / g
+    int m;
+    int contiguous;       // register = [lo, lo+m) ascending
+    int lo;
+    uint8_t reg[64];      // register qubits (bit j <-> reg[j])
+    uint8_t reg_sorted[64];   // register qubits ascending (for inserting zeros)
+};
+
+template <class S>
+__device__ __forceinline__ uint64_t reg_deposit(const WalkArgs<S>& a, uint64_t r) {
+    if (a.contiguous) return r << a.lo;
+    uint64_t x = 0;
+    for (int j = 0; j < a.m; ++j) x |= ((r >> j) & 1ull) << a.reg[j];
+    return x;
+}
+
+// Cycle walks are split into S segments so that enough threads run even when
+// there are few columns: a first kernel saves the last element of every
+// segment to scratch, the second shifts each segment by one position along
+// its cycle, seeding it with the saved element of the previous segment.
+// Work item = ((segment * g) + cycle start) * columns + column.
+template <class S>
+__device__ __forceinline__ void walk_item(const WalkArgs<S>& a, uint64_t t, uint64_t& x0,
+                                          uint64_t& start, uint64_t& seg) {
+    const uint64_t col = t % a.columns;
+    const uint64_t rest = t / a.columns;
+    start = rest % a.g;
+    seg = rest / a.g;
+    x0 = insert_zero_bits(col, a.reg_sorted, a.m);
+}
+
+template <class S>
+__global__ void __launch_bounds__(256) k_add_walk_save(const __grid_constant__ WalkArgs<S> a) {
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < a.items;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t x0, start, seg;
+        walk_item(a, t, x0, start, seg);
+        const uint64_t last = min((seg + 1) * a.seg_len, a.cycle_len) - 1;
+        const uint64_t r = (start + last * a.c) & a.mmask;
+        a.scratch[t] = a.x[x0 | reg_deposit(a, r)];
+    }
+}
+
+template <class S, int U>
+__global__ void __launch_bounds__(256) k_add_walk(const __grid_constant__ WalkArgs<S> a) {
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < a.items;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t x0, start, seg;
+        walk_item(a, t, x0, start, seg);
+        const uint64_t first = seg * a.seg_len;
+        const uint64_t end = min(first + a.seg_len, a.cycle_len);
+        // the element before this segment on the cycle was saved by the
+        // previous segment's item (segment nseg-1 precedes segment 0)
+        const uint64_t prev_seg = (seg == 0) ? a.nseg - 1 : seg - 1;
+        S v = a.scratch[t + (prev_seg - seg) * a.g * a.columns];
+        uint64_t r = (start + first * a.c) & a.mmask;
+        for (uint64_t step = first; step < end; step += U) {
+            const uint64_t left = end - step;
+            const int cnt = left < (uint64_t)U ? (int)left : U;
+            S buf[U];
+            uint64_t pos[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (u < cnt) {
+                    pos[u] = x0 | reg_deposit(a, r);
+                    buf[u] = a.x[pos[u]];
+                    r = (r + a.c) & a.mmask;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (u < cnt) a.x[pos[u]] = (u == 0) ? v : buf[u - 1];
+            v = buf[cnt - 1];
+        }
+    }
+}
+
+// One CTA per slice of 2^S contiguous amplitudes; rotation by c * 2^lo.
+template <class S>
+__global__ void __launch_bounds__(512) k_add_slice(S* __restrict__ x, uint64_t nslices, int Sbits,
+                                                   uint64_t shift) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* buf = reinterpret_cast<S*>(smem_raw);
+    const uint32_t E = 1u << Sbits, mask = E - 1u;
+    const uint32_t sh = (uint32_t)shift;
+    for (uint64_t sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
+        S* base = x + (sl << Sbits);
+        for (uint32_t i = threadIdx.x; i < E; i += blockDim.x) buf[i] = base[i];
+        __syncthreads();
+        for (uint32_t p = threadIdx.x; p < E; p += blockDim.x) base[p] = buf[(p - sh) & mask];
+        __syncthreads();
+    }
+}
+
+// Eight CTAs (one cluster) per slice of 2^S amplitudes, each holding 2^S/8.
+template <class S>
+__global__ void __launch_bounds__(512) k_add_cluster(S* __restrict__ x, int Sbits, uint64_t shift) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* buf = reinterpret_cast<S*>(smem_raw);
+    cg::cluster_group cl = cg::this_cluster();
+    const uint32_t rank = cl.block_rank();
+    const uint32_t nblk = cl.num_blocks();
+    const uint32_t E = (1u << Sbits) / nblk;      // elements per CTA
+    const uint32_t mask = (1u << Sbits) - 1u;
+    const uint64_t slice = blockIdx.x / nblk;
+    S* base = x + (slice << Sbits);
+    for (uint32_t i = threadIdx.x; i < E; i += blockDim.x) buf[i] = base[rank * E + i];
+    cl.sync();
+    const uint32_t sh = (uint32_t)shift;
+    for (uint32_t i = threadIdx.x; i < E; i += blockDim.x) {
+        const uint32_t p = rank * E + i;
+        const uint32_t src = (p - sh) & mask;
+        const S* remote = cl.map_shared_rank(buf, src / E);
+        base[p] = remote[src % E];
+    }
+    cl.sync();
+}
+
+template <class S>
+void add_impl(qe_state* s, int m, const int* qubits, uint64_t c) {
+    const uint64_t mmask = (m >= 64) ? ~0ull : ((1ull << m) - 1ull);
+    c &= mmask;
+    if (c == 0) return;
+    bool contiguous = true;
+    for (int j = 1; j < m; ++j) contiguous &= qubits[j] == qubits[0] + j;
+    const int lo = qubits[0];
+    const int n = s->n;
+    const int Sbits = contiguous ? lo + m : 0;
+    const int cap_bits = (sizeof(S) >= 16) ? 12 : 13;      // 64 KB per CTA
+    const int ccap_bits = (sizeof(S) >= 16) ? 13 : 14;     // 128 KB per CTA, 8 per cluster
+    S* x = reinterpret_cast<S*>(s->d);
+    const bool use_slice = contiguous && lo < 5 && Sbits <= cap_bits;
+    const bool use_cluster = !use_slice && contiguous && lo < 5 && Sbits <= ccap_bits + 3 && Sbits >= 3;
+    Launch L(s, use_slice ? "add_slice" : use_cluster ? "add_cluster" : "add_walk",
+             2.0 * dim(s) * amp_bytes(s));
+    if (use_slice) {
+        const uint64_t nslices = 1ull << (n - Sbits);
+        size_t smem = sizeof(S) << Sbits;
+        QE_CUDA(cudaFuncSetAttribute(k_add_slice<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int occ = 0;
+        QE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_add_slice<S>, 512, smem));
+        uint64_t grid = std::min<uint64_t>(nslices, (uint64_t)num_sms() * std::max(occ, 1));
+        k_add_slice<S><<<(unsigned)grid, 512, smem, s->stream>>>(x, nslices, Sbits, c << lo);
+    } else if (use_cluster) {
+        const uint64_t nslices = 1ull << (n - Sbits);
+        size_t smem = sizeof(S) << (Sbits - 3);
+        QE_CUDA(cudaFuncSetAttribute(k_add_cluster<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(nslices * 8));
+        cfg.blockDim = dim3(512);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 8;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (nslices * 8 > 0x7FFFFFFFull) fail(QE_ERR_UNSUPPORTED, "too many slices for one launch");
+        QE_CUDA(cudaLaunchKernelEx(&cfg, k_add_cluster<S>, x, Sbits, (uint64_t)(c << lo)));
+    } else {
+        static thread_local WalkArgs<S> a;
+        a.x = x;
+        a.m = m;
+        a.c = c;
+        a.mmask = mmask;
+        a.contiguous = contiguous;
+        a.lo = lo;
+        a.g = 1ull << __builtin_ctzll(c);   // gcd(c, 2^m), c != 0 mod 2^m
+        a.columns = 1ull << (n - m);
+        a.cycle_len = (mmask >> __builtin_ctzll(c)) + 1ull;
+        // enough independent walks to fill the GPU, segments of >= 64 steps
+        const uint64_t want = (uint64_t)num_sms() * 2048;
+        const uint64_t base_items = a.columns * a.g;
+        uint64_t nseg = (want + base_items - 1) / base_items;
+        nseg = std::max<uint64_t>(1, std::min<uint64_t>(nseg, a.cycle_len / 64));
+        a.seg_len = (a.cycle_len + nseg - 1) / nseg;
+        a.nseg = (a.cycle_len + a.seg_len - 1) / a.seg_len;
+        a.items = base_items * a.nseg;
+        a.scratch = (S*)ensure_scratch(s, a.items * sizeof(S));
+        for (int j = 0; j < m; ++j) a.reg[j] = (uint8_t)qubits[j];
+        int tmp[64];
+        for (int j = 0; j < m; ++j) tmp[j] = qubits[j];
+        std::sort(tmp, tmp + m);
+        for (int j = 0; j < m; ++j) a.reg_sorted[j] = (uint8_t)tmp[j];
+        uint64_t grid = std::min<uint64_t>((a.items + 255) / 256, (uint64_t)num_sms() * 8);
+        grid = std::max<uint64_t>(grid, 1);
+        k_add_walk_save<S><<<(unsigned)grid, 256, 0, s->stream>>>(a);
+        QE_CUDA(cudaGetLastError());
+        k_add_walk<S, 8><<<(unsigned)grid, 256, 0, s->stream>>>(a);
+    }
+    QE_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+void launch_add_const(qe_state* s, int m, const int* qubits, uint64_t c) {
+    if (s->dtype == QE_C128) add_impl<double2>(s, m, qubits, c);
+    else add_impl<float2>(s, m, qubits, c);
+}
+
+}  // namespace qe

@@ -1,0 +1,70 @@
+// Analytic cross-over rule between emulation and simulation.
+//
+// Sec. III-B models the simulated QFT by its memory traffic, 4 N n^2 bytes
+// for n^2/2 controlled phases that touch a quarter of the state plus the
+// Hadamards, and the FFT by 5 N n flops at an FFT efficiency; the expected
+// speedup is n * FLOPS_achieved / B_mem (Sec. IV-C).  On one GPU the network
+// terms drop out.  The constants below are this device's measured copy
+// bandwidth and the FP32-pipe throughput that the FFT butterflies use.
+#include <cmath>
+
+#include "qe_plan.h"
+
+namespace qe {
+
+namespace {
+constexpr double kBandwidth = 6.7e12;      // bytes/s, device copy bandwidth
+constexpr double kFp32Ops = 3.4e13;        // FP32-pipe instructions/s
+// FP32-pipe instructions per complex element per radix-2 stage of the FFT:
+// about 46 in double-float arithmetic, 5 in FP32.
+double stage_ops(const qe_state* s) { return s->dtype == QE_C128 ? 46.0 : 5.0; }
+}  // namespace
+
+double analytic_qft_simulate(const qe_state* s, int m) {
+    const double N = std::ldexp(1.0, s->n), B = s->dtype == QE_C128 ? 16.0 : 8.0;
+    const double h_bytes = m * 2.0 * N * B;                       // m Hadamards
+    const double cr_bytes = 0.5 * m * (m - 1) * 2.0 * (N / 4.0) * B;  // quarter-state phases
+    const double rev_bytes = m > 1 ? 2.0 * N * B : 0.0;
+    return (h_bytes + cr_bytes + rev_bytes) / kBandwidth;
+}
+
+double analytic_qft_emulate(const qe_state* s, int m) {
+    const double N = std::ldexp(1.0, s->n), B = s->dtype == QE_C128 ? 16.0 : 8.0;
+    const int per_pass = s->dtype == QE_C128 ? 12 : 13;
+    const int passes = (m + per_pass - 1) / per_pass + (m > per_pass ? 1 : 0);
+    const double mem = passes * 2.0 * N * B / kBandwidth;
+    const double alu = N * m * stage_ops(s) / kFp32Ops;
+    return mem > alu ? mem : alu;
+}
+
+double analytic_add_simulate(const qe_state* s, int m, uint64_t c) {
+    const double N = std::ldexp(1.0, s->n), B = s->dtype == QE_C128 ? 16.0 : 8.0;
+    double bytes = 0.0;
+    for (int j = 0; j < m; ++j) {
+        if (!((c >> j) & 1ull)) continue;
+        for (int i = m - 1; i >= j; --i) bytes += 2.0 * std::ldexp(N, -(i - j)) * B;
+    }
+    return bytes / kBandwidth;
+}
+
+double analytic_add_emulate(const qe_state* s, int m) {
+    (void)m;
+    const double N = std::ldexp(1.0, s->n), B = s->dtype == QE_C128 ? 16.0 : 8.0;
+    return 2.0 * N * B / kBandwidth;
+}
+
+bool choose_emulate_qft(qe_state* s, int lo, int m) {
+    (void)lo;
+    if (s->policy == QE_POLICY_EMULATE) return true;
+    if (s->policy == QE_POLICY_SIMULATE) return false;
+    return analytic_qft_emulate(s, m) <= analytic_qft_simulate(s, m);
+}
+
+bool choose_emulate_add(qe_state* s, int m, const int* qubits, uint64_t c) {
+    (void)qubits;
+    if (s->policy == QE_POLICY_EMULATE) return true;
+    if (s->policy == QE_POLICY_SIMULATE) return false;
+    return analytic_add_emulate(s, m) <= analytic_add_simulate(s, m, c);
+}
+
+}  // namespace qe

@@ -1,0 +1,119 @@
+// Host-side declarations shared by the translation units of libqe.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qe.h"
+
+namespace qe {
+
+using cd = std::complex<double>;
+
+// Thrown inside the library, caught at the C boundary and turned into a status.
+struct Error {
+    int status;
+    std::string msg;
+};
+[[noreturn]] void fail(int status, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what);
+#define QE_CUDA(call) ::qe::check_cuda((call), #call)
+
+// A queued (not yet applied) gate.
+struct PendingGate {
+    int k = 0;                  // number of target qubits
+    int q[5] = {0, 0, 0, 0, 0}; // target qubits (matrix bit j <-> q[j])
+    uint64_t cmask = 0;         // control qubits (all must be 1)
+    std::vector<cd> U;          // 2^k x 2^k row-major
+};
+
+struct Stats {
+    uint64_t launches = 0, passes = 0, gates = 0, blocks = 0;
+    double bytes = 0.0;
+};
+
+struct ProfRec {
+    const char* tag;
+    cudaEvent_t start, stop;
+    double bytes;
+};
+
+}  // namespace qe
+
+struct qe_state {
+    int n = 0;
+    int dtype = QE_C128;
+    void* d = nullptr;            // amplitudes
+    size_t bytes = 0;
+    bool owned = false;
+    cudaStream_t stream = nullptr;
+    int policy = QE_POLICY_AUTO;
+    int max_k = 4;
+    int c128_native = 0;          // 1: native FP64 arithmetic for complex128
+    std::vector<qe::PendingGate> queue;
+    // device scratch for reductions, grown on demand
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    // pinned host mirror of small results
+    double* host_result = nullptr;
+    qe::Stats stats;
+    // optional per-launch event timing
+    bool profile = false;
+    std::vector<qe::ProfRec> prof;
+    std::vector<cudaEvent_t> event_pool;
+    int magic = 0x51E57A7E;
+};
+
+namespace qe {
+
+inline uint64_t dim(const qe_state* s) { return 1ull << s->n; }
+
+// Brackets one kernel launch: counts it, adds its algorithmic bytes and, when
+// profiling is on, records CUDA events around it on the state's stream.
+class Launch {
+  public:
+    Launch(qe_state* s, const char* tag, double bytes, bool full_pass = true);
+    ~Launch();
+  private:
+    qe_state* s_;
+    int idx_ = -1;
+};
+void profile_clear(qe_state* s);
+inline int amp_bytes(const qe_state* s) { return s->dtype == QE_C128 ? 16 : 8; }
+int num_sms();
+void* ensure_scratch(qe_state* s, size_t bytes);
+
+// ---- kernels (each launcher enqueues on s->stream and updates s->stats)
+void launch_init_basis(qe_state* s, uint64_t index);
+void launch_init_random(qe_state* s, uint64_t seed);
+void launch_scale(qe_state* s, double factor);
+
+// dense k-qubit gate (1 <= k <= 5) through shared-memory tiles
+void launch_gate_dense(qe_state* s, int k, const int* qubits, const cd* U);
+// diagonal gate: amplitude x *= d[row(x)] for all x
+void launch_gate_diag(qe_state* s, int k, const int* qubits, const cd* d);
+// amplitudes with (x & mask) == value are multiplied by phase
+void launch_phase_pattern(qe_state* s, uint64_t mask, uint64_t value, cd phase);
+// U (k <= 2 targets) applied where all controls in cmask are 1
+void launch_controlled(qe_state* s, uint64_t cmask, int k, const int* targets, const cd* U);
+// 0/1 permutation within groups of targets, under controls: out[r] = in[perm[r]]
+void launch_permute(qe_state* s, uint64_t cmask, int k, const int* targets, const int* perm);
+
+// QFT on register [lo, lo+m) as an FFT
+void launch_qft_fft(qe_state* s, int lo, int m, int inverse);
+// register-value bit reversal of [lo, lo+m) (bit-exact)
+void launch_bitrev(qe_state* s, int lo, int m);
+
+// register + c mod 2^m, register bit j <-> qubits[j]
+void launch_add_const(qe_state* s, int m, const int* qubits, uint64_t c);
+
+// reductions (synchronise the stream)
+double reduce_norm2(qe_state* s);
+double reduce_expectation(qe_state* s, int nterms, const uint64_t* xm, const uint64_t* zm,
+                          const double* cf);
+void reduce_probs(qe_state* s, int m, const int* qubits, double* out);
+
+}  // namespace qe

@@ -1,0 +1,254 @@
+"""Python binding of the C ABI in ``include/qe.h`` (argument marshalling only).
+
+Every operation runs in the CUDA kernels of ``libqe.so``; this module only
+converts Python/numpy arguments to the C types, allocates the state's device
+memory through PyTorch (so that torch's caching allocator and streams are
+used) and turns error codes into exceptions.  There is no CPU fallback: if
+the library is missing or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+_LIB_PATH = Path(__file__).resolve().parent / "_build" / "libqe.so"
+_lib = None
+
+C64, C128 = 0, 1
+POLICY_AUTO, POLICY_ANALYTIC, POLICY_EMULATE, POLICY_SIMULATE = 0, 1, 2, 3
+
+STATUS = {0: "QE_OK", -1: "QE_ERR_ARG", -2: "QE_ERR_OOM", -3: "QE_ERR_CUDA",
+          -4: "QE_ERR_TIMEOUT", -5: "QE_ERR_STATE", -6: "QE_ERR_UNSUPPORTED"}
+
+# name -> (restype, argtypes); exactly the entry points declared in include/qe.h
+_vp, _i, _u64, _sz, _dp = C.c_void_p, C.c_int, C.c_uint64, C.c_size_t, C.c_void_p
+
+
+class Stats(C.Structure):
+    _fields_ = [("launches", C.c_uint64), ("passes", C.c_uint64),
+                ("algorithmic_bytes", C.c_double), ("gates_applied", C.c_uint64),
+                ("fused_blocks", C.c_uint64)]
+
+
+class KernelProfile(C.Structure):
+    _fields_ = [("name", C.c_char * 48), ("launches", C.c_uint64), ("total_ms", C.c_double),
+                ("bytes", C.c_double)]
+
+
+SIGNATURES = {
+    "qe_alloc_state": (_i, [_i, _i, _vp, _sz, _vp, C.POINTER(_vp)]),
+    "qe_free_state": (_i, [_vp]),
+    "qe_state_info": (_i, [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_vp)]),
+    "qe_init_basis": (_i, [_vp, _u64]),
+    "qe_init_random": (_i, [_vp, _u64]),
+    "qe_set_amplitudes": (_i, [_vp, _vp, _u64, _u64]),
+    "qe_get_amplitudes": (_i, [_vp, _vp, _u64, _u64]),
+    "qe_apply_gate": (_i, [_vp, _i, _vp, _vp]),
+    "qe_apply_controlled": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
+    "qe_apply_qft": (_i, [_vp, _i, _i, _i]),
+    "qe_apply_add_const": (_i, [_vp, _i, _vp, _u64]),
+    "qe_expectation": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
+    "qe_probs": (_i, [_vp, _i, _vp, _vp]),
+    "qe_norm2": (_i, [_vp, _vp]),
+    "qe_flush": (_i, [_vp]),
+    "qe_sync": (_i, [_vp]),
+    "qe_set_policy": (_i, [_vp, _i, _i]),
+    "qe_get_stats": (_i, [_vp, C.POINTER(Stats)]),
+    "qe_reset_stats": (_i, [_vp]),
+    "qe_profile_enable": (_i, [_vp, _i]),
+    "qe_profile_read": (_i, [_vp, C.POINTER(KernelProfile), _i, C.POINTER(_i)]),
+    "qe_last_error": (C.c_char_p, []),
+}
+
+
+class QEError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def library_path() -> Path:
+    return _LIB_PATH
+
+
+def load(path: str | Path | None = None):
+    """Load libqe.so (built by ``paper_1604_06460_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is None or path is not None:
+        p = Path(path) if path else _LIB_PATH
+        if not p.exists():
+            raise RuntimeError(f"CUDA library {p} is missing: run the package build first")
+        lib = C.CDLL(str(p))
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        raise QEError(status, load().qe_last_error().decode())
+
+
+def _i32(xs):
+    return np.ascontiguousarray(np.asarray(xs, dtype=np.int32).reshape(-1))
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _mat(U, k):
+    M = np.ascontiguousarray(np.asarray(U, dtype=np.complex128))
+    if M.shape != (1 << k, 1 << k):
+        raise ValueError(f"matrix must be {1 << k}x{1 << k}")
+    return M
+
+
+class State:
+    """One state vector of 2**n amplitudes on the current CUDA device.
+
+    ``dtype`` is ``"c128"`` or ``"c64"``.  Memory comes from a torch tensor
+    (kept alive by this object); work is enqueued on ``stream`` (a
+    ``torch.cuda.Stream``; default: torch's current stream).
+    """
+
+    def __init__(self, n: int, dtype: str = "c128", stream=None, tensor=None):
+        import torch
+
+        lib = load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the emulator has no CPU fallback")
+        self.n = int(n)
+        self.dtype = dtype
+        self._dt = C128 if dtype == "c128" else C64
+        if dtype not in ("c128", "c64"):
+            raise ValueError("dtype must be 'c128' or 'c64'")
+        real = torch.float64 if self._dt == C128 else torch.float32
+        if tensor is None:
+            tensor = torch.empty(2 << self.n, dtype=real, device="cuda")
+        self.tensor = tensor
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(lib.qe_alloc_state(self.n, self._dt, C.c_void_p(tensor.data_ptr()),
+                                  tensor.numel() * tensor.element_size(),
+                                  C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self._h = h
+
+    # -- lifetime --------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(load().qe_free_state(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- initialisation and data movement -------------------------------------
+    def init_basis(self, index=0):
+        _check(load().qe_init_basis(self._h, int(index)))
+
+    def init_random(self, seed):
+        _check(load().qe_init_random(self._h, int(seed)))
+
+    def set(self, psi, offset=0):
+        a = np.ascontiguousarray(psi, dtype=np.complex128 if self._dt == C128 else np.complex64)
+        _check(load().qe_set_amplitudes(self._h, _ptr(a), int(offset), a.size))
+
+    def get(self, offset=0, count=None, out=None):
+        """Copy amplitudes to host memory (into ``out`` when given, e.g. a view
+        of pinned memory)."""
+        count = (1 << self.n) - offset if count is None else count
+        dt = np.complex128 if self._dt == C128 else np.complex64
+        a = np.empty(count, dtype=dt) if out is None else out
+        if a.dtype != dt or a.size != count or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("out has the wrong dtype, size or layout")
+        _check(load().qe_get_amplitudes(self._h, _ptr(a), int(offset), int(count)))
+        return a
+
+    # -- operations ---------------------------------------------------------
+    def apply_gate(self, qubits, U):
+        q = _i32(qubits)
+        M = _mat(U, q.size)
+        _check(load().qe_apply_gate(self._h, q.size, _ptr(q), _ptr(M)))
+
+    def apply_controlled(self, controls, targets, U):
+        c, t = _i32(controls), _i32(targets)
+        M = _mat(U, t.size)
+        _check(load().qe_apply_controlled(self._h, c.size, _ptr(c), t.size, _ptr(t), _ptr(M)))
+
+    def apply(self, gate):
+        """Apply an ``inputs.Gate`` (dense, or controlled when it has controls)."""
+        if gate.controls:
+            self.apply_controlled(gate.controls, gate.qubits, gate.matrix)
+        else:
+            self.apply_gate(gate.qubits, gate.matrix)
+
+    def apply_qft(self, lo, m, inverse=False):
+        _check(load().qe_apply_qft(self._h, int(lo), int(m), int(bool(inverse))))
+
+    def add_const(self, qubits, c):
+        q = _i32(qubits)
+        _check(load().qe_apply_add_const(self._h, q.size, _ptr(q), int(c) & ((1 << 64) - 1)))
+
+    def expectation(self, xmask, zmask, coeff):
+        xm = np.ascontiguousarray(np.asarray(xmask, dtype=np.uint64))
+        zm = np.ascontiguousarray(np.asarray(zmask, dtype=np.uint64))
+        cf = np.ascontiguousarray(np.asarray(coeff, dtype=np.float64))
+        out = C.c_double()
+        _check(load().qe_expectation(self._h, xm.size, _ptr(xm), _ptr(zm), _ptr(cf), C.byref(out)))
+        return out.value
+
+    def probs(self, qubits):
+        q = _i32(qubits)
+        out = np.empty(1 << q.size, dtype=np.float64)
+        _check(load().qe_probs(self._h, q.size, _ptr(q), _ptr(out)))
+        return out
+
+    def norm2(self):
+        out = C.c_double()
+        _check(load().qe_norm2(self._h, C.byref(out)))
+        return out.value
+
+    def flush(self):
+        _check(load().qe_flush(self._h))
+
+    def sync(self):
+        _check(load().qe_sync(self._h))
+
+    def set_policy(self, policy=POLICY_AUTO, max_k=None):
+        if max_k is None:
+            max_k = 2 if self._dt == C128 else 4
+        _check(load().qe_set_policy(self._h, int(policy), int(max_k)))
+
+    def stats(self):
+        st = Stats()
+        _check(load().qe_get_stats(self._h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in Stats._fields_}
+
+    def reset_stats(self):
+        _check(load().qe_reset_stats(self._h))
+
+    def profile(self, enable=True):
+        _check(load().qe_profile_enable(self._h, int(bool(enable))))
+
+    def profile_read(self):
+        """{kernel name: (launches, total_ms, algorithmic bytes)}; synchronises."""
+        buf = (KernelProfile * 64)()
+        cnt = C.c_int()
+        _check(load().qe_profile_read(self._h, buf, 64, C.byref(cnt)))
+        return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms, buf[i].bytes)
+                for i in range(min(cnt.value, 64))}

@@ -1,0 +1,391 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Every input comes from ``inputs`` (seeded); the oracle computes the expected
+values; the GPU result is compared element by element.
+
+Tolerances (complex128, double-float arithmetic on the FP32 pipes):
+  max |gpu - oracle| <= 1e-12 and fidelity >= 1 - 1e-10 (the FP64 bar);
+  permutations (CNOT/MCX/SWAP, add-constant, bit reversal) are bit-exact.
+complex64: FP32 arithmetic, max-abs <= 2e-6 per operation sequence used here
+(about 2^-24 per gate times the few dozen gates of each test), stated per test.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1604_06460_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+FID = 1 - 1e-10
+
+
+@pytest.fixture(scope="module")
+def qe():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1604_06460_gb300 import build as B
+    B.build()
+    from paper_1604_06460_gb300 import qe as Q
+    Q.load()
+    return Q
+
+
+def close(got, ref, tol=TOL, fid=FID):
+    err = float(np.max(np.abs(got - ref)))
+    f = oracle.fidelity(ref, got)
+    assert err <= tol, f"max-abs {err:.3e} > {tol}"
+    assert f >= fid, f"fidelity {f!r}"
+    return err
+
+
+def make(qe, n, dtype="c128", psi=None, max_k=1, native=False):
+    import os
+    if native:
+        os.environ["QE_C128_ARITH"] = "f64"
+    try:
+        st = qe.State(n, dtype)
+    finally:
+        os.environ.pop("QE_C128_ARITH", None)
+    st.set_policy(qe.POLICY_AUTO, max_k)
+    if psi is not None:
+        st.set(psi)
+    return st
+
+
+def rand_unitary(d, rng):
+    z = rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))
+    q, r = np.linalg.qr(z)
+    return q * (np.diag(r) / np.abs(np.diag(r)))[None, :]
+
+
+# ------------------------------------------------------------------ init
+def test_init_basis_exact(qe):
+    with make(qe, 9) as st:
+        st.init_basis(300)
+        got = st.get()
+    want = np.zeros(512, complex)
+    want[300] = 1
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("n", [5, 12, 17])
+def test_init_random_matches_oracle_generator(qe, n):
+    with make(qe, n) as st:
+        st.init_random(1234 + n)
+        got = st.get()
+    ref = oracle.gaussian_state(n, 1234 + n)
+    # same Philox words; libm vs CUDA log/sin/cos differ in the last ulp
+    close(got, ref, tol=1e-14)
+
+
+def test_init_random_c64(qe):
+    with make(qe, 12, "c64") as st:
+        st.init_random(7)
+        got = st.get().astype(np.complex128)
+    ref = oracle.gaussian_state(12, 7)
+    assert np.max(np.abs(got - ref)) < 1e-7
+
+
+# ------------------------------------------------------- single gates
+@pytest.mark.parametrize("native", [False, True])
+@pytest.mark.parametrize("q", [0, 1, 3, 4, 5, 9, 10, 13])
+def test_1q_dense_every_position(qe, q, native):
+    n = 14
+    psi = I.random_state(n, q)
+    U = I.haar_u2(np.random.default_rng(q))
+    with make(qe, n, psi=psi, native=native) as st:
+        st.apply_gate([q], U)
+        got = st.get()
+    close(got, oracle.apply_gate(psi, [q], U))
+
+
+@pytest.mark.parametrize("qubits", [[0, 1], [1, 0], [4, 11], [12, 2, 7], [0, 5, 10, 13],
+                                    [3, 4, 5, 6, 7], [13, 0, 9, 1, 6], [10, 11, 12, 13]])
+def test_kq_dense(qe, qubits):
+    n = 14
+    rng = np.random.default_rng(len(qubits) * 100 + qubits[0])
+    U = rand_unitary(1 << len(qubits), rng)
+    psi = I.random_state(n, 3)
+    with make(qe, n, psi=psi, max_k=5) as st:
+        st.apply_gate(qubits, U)
+        got = st.get()
+    close(got, oracle.apply_gate(psi, qubits, U))
+
+
+def test_kq_dense_small_state(qe):
+    # n below the tile size: one tile covers the whole state
+    n = 6
+    U = rand_unitary(8, np.random.default_rng(2))
+    psi = I.random_state(n, 4)
+    with make(qe, n, psi=psi, max_k=5) as st:
+        st.apply_gate([5, 0, 3], U)
+        got = st.get()
+    close(got, oracle.apply_gate(psi, [5, 0, 3], U))
+
+
+def test_structured_gates(qe):
+    n = 13
+    psi = I.random_state(n, 8)
+    ref = psi.copy()
+    gates = [I.cnot(3, 0), I.cnot(0, 12), I.cz(2, 9), I.cr(5, 1, 0.3), I.cr(0, 11, -1.7),
+             I.single(7, I.mat_rz(0.4)), I.single(0, I.mat_t()), I.single(4, I.mat_s()),
+             I.single(6, I.mat_x()), I.single(8, I.mat_y()), I.single(10, I.mat_z()),
+             I.Gate((4, 9), np.eye(4)[[0, 2, 1, 3]].astype(complex), (), "swap")]
+    with make(qe, n, psi=psi) as st:
+        for g in gates:
+            st.apply(g)
+            ref = oracle.apply_gate(ref, g.qubits, g.matrix)
+        got = st.get()
+    close(got, ref)
+
+
+def test_permutation_gates_bit_exact(qe):
+    n = 12
+    psi = I.random_state(n, 9)
+    ref = psi.copy()
+    gates = [I.cnot(0, 1), I.cnot(11, 3), I.single(5, I.mat_x()), I.mcx([0, 2, 7], 11),
+             I.mcx([1, 3, 4, 5, 6, 8, 9, 10], 0)]
+    with make(qe, n, psi=psi) as st:
+        for g in gates:
+            st.apply(g)
+            if g.controls:
+                ref = oracle.apply_mcx(ref, list(g.controls), g.qubits[0])
+            else:
+                ref = oracle.apply_gate(ref, g.qubits, g.matrix)
+        got = st.get()
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("controls,targets", [([3], [0]), ([0, 9], [4]), ([2], [5, 11]), ([1, 4, 7], [0, 12])])
+def test_controlled_dense(qe, controls, targets):
+    n = 13
+    U = rand_unitary(1 << len(targets), np.random.default_rng(len(controls)))
+    psi = I.random_state(n, 10)
+    with make(qe, n, psi=psi) as st:
+        st.apply_controlled(controls, targets, U)
+        got = st.get()
+    close(got, oracle.apply_controlled(psi, controls, targets, U))
+
+
+# ------------------------------------------------------------ circuits
+@pytest.mark.parametrize("max_k", [1, 2, 3, 4, 5])
+def test_random_circuit_fused_vs_oracle(qe, max_k):
+    n = 14
+    gates = I.random_circuit(n, 10, seed=11)
+    ref = oracle.zero_state(n)
+    for g in gates:
+        ref = oracle.apply_gate(ref, g.qubits, g.matrix)
+    with make(qe, n, max_k=max_k) as st:
+        for g in gates:
+            st.apply(g)
+        got = st.get()
+        stats = st.stats()
+    close(got, ref)
+    assert stats["gates_applied"] == len(gates)
+
+
+def test_ghz_closed_form(qe):
+    n = 16
+    with make(qe, n) as st:
+        for g in I.ghz_circuit(n):
+            st.apply(g)
+        got = st.get()
+    want = np.zeros(1 << n, complex)
+    want[0] = want[-1] = 1 / np.sqrt(2)
+    assert np.max(np.abs(got - want)) < 1e-15
+
+
+def test_random_circuit_c64(qe):
+    n = 14
+    gates = I.random_circuit(n, 6, seed=5)
+    ref = oracle.zero_state(n)
+    for g in gates:
+        ref = oracle.apply_gate(ref, g.qubits, g.matrix)
+    for max_k in (1, 4):
+        with make(qe, n, "c64", max_k=max_k) as st:
+            for g in gates:
+                st.apply(g)
+            got = st.get().astype(np.complex128)
+        # FP32: ~2^-24 per operation on amplitudes of size ~2^-7
+        assert np.max(np.abs(got - ref)) < 2e-6
+        assert oracle.fidelity(ref, got) > 1 - 1e-9
+
+
+# ----------------------------------------------------------------- QFT
+@pytest.mark.parametrize("n,lo,m", [(8, 0, 8), (10, 2, 5), (12, 0, 12), (14, 0, 14), (15, 1, 13), (13, 6, 7)])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_qft_emulated_vs_dft(qe, n, lo, m, inverse):
+    psi = I.random_state(n, n + lo + m)
+    with make(qe, n, psi=psi) as st:
+        st.set_policy(qe.POLICY_EMULATE, 1)
+        st.apply_qft(lo, m, inverse)
+        got = st.get()
+    close(got, oracle.qft_dft(psi, lo, m, inverse))
+
+
+@pytest.mark.parametrize("n,lo,m", [(9, 0, 9), (12, 3, 6)])
+def test_qft_simulated_vs_dft(qe, n, lo, m):
+    psi = I.random_state(n, 40 + m)
+    with make(qe, n, psi=psi) as st:
+        st.set_policy(qe.POLICY_SIMULATE, 1)
+        st.apply_qft(lo, m)
+        got = st.get()
+    close(got, oracle.qft_dft(psi, lo, m))
+
+
+def test_qft_basis_state_closed_form(qe):
+    n, x = 13, 1234
+    with make(qe, n) as st:
+        st.set_policy(qe.POLICY_EMULATE, 1)
+        st.init_basis(x)
+        st.apply_qft(0, n)
+        got = st.get()
+    l = np.arange(1 << n)
+    want = np.exp(2j * np.pi * ((x * l) % (1 << n)) / (1 << n)) / np.sqrt(1 << n)
+    assert np.max(np.abs(got - want)) < 1e-15
+
+
+def test_qft_many_passes_sampled(qe):
+    # 24 register qubits: three FFT passes plus the bit reversal
+    n, lo, m = 25, 1, 24
+    with make(qe, n) as st:
+        st.set_policy(qe.POLICY_EMULATE, 1)
+        st.init_random(3)
+        psi = st.get()
+        st.apply_qft(lo, m)
+        rng = np.random.default_rng(0)
+        idx = [0, 1, (1 << n) - 1] + list(rng.integers(0, 1 << n, size=3))
+        for i in idx:
+            want = oracle.qft_amplitude(psi, lo, m, int(i))
+            got = st.get(int(i), 1)[0]
+            assert abs(got - want) < 1e-12
+        st.apply_qft(lo, m, inverse=True)
+        back = st.get()
+    close(back, psi)
+
+
+def test_qft_c64(qe):
+    n, lo, m = 14, 0, 14
+    psi = I.random_state(n, 77)
+    with make(qe, n, "c64", psi=psi) as st:
+        st.set_policy(qe.POLICY_EMULATE, 1)
+        st.apply_qft(lo, m)
+        got = st.get().astype(np.complex128)
+    ref = oracle.qft_dft(psi, lo, m)
+    assert np.max(np.abs(got - ref)) < 1e-6
+
+
+# --------------------------------------------------------- add constant
+@pytest.mark.parametrize("n,qubits,c", [
+    (12, list(range(0, 8)), 77),          # slice in shared memory
+    (12, list(range(2, 12)), 1000),       # slice of 2^12
+    (18, list(range(0, 16)), 40503),      # cluster of 8 CTAs
+    (17, list(range(1, 16)), 12345),      # cluster, lo = 1
+    (14, list(range(6, 14)), 201),        # walk, coalesced columns
+    (14, list(range(5, 14)), 256),        # walk with gcd > 1
+    (13, [1, 5, 3, 12], 11),              # non-contiguous register
+    (10, list(range(10)), 1023),          # whole state
+])
+def test_add_const_bit_exact(qe, n, qubits, c):
+    psi = I.random_state(n, c)
+    with make(qe, n, psi=psi) as st:
+        st.set_policy(qe.POLICY_EMULATE, 1)
+        st.add_const(qubits, c)
+        got = st.get()
+    assert np.array_equal(got, oracle.add_const(psi, qubits, c))
+
+
+def test_add_const_simulated_bit_exact(qe):
+    n, qubits, c = 12, list(range(2, 10)), 173
+    psi = I.random_state(n, 5)
+    with make(qe, n, psi=psi) as st:
+        st.set_policy(qe.POLICY_SIMULATE, 1)
+        st.add_const(qubits, c)
+        got = st.get()
+    assert np.array_equal(got, oracle.add_const(psi, qubits, c))
+
+
+def test_add_const_c64_and_roundtrip(qe):
+    n, qubits, c = 16, list(range(0, 16)), 999
+    psi = I.random_state(n, 6).astype(np.complex64)
+    with make(qe, n, "c64", psi=psi) as st:
+        st.add_const(qubits, c)
+        got = st.get()
+        st.add_const(qubits, (1 << 16) - c)
+        back = st.get()
+    want = oracle.add_const(psi.astype(np.complex128), qubits, c).astype(np.complex64)
+    assert np.array_equal(got, want)
+    assert np.array_equal(back, psi)
+
+
+# ----------------------------------------------- expectation and probs
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_tfim_expectation(qe, dtype):
+    n = 12
+    psi = I.random_state(n, 21)
+    xm, zm, cf = I.tfim_terms(n)
+    with make(qe, n, dtype, psi=psi) as st:
+        e = st.expectation(xm, zm, cf)
+    ref = oracle.expectation(psi, xm, zm, cf)
+    assert abs(e - ref) < (1e-12 if dtype == "c128" else 1e-5)
+
+
+def test_tfim_closed_forms(qe):
+    n = 11
+    xm, zm, cf = I.tfim_terms(n)
+    with make(qe, n) as st:
+        assert abs(st.expectation(xm, zm, cf) - (n - 1)) < 1e-13
+        for q in range(n):
+            st.apply_gate([q], I.mat_h())
+        assert abs(st.expectation(xm, zm, cf) - 0.7 * n) < 1e-12
+
+
+def test_general_pauli_terms(qe):
+    n = 10
+    rng = np.random.default_rng(5)
+    xm = rng.integers(0, 1 << n, size=13).astype(np.uint64)
+    zm = rng.integers(0, 1 << n, size=13).astype(np.uint64)
+    cf = rng.standard_normal(13)
+    psi = I.random_state(n, 31)
+    with make(qe, n, psi=psi) as st:
+        e = st.expectation(xm, zm, cf)
+    assert abs(e - oracle.expectation(psi, xm, zm, cf)) < 1e-12
+
+
+@pytest.mark.parametrize("qubits", [[0], [3, 0], [11, 2, 6], [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11]])
+def test_probs(qe, qubits):
+    n = 12
+    psi = I.random_state(n, 17)
+    with make(qe, n, psi=psi) as st:
+        p = st.probs(qubits)
+        nrm = st.norm2()
+    ref = oracle.probs(psi, qubits)
+    # per-thread double-float partials carry about 44 significant bits
+    assert np.max(np.abs(p - ref)) < 1e-13
+    assert abs(nrm - 1) < 1e-13
+
+
+def test_probs_ghz(qe):
+    n = 9
+    with make(qe, n) as st:
+        for g in I.ghz_circuit(n):
+            st.apply(g)
+        p = st.probs([0, 8])
+    assert np.allclose(p, [0.5, 0, 0, 0.5], atol=1e-15)
+
+
+# --------------------------------------------------------- error paths
+def test_invalid_arguments_leave_state_untouched(qe):
+    n = 6
+    psi = I.random_state(n, 1)
+    with make(qe, n, psi=psi) as st:
+        for bad in [lambda: st.apply_gate([0, 0], np.eye(4)), lambda: st.apply_gate([6], np.eye(2)),
+                    lambda: st.apply_qft(3, 4), lambda: st.add_const([7], 1),
+                    lambda: st.probs([0, 0]), lambda: st.apply_gate([1], np.full((2, 2), np.nan))]:
+            with pytest.raises(qe.QEError) as ei:
+                bad()
+            assert ei.value.status == -1
+        assert np.array_equal(st.get(), psi)
