@@ -347,6 +347,8 @@ int qe_alloc_state(int n, int dtype, void* dev_ptr, size_t bytes, void* stream, 
     s->max_k = dtype == QE_C128 ? 2 : 4;
     const char* ar = std::getenv("QE_C128_ARITH");
     s->c128_native = (ar && std::strcmp(ar, "f64") == 0) ? 1 : 0;
+    const char* tl = std::getenv("QE_DENSE_TILE");
+    s->force_tile = (tl && std::strcmp(tl, "1") == 0) ? 1 : 0;
     try {
         if (dev_ptr) {
             if (bytes < need) fail(QE_ERR_ARG, "borrowed buffer too small");

@@ -153,16 +153,93 @@ void dense_impl(qe_state* s, const int* qubits, const cd* U) {
     QE_CUDA(cudaGetLastError());
 }
 
+template <class P, int K>
+void direct_impl(qe_state* s, const int* qubits, const cd* U);
+
 template <class P>
 void dense_k(qe_state* s, int k, const int* qubits, const cd* U) {
+    // 1..3 qubits: direct kernel (dense_tile forces the shared-memory tile path)
+    const bool tile = s->force_tile;
     switch (k) {
-        case 1: dense_impl<P, 1>(s, qubits, U); break;
-        case 2: dense_impl<P, 2>(s, qubits, U); break;
-        case 3: dense_impl<P, 3>(s, qubits, U); break;
+        case 1: tile ? dense_impl<P, 1>(s, qubits, U) : direct_impl<P, 1>(s, qubits, U); break;
+        case 2: tile ? dense_impl<P, 2>(s, qubits, U) : direct_impl<P, 2>(s, qubits, U); break;
+        case 3: tile ? dense_impl<P, 3>(s, qubits, U) : direct_impl<P, 3>(s, qubits, U); break;
         case 4: dense_impl<P, 4>(s, qubits, U); break;
         case 5: dense_impl<P, 5>(s, qubits, U); break;
         default: fail(QE_ERR_ARG, "dense gate needs 1 <= k <= 5");
     }
+}
+
+// --------------------------------------------------------------- direct
+// Small dense gates (k <= 3) without shared memory: each thread owns whole
+// groups of 2^k amplitudes, loads them straight from global memory and
+// multiplies by the matrix held in the kernel parameters (a uniform,
+// broadcast constant-bank operand).  Consecutive threads own groups that are
+// consecutive in the non-gate index bits, so every load and store instruction
+// of a warp covers contiguous sectors.  G groups per iteration keep 2^k * G
+// independent loads in flight per thread.
+template <class P, int K>
+struct DirectArgs {
+    typename P::S* x;
+    uint64_t ngroups;
+    uint8_t sorted[8];
+    uint64_t dep[1 << K];
+    typename P::M U[(1 << K) * (1 << K)];
+};
+
+template <class P, int K, int G>
+__global__ void __launch_bounds__(kThreads) k_gate_direct(const __grid_constant__ DirectArgs<P, K> a) {
+    constexpr int D = 1 << K;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t g0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g0 < a.ngroups; g0 += stride * G) {
+        uint64_t base[G];
+        typename P::V v[G][D];
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            const uint64_t g = g0 + j * stride;
+            base[j] = insert_zero_bits(g < a.ngroups ? g : 0, a.sorted, K);
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+                if (g < a.ngroups) v[j][c] = P::load(a.x[base[j] + a.dep[c]]);
+        }
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            if (g0 + j * stride >= a.ngroups) break;
+#pragma unroll
+            for (int r = 0; r < D; ++r) {
+                auto acc = P::zero();
+#pragma unroll
+                for (int c = 0; c < D; ++c) P::mac(acc, a.U[r * D + c], v[j][c]);
+                a.x[base[j] + a.dep[r]] = P::out(acc);
+            }
+        }
+    }
+}
+
+template <class P, int K>
+void direct_impl(qe_state* s, const int* qubits, const cd* U) {
+    constexpr int D = 1 << K;
+    static thread_local DirectArgs<P, K> a;
+    a.x = reinterpret_cast<typename P::S*>(s->d);
+    a.ngroups = dim(s) >> K;
+    int srt[8];
+    for (int j = 0; j < K; ++j) srt[j] = qubits[j];
+    std::sort(srt, srt + K);
+    for (int j = 0; j < K; ++j) a.sorted[j] = (uint8_t)srt[j];
+    for (int c = 0; c < D; ++c) {
+        uint64_t o = 0;
+        for (int j = 0; j < K; ++j)
+            if ((c >> j) & 1) o |= 1ull << qubits[j];
+        a.dep[c] = o;
+    }
+    for (int i = 0; i < D * D; ++i) a.U[i] = to_m<P>(U[i]);
+    constexpr int G = (K <= 2) ? 2 : 1;
+    auto fn = k_gate_direct<P, K, G>;
+    unsigned grid = persistent_grid((const void*)fn, kThreads, 0, (a.ngroups + kThreads * G - 1) / (kThreads * G));
+    static const char* names[] = {"", "gate_direct_k1", "gate_direct_k2", "gate_direct_k3"};
+    Launch L(s, names[K], 2.0 * dim(s) * amp_bytes(s));
+    fn<<<grid, kThreads, 0, s->stream>>>(a);
+    QE_CUDA(cudaGetLastError());
 }
 
 // --------------------------------------------------------------- diagonal

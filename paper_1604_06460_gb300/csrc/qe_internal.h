@@ -53,6 +53,7 @@ struct qe_state {
     int policy = QE_POLICY_AUTO;
     int max_k = 4;
     int c128_native = 0;          // 1: native FP64 arithmetic for complex128
+    int force_tile = 0;           // 1: dense gates always through shared-memory tiles
     std::vector<qe::PendingGate> queue;
     // device scratch for reductions, grown on demand
     void* scratch = nullptr;

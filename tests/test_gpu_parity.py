@@ -41,14 +41,17 @@ def close(got, ref, tol=TOL, fid=FID):
     return err
 
 
-def make(qe, n, dtype="c128", psi=None, max_k=1, native=False):
+def make(qe, n, dtype="c128", psi=None, max_k=1, native=False, tile=False):
     import os
     if native:
         os.environ["QE_C128_ARITH"] = "f64"
+    if tile:
+        os.environ["QE_DENSE_TILE"] = "1"
     try:
         st = qe.State(n, dtype)
     finally:
         os.environ.pop("QE_C128_ARITH", None)
+        os.environ.pop("QE_DENSE_TILE", None)
     st.set_policy(qe.POLICY_AUTO, max_k)
     if psi is not None:
         st.set(psi)
@@ -90,26 +93,27 @@ def test_init_random_c64(qe):
 
 
 # ------------------------------------------------------- single gates
-@pytest.mark.parametrize("native", [False, True])
+@pytest.mark.parametrize("native,tile", [(False, False), (True, False), (False, True)])
 @pytest.mark.parametrize("q", [0, 1, 3, 4, 5, 9, 10, 13])
-def test_1q_dense_every_position(qe, q, native):
+def test_1q_dense_every_position(qe, q, native, tile):
     n = 14
     psi = I.random_state(n, q)
     U = I.haar_u2(np.random.default_rng(q))
-    with make(qe, n, psi=psi, native=native) as st:
+    with make(qe, n, psi=psi, native=native, tile=tile) as st:
         st.apply_gate([q], U)
         got = st.get()
     close(got, oracle.apply_gate(psi, [q], U))
 
 
+@pytest.mark.parametrize("tile", [False, True])
 @pytest.mark.parametrize("qubits", [[0, 1], [1, 0], [4, 11], [12, 2, 7], [0, 5, 10, 13],
                                     [3, 4, 5, 6, 7], [13, 0, 9, 1, 6], [10, 11, 12, 13]])
-def test_kq_dense(qe, qubits):
+def test_kq_dense(qe, qubits, tile):
     n = 14
     rng = np.random.default_rng(len(qubits) * 100 + qubits[0])
     U = rand_unitary(1 << len(qubits), rng)
     psi = I.random_state(n, 3)
-    with make(qe, n, psi=psi, max_k=5) as st:
+    with make(qe, n, psi=psi, max_k=5, tile=tile) as st:
         st.apply_gate(qubits, U)
         got = st.get()
     close(got, oracle.apply_gate(psi, qubits, U))
@@ -171,14 +175,15 @@ def test_controlled_dense(qe, controls, targets):
 
 
 # ------------------------------------------------------------ circuits
-@pytest.mark.parametrize("max_k", [1, 2, 3, 4, 5])
-def test_random_circuit_fused_vs_oracle(qe, max_k):
+@pytest.mark.parametrize("max_k,tile", [(1, False), (2, False), (3, False), (4, False), (5, False),
+                                        (2, True)])
+def test_random_circuit_fused_vs_oracle(qe, max_k, tile):
     n = 14
     gates = I.random_circuit(n, 10, seed=11)
     ref = oracle.zero_state(n)
     for g in gates:
         ref = oracle.apply_gate(ref, g.qubits, g.matrix)
-    with make(qe, n, max_k=max_k) as st:
+    with make(qe, n, max_k=max_k, tile=tile) as st:
         for g in gates:
             st.apply(g)
         got = st.get()
