@@ -177,6 +177,31 @@ typedef struct {
 int qe_profile_enable(qe_state* s, int enable);
 int qe_profile_read(qe_state* s, qe_kernel_profile* out, int max, int* count);
 
+/* Marginal probabilities that allocate nothing.  The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate
+ * device memory: code running while another component captures a CUDA graph,
+ * processes whose GPU memory belongs entirely to another allocator or arena,
+ * and hosts that forbid allocation after start-up.  It computes what
+ * qe_probs computes, from a raw state pointer instead of a handle:
+ *   state  device pointer to 2^n amplitudes of dtype (QE_C64 / QE_C128);
+ *   qubits host array of m distinct qubits < n, 1 <= m <= 16;
+ *   out    device pointer to 2^m doubles (written; caller-owned);
+ *   stream cudaStream_t the work is enqueued on (NULL = legacy default).
+ * It returns after enqueueing (synchronise the stream before reading out).
+ * Block partial sums live in one static device array of 65536 (sum,
+ * compensation) pairs, 1 MiB, which every GPU that loads the library keeps
+ * until the process exits; requests needing more partials than that return
+ * QE_ERR_ARG (with m <= 16 none does).  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress) once for that device,
+ * so make the first call on each device before any stream capture.  All
+ * calls share the array: calls whose work overlaps on the GPU (other streams,
+ * other threads) race and must be serialised by the caller.  Every partial a
+ * call reads is written earlier by the same call, so nothing needs clearing.
+ * Status only (QE_ERR_ARG for bad arguments, QE_ERR_CUDA for a failed
+ * launch); qe_last_error() is not updated. */
+int qe_probs_noalloc(const void* state, int n, int dtype, int m, const int* qubits,
+                     double* out, void* stream);
+
 /* Human-readable description of the calling thread's last failure. */
 const char* qe_last_error(void);
 

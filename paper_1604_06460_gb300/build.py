@@ -19,7 +19,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", f"-I{INCLUDE}"]
-SOURCES = ["api.cu", "plan.cu", "state.cu", "gates.cu", "fft.cu", "perm.cu", "reduce.cu"]
+SOURCES = ["api.cu", "plan.cu", "state.cu", "gates.cu", "fft.cu", "perm.cu", "reduce.cu", "noalloc.cu"]
 
 
 def _newest_input() -> float:

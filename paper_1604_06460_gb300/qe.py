@@ -59,6 +59,7 @@ SIGNATURES = {
     "qe_reset_stats": (_i, [_vp]),
     "qe_profile_enable": (_i, [_vp, _i]),
     "qe_profile_read": (_i, [_vp, C.POINTER(KernelProfile), _i, C.POINTER(_i)]),
+    "qe_probs_noalloc": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp]),
     "qe_last_error": (C.c_char_p, []),
 }
 
