@@ -161,6 +161,68 @@ typedef struct {
 int qe_get_stats(const qe_state* s, qe_stats* out);
 int qe_reset_stats(qe_state* s);
 
+/* ---------------------------------------------------------------- batch
+ * Many small parameterised circuits in one persistent launch, replayed as a
+ * CUDA graph.  Circuit c acts on nqubits[c] qubits (1 <= n <= 23 for
+ * QE_C128, <= 25 for QE_C64), starts from |0...0> and applies `layers` times:
+ * RY(theta) then RZ(phi) on every qubit q (RY(t) = [[cos t/2, -sin t/2],
+ * [sin t/2, cos t/2]], RZ as in Table I), then CZ on (q, q+1) for
+ * q = 0..n-2.  angles holds, circuit after circuit, layer after layer, qubit
+ * after qubit, the pair (theta, phi).  The result of circuit c is the energy
+ * <psi_c| sum_{i<n-1} Z_i Z_{i+1} + hx sum_i X_i |psi_c> (open transverse-field
+ * Ising chain; the expectation computed directly, Sec. III-D).  qe_batch_create
+ * copies the inputs, allocates the device states of circuits too large for
+ * one CTA's shared memory, builds the work queue and captures the graph.
+ * qe_batch_run replays it and writes count energies to host memory.
+ * qe_batch_tune times the candidate tile schedules (tile bits, tiles per work
+ * item, threads per CTA) reps times each and keeps the fastest; the chosen
+ * plan is returned through the optional pointers.  qe_batch_info reports
+ * the algorithmic HBM bytes of one run and the number of work items. */
+typedef struct qe_batch qe_batch;
+int qe_batch_create(int count, const int* nqubits, int layers, const double* angles,
+                    double hx, int dtype, void* stream, qe_batch** out);
+int qe_batch_run(qe_batch* b, double* energies);
+int qe_batch_tune(qe_batch* b, int reps, int* tile_bits, int* tiles_per_item, int* threads);
+int qe_batch_set_plan(qe_batch* b, int tile_bits, int tiles_per_item, int threads);
+int qe_batch_info(const qe_batch* b, double* hbm_bytes, int* items);
+int qe_batch_free(qe_batch* b);
+
+/* ------------------------------------------------------------ cost model
+ * A small network (16 features -> h1 -> h2 tanh units -> 1) that predicts
+ * log(milliseconds) of an operation, trained on timings the emulator itself
+ * measures.  With QE_POLICY_AUTO and a model attached (qe_set_cost_model) the
+ * planner uses it to choose emulation or simulation for each QFT / addition
+ * and the fusion width of each flushed gate sequence; without a model it
+ * falls back to the analytic rule.  The choice never changes a result beyond
+ * the arithmetic's rounding.  Forward, backward and Adam steps run in the
+ * library's own kernels on a private stream.
+ *   qe_cost_features: the 16 features of an operation: op (0 gate pass,
+ *     1 QFT emulated, 2 QFT simulated, 3 addition emulated, 4 addition
+ *     simulated), n, dtype, k (gate width), lo/hi (lowest/highest qubit
+ *     touched), m (register size), c (the added constant);
+ *   qe_cost_model_gradient: loss (mean squared error) and its gradient with
+ *     respect to all parameters for the samples X[n][16], targets t[n];
+ *   qe_cost_model_train: full-batch Adam for `epochs` steps at rate lr;
+ *     *loss receives the final training loss;
+ *   params: W1[h1][16] b1[h1] W2[h2][h1] b2[h2] W3[h2] b3 (float). */
+typedef struct qe_cost_model qe_cost_model;
+int qe_cost_model_create(int hidden1, int hidden2, uint64_t seed, qe_cost_model** out);
+int qe_cost_model_param_count(const qe_cost_model* m, int* count);
+int qe_cost_model_get_params(const qe_cost_model* m, float* params, int count);
+int qe_cost_model_set_params(qe_cost_model* m, const float* params, int count);
+int qe_cost_model_gradient(qe_cost_model* m, const float* X, const float* t, int n, float* grad,
+                           float* loss);
+int qe_cost_model_train(qe_cost_model* m, const float* X, const float* t, int n, int epochs,
+                        float lr, float* loss);
+int qe_cost_model_predict(qe_cost_model* m, const float* X, int n, float* y);
+int qe_cost_model_free(qe_cost_model* m);
+int qe_cost_features(int op, int n, int dtype, int k, int lo, int hi, int m, uint64_t c,
+                     float* features);
+int qe_set_cost_model(qe_state* s, qe_cost_model* model);
+/* Fusion width the planner would use for the gates queued now (the state's
+ * max_k, or the model's choice under QE_POLICY_AUTO), without applying them. */
+int qe_planned_fusion_width(qe_state* s, int* k);
+
 /* Per-kernel timing with CUDA events recorded on the state's stream around
  * every launch (measurement aid; the events add a few microseconds per
  * launch).  qe_profile_enable(s, 1) clears earlier records and starts

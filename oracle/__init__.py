@@ -60,6 +60,9 @@ def _load():
             "or_add_const_circuit": (None, [dp, i, i, dp, u64]),
             "or_expectation": (d, [dp, i, i, dp, dp, dp]),
             "or_probs": (None, [dp, i, i, dp, dp]),
+            "or_mlp_param_count": (i, [i, i, i]),
+            "or_mlp_forward": (None, [dp, i, i, i, dp, i, dp]),
+            "or_mlp_grad": (d, [dp, i, i, i, dp, dp, i, dp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -206,3 +209,28 @@ def fidelity(ref, got):
     g = np.asarray(got, dtype=np.complex128)
     ov = np.vdot(r, g)
     return float(abs(ov) ** 2 / (np.vdot(r, r).real * np.vdot(g, g).real))
+
+
+# --- cost-model network -------------------------------------------------
+def mlp_param_count(d, h1, h2):
+    return _load().or_mlp_param_count(d, h1, h2)
+
+
+def mlp_forward(params, X, h1, h2):
+    X = np.ascontiguousarray(np.asarray(X, dtype=np.float64))
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+    n, d = X.shape
+    y = np.empty(n)
+    _load().or_mlp_forward(_ptr(p), d, h1, h2, _ptr(X), n, _ptr(y))
+    return y
+
+
+def mlp_grad(params, X, t, h1, h2):
+    """(loss, gradient) of the mean squared error by backpropagation."""
+    X = np.ascontiguousarray(np.asarray(X, dtype=np.float64))
+    t = np.ascontiguousarray(np.asarray(t, dtype=np.float64))
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+    n, d = X.shape
+    g = np.empty_like(p)
+    loss = _load().or_mlp_grad(_ptr(p), d, h1, h2, _ptr(X), _ptr(t), n, _ptr(g))
+    return loss, g

@@ -378,3 +378,102 @@ void or_probs(const cplx* psi, int n, int m, const int* qubits, double* out) {
     for (uint64_t r = 0; r < M; ++r) out[r] = nsum_val(&acc[r]);
     free(acc);
 }
+
+/* ------------------------------------------------------------------ */
+/* The cost model's network (a multilayer perceptron; not from the paper,
+ * which chooses between emulation and simulation by performance models and
+ * measured cross-overs, Sec. III-B and Sec. IV-D).  Layout of params:
+ * W1[h1][d] b1[h1] W2[h2][h1] b2[h2] W3[h2] b3, tanh hidden units, linear
+ * output:  y = W3 . tanh(W2 tanh(W1 x + b1) + b2) + b3.
+ * Loss over a batch: L = (1/N) sum_s (y_s - t_s)^2. */
+static void mlp_sizes(int d, int h1, int h2, int* o1, int* o2, int* o3, int* o4, int* o5, int* o6) {
+    *o1 = 0;                 /* W1 */
+    *o2 = *o1 + h1 * d;      /* b1 */
+    *o3 = *o2 + h1;          /* W2 */
+    *o4 = *o3 + h2 * h1;     /* b2 */
+    *o5 = *o4 + h2;          /* W3 */
+    *o6 = *o5 + h2;          /* b3 */
+}
+
+int or_mlp_param_count(int d, int h1, int h2) { return h1 * d + h1 + h2 * h1 + h2 + h2 + 1; }
+
+void or_mlp_forward(const double* p, int d, int h1, int h2, const double* X, int n, double* y) {
+    int oW1, ob1, oW2, ob2, oW3, ob3;
+    mlp_sizes(d, h1, h2, &oW1, &ob1, &oW2, &ob2, &oW3, &ob3);
+    double* a1 = (double*)malloc(sizeof(double) * h1);
+    double* a2 = (double*)malloc(sizeof(double) * h2);
+    for (int s = 0; s < n; ++s) {
+        const double* x = X + (size_t)s * d;
+        for (int j = 0; j < h1; ++j) {
+            double z = p[ob1 + j];
+            for (int i = 0; i < d; ++i) z += p[oW1 + j * d + i] * x[i];
+            a1[j] = tanh(z);
+        }
+        for (int j = 0; j < h2; ++j) {
+            double z = p[ob2 + j];
+            for (int i = 0; i < h1; ++i) z += p[oW2 + j * h1 + i] * a1[i];
+            a2[j] = tanh(z);
+        }
+        double out = p[ob3];
+        for (int i = 0; i < h2; ++i) out += p[oW3 + i] * a2[i];
+        y[s] = out;
+    }
+    free(a1);
+    free(a2);
+}
+
+/* Gradient of L with respect to every parameter (backpropagation: the chain
+ * rule applied layer by layer, d tanh(z)/dz = 1 - tanh(z)^2).  Returns L. */
+double or_mlp_grad(const double* p, int d, int h1, int h2, const double* X, const double* t,
+                   int n, double* grad) {
+    int oW1, ob1, oW2, ob2, oW3, ob3;
+    mlp_sizes(d, h1, h2, &oW1, &ob1, &oW2, &ob2, &oW3, &ob3);
+    const int np = or_mlp_param_count(d, h1, h2);
+    for (int k = 0; k < np; ++k) grad[k] = 0.0;
+    double* a1 = (double*)malloc(sizeof(double) * h1);
+    double* a2 = (double*)malloc(sizeof(double) * h2);
+    double* d1 = (double*)malloc(sizeof(double) * h1);
+    double* d2 = (double*)malloc(sizeof(double) * h2);
+    double loss = 0.0;
+    for (int s = 0; s < n; ++s) {
+        const double* x = X + (size_t)s * d;
+        for (int j = 0; j < h1; ++j) {
+            double z = p[ob1 + j];
+            for (int i = 0; i < d; ++i) z += p[oW1 + j * d + i] * x[i];
+            a1[j] = tanh(z);
+        }
+        for (int j = 0; j < h2; ++j) {
+            double z = p[ob2 + j];
+            for (int i = 0; i < h1; ++i) z += p[oW2 + j * h1 + i] * a1[i];
+            a2[j] = tanh(z);
+        }
+        double y = p[ob3];
+        for (int i = 0; i < h2; ++i) y += p[oW3 + i] * a2[i];
+        const double r = y - t[s];
+        loss += r * r / n;
+        const double dy = 2.0 * r / n;                 /* dL/dy */
+        grad[ob3] += dy;
+        for (int i = 0; i < h2; ++i) {
+            grad[oW3 + i] += dy * a2[i];
+            d2[i] = dy * p[oW3 + i] * (1.0 - a2[i] * a2[i]);
+        }
+        for (int j = 0; j < h2; ++j) {
+            grad[ob2 + j] += d2[j];
+            for (int i = 0; i < h1; ++i) grad[oW2 + j * h1 + i] += d2[j] * a1[i];
+        }
+        for (int i = 0; i < h1; ++i) {
+            double acc = 0.0;
+            for (int j = 0; j < h2; ++j) acc += p[oW2 + j * h1 + i] * d2[j];
+            d1[i] = acc * (1.0 - a1[i] * a1[i]);
+        }
+        for (int j = 0; j < h1; ++j) {
+            grad[ob1 + j] += d1[j];
+            for (int i = 0; i < d; ++i) grad[oW1 + j * d + i] += d1[j] * x[i];
+        }
+    }
+    free(a1);
+    free(a2);
+    free(d1);
+    free(d2);
+    return loss;
+}

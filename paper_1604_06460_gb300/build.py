@@ -19,7 +19,8 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", f"-I{INCLUDE}"]
-SOURCES = ["api.cu", "plan.cu", "state.cu", "gates.cu", "fft.cu", "perm.cu", "reduce.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "plan.cu", "state.cu", "gates.cu", "fft.cu", "perm.cu", "reduce.cu", "batch.cu", "mlp.cu", "tcgen05.cu",
+           "noalloc.cu"]
 
 
 def _newest_input() -> float:

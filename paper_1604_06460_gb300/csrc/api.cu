@@ -9,7 +9,9 @@
 #include <string>
 #include <vector>
 
+#include "qe_batch.h"
 #include "qe_internal.h"
+#include "qe_mlp.h"
 #include "qe_plan.h"
 
 namespace {
@@ -206,45 +208,64 @@ void merge_into(Block& b, const Block& o) {
 }
 }  // namespace
 
-void flush(qe_state* s) {
-    if (s->queue.empty()) return;
-    std::vector<PendingGate> q;
-    q.swap(s->queue);
-    const int max_k = s->max_k;
+// A fused block ready to run (controls only for gates that came with them).
+struct Planned {
+    std::vector<int> q;
+    std::vector<cd> U;
+    uint64_t cmask = 0;
+};
+
+// Greedy fusion: consecutive gates whose qubits stay within max_k qubits are
+// multiplied into one block.  Open blocks have disjoint qubit sets (so they
+// commute); a gate that would overflow closes the blocks it touches.
+std::vector<Planned> plan_fusion(const std::vector<PendingGate>& q, int max_k) {
+    std::vector<Planned> out;
+    auto emit = [&](Block& b) {
+        Planned p;
+        p.q = std::move(b.q);
+        p.U = std::move(b.U);
+        out.push_back(std::move(p));
+    };
     if (max_k <= 1) {
         for (auto& g : q) {
-            apply_block(s, g.k, g.q, g.U, g.cmask);
-            s->stats.gates += 1;
+            Planned p;
+            p.q.assign(g.q, g.q + g.k);
+            p.U = g.U;
+            p.cmask = g.cmask;
+            out.push_back(std::move(p));
         }
-        return;
+        return out;
     }
     std::vector<Block> open;
     auto close_if = [&](uint64_t touch) {
         std::vector<Block> keep;
         for (auto& b : open) {
-            if (b.mask & touch) apply_block(s, (int)b.q.size(), b.q.data(), b.U, 0);
+            if (b.mask & touch) emit(b);
             else keep.push_back(std::move(b));
         }
         open.swap(keep);
     };
     for (auto& g : q) {
-        s->stats.gates += 1;
         uint64_t gmask = 0;
         for (int j = 0; j < g.k; ++j) gmask |= 1ull << g.q[j];
         if (g.cmask != 0 || g.k > max_k) {
             close_if(gmask | g.cmask);
-            apply_block(s, g.k, g.q, g.U, g.cmask);
+            Planned p;
+            p.q.assign(g.q, g.q + g.k);
+            p.U = g.U;
+            p.cmask = g.cmask;
+            out.push_back(std::move(p));
             continue;
         }
         uint64_t uni = gmask;
         for (auto& b : open)
             if (b.mask & gmask) uni |= b.mask;
+        Block nb;
+        nb.q.assign(g.q, g.q + g.k);
+        nb.U = g.U;
+        nb.mask = gmask;
+        nb.gates = 1;
         if (__builtin_popcountll(uni) <= max_k) {
-            Block nb;
-            nb.q.assign(g.q, g.q + g.k);
-            nb.U = g.U;
-            nb.mask = gmask;
-            nb.gates = 1;
             // earlier blocks touching the gate act first
             Block merged;
             bool first = true;
@@ -266,15 +287,49 @@ void flush(qe_state* s) {
             open.swap(keep);
         } else {
             close_if(gmask);
-            Block nb;
-            nb.q.assign(g.q, g.q + g.k);
-            nb.U = g.U;
-            nb.mask = gmask;
-            nb.gates = 1;
             open.push_back(std::move(nb));
         }
     }
     close_if(~0ull);
+    return out;
+}
+
+void flush(qe_state* s) {
+    if (s->queue.empty()) return;
+    std::vector<PendingGate> q;
+    q.swap(s->queue);
+    const int k = choose_fusion_width(s, q);
+    s->stats.gates += q.size();
+    for (auto& b : plan_fusion(q, k)) apply_block(s, (int)b.q.size(), b.q.data(), b.U, b.cmask);
+}
+
+// Fusion width: the state's max_k, or, under QE_POLICY_AUTO with a learned
+// model, the width in [1, max_k] whose planned blocks the model predicts to
+// run fastest (sum over blocks of the predicted pass time).
+int choose_fusion_width(qe_state* s, const std::vector<PendingGate>& q) {
+    if (s->policy != QE_POLICY_AUTO || !s->model || q.empty() || s->max_k <= 1) return s->max_k;
+    std::vector<float> X;
+    std::vector<int> owner;
+    for (int k = 1; k <= s->max_k; ++k) {
+        for (auto& b : plan_fusion(q, k)) {
+            int lo = s->n, hi = 0;
+            for (int v : b.q) { lo = std::min(lo, v); hi = std::max(hi, v); }
+            for (int j = 0; j < s->n; ++j)
+                if ((b.cmask >> j) & 1ull) { lo = std::min(lo, j); hi = std::max(hi, j); }
+            float f[kCostFeatures];
+            cost_features(kOpGatePass, s->n, s->dtype, (int)b.q.size(), lo, hi, 0, 0, f);
+            X.insert(X.end(), f, f + kCostFeatures);
+            owner.push_back(k);
+        }
+    }
+    std::vector<float> y(owner.size());
+    mlp_predict(s->model, X.data(), (int)owner.size(), y.data());
+    std::vector<double> total(s->max_k + 1, 0.0);
+    for (size_t i = 0; i < owner.size(); ++i) total[owner[i]] += std::exp((double)y[i]);
+    int best = 1;
+    for (int k = 2; k <= s->max_k; ++k)
+        if (total[k] < total[best]) best = k;
+    return best;
 }
 
 // ------------------------------------------------------------ subroutines
@@ -329,6 +384,10 @@ static void add_simulated(qe_state* s, int m, const int* qubits, uint64_t c) {
 // =================================================================== C ABI
 using namespace qe;
 
+static void check_batch(const qe_batch* b) {
+    if (!b || b->magic != 0xBA7C4) fail(QE_ERR_STATE, "invalid batch handle");
+}
+
 extern "C" {
 
 const char* qe_last_error(void) { return g_last_error.c_str(); }
@@ -349,6 +408,8 @@ int qe_alloc_state(int n, int dtype, void* dev_ptr, size_t bytes, void* stream, 
     s->c128_native = (ar && std::strcmp(ar, "f64") == 0) ? 1 : 0;
     const char* tl = std::getenv("QE_DENSE_TILE");
     s->force_tile = (tl && std::strcmp(tl, "1") == 0) ? 1 : 0;
+    const char* tc = std::getenv("QE_TENSOR_CORES");
+    s->tensor_cores = (tc && std::strcmp(tc, "0") == 0) ? 0 : 1;
     try {
         if (dev_ptr) {
             if (bytes < need) fail(QE_ERR_ARG, "borrowed buffer too small");
@@ -615,6 +676,244 @@ int qe_profile_read(qe_state* s, qe_kernel_profile* out, int max, int* count) {
     }
     *count = (int)acc.size();
     for (int i = 0; i < (int)acc.size() && i < max; ++i) out[i] = acc[i];
+    QE_API_END
+}
+
+int qe_batch_create(int count, const int* nqubits, int layers, const double* angles, double hx,
+                    int dtype, void* stream, qe_batch** out) {
+    QE_API_BEGIN
+    if (!out) fail(QE_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !nqubits || !angles || layers < 1) fail(QE_ERR_ARG, "bad batch description");
+    if (dtype != QE_C64 && dtype != QE_C128) fail(QE_ERR_ARG, "unknown dtype");
+    if (!std::isfinite(hx)) fail(QE_ERR_ARG, "non-finite field");
+    const int nmax = dtype == QE_C64 ? 25 : 23;
+    size_t nang = 0;
+    for (int c = 0; c < count; ++c) {
+        if (nqubits[c] < 1 || nqubits[c] > nmax) fail(QE_ERR_ARG, "qubit count out of range");
+        nang += (size_t)2 * layers * nqubits[c];
+    }
+    for (size_t i = 0; i < nang; ++i)
+        if (!std::isfinite(angles[i])) fail(QE_ERR_ARG, "non-finite angle");
+    auto* b = new qe_batch();
+    b->count = count;
+    b->layers = layers;
+    b->dtype = dtype;
+    b->hx = hx;
+    b->stream = (cudaStream_t)stream;
+    b->n.assign(nqubits, nqubits + count);
+    b->angles.assign(angles, angles + nang);
+    b->plan.T = dtype == QE_C64 ? 13 : 12;
+    int nbig = 0;
+    for (int v : b->n) nbig = std::max(nbig, v);
+    while (2 * b->plan.T - 1 < nbig) ++b->plan.T;   // cannot happen within the limits above
+    try {
+        batch_create(b);
+    } catch (...) {
+        batch_destroy(b);
+        delete b;
+        throw;
+    }
+    *out = b;
+    QE_API_END
+}
+
+int qe_batch_run(qe_batch* b, double* energies) {
+    QE_API_BEGIN
+    check_batch(b);
+    batch_run(b, energies);
+    QE_API_END
+}
+
+int qe_batch_set_plan(qe_batch* b, int tile_bits, int tiles_per_item, int threads) {
+    QE_API_BEGIN
+    check_batch(b);
+    batch_set_plan(b, tile_bits, tiles_per_item, threads);
+    QE_API_END
+}
+
+int qe_batch_tune(qe_batch* b, int reps, int* tile_bits, int* tiles_per_item, int* threads) {
+    QE_API_BEGIN
+    check_batch(b);
+    if (reps < 1) fail(QE_ERR_ARG, "reps must be >= 1");
+    const int tmax = b->dtype == QE_C64 ? 13 : 12;
+    int nmax = 0;
+    for (int v : b->n) nmax = std::max(nmax, v);
+    float best = 1e30f;
+    int bt = b->plan.T, bp = b->plan.tiles_per_item, bth = b->plan.threads;
+    cudaEvent_t e0, e1;
+    QE_CUDA(cudaEventCreate(&e0));
+    QE_CUDA(cudaEventCreate(&e1));
+    for (int T = tmax - 1; T <= tmax; ++T) {
+        if (2 * T - 1 < nmax) continue;
+        for (int per : {1, 4, 16})
+            for (int th : {256, 512}) {
+                batch_set_plan(b, T, per, th);
+                batch_run(b, nullptr);   // warm-up
+                QE_CUDA(cudaEventRecord(e0, b->stream));
+                for (int r = 0; r < reps; ++r) QE_CUDA(cudaGraphLaunch(b->exec, b->stream));
+                QE_CUDA(cudaEventRecord(e1, b->stream));
+                QE_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                QE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (*b->host_status != 0) fail(QE_ERR_TIMEOUT, "a batch work item timed out while tuning");
+                if (ms < best) { best = ms; bt = T; bp = per; bth = th; }
+            }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    batch_set_plan(b, bt, bp, bth);
+    if (tile_bits) *tile_bits = bt;
+    if (tiles_per_item) *tiles_per_item = bp;
+    if (threads) *threads = bth;
+    QE_API_END
+}
+
+int qe_batch_info(const qe_batch* b, double* hbm_bytes, int* items) {
+    QE_API_BEGIN
+    check_batch(b);
+    if (hbm_bytes) *hbm_bytes = b->hbm_bytes;
+    if (items) *items = b->nitems;
+    QE_API_END
+}
+
+int qe_batch_free(qe_batch* b) {
+    QE_API_BEGIN
+    if (!b) return QE_OK;
+    check_batch(b);
+    cudaStreamSynchronize(b->stream);
+    batch_destroy(b);
+    b->magic = 0;
+    delete b;
+    QE_API_END
+}
+
+static void check_model(const qe_cost_model* m) {
+    if (!m || m->magic != 0xC057) fail(QE_ERR_STATE, "invalid cost model handle");
+}
+
+int qe_cost_model_create(int hidden1, int hidden2, uint64_t seed, qe_cost_model** out) {
+    QE_API_BEGIN
+    if (!out) fail(QE_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (hidden1 < 1 || hidden1 > 256 || hidden2 < 1 || hidden2 > 256) fail(QE_ERR_ARG, "hidden sizes in [1, 256]");
+    auto* m = new qe_cost_model();
+    m->d = kCostFeatures;
+    m->h1 = hidden1;
+    m->h2 = hidden2;
+    try {
+        mlp_create(m, seed);
+    } catch (...) {
+        mlp_destroy(m);
+        delete m;
+        throw;
+    }
+    *out = m;
+    QE_API_END
+}
+
+int qe_cost_model_param_count(const qe_cost_model* m, int* count) {
+    QE_API_BEGIN
+    check_model(m);
+    if (!count) fail(QE_ERR_ARG, "count is NULL");
+    *count = m->np;
+    QE_API_END
+}
+
+int qe_cost_model_get_params(const qe_cost_model* m, float* params, int count) {
+    QE_API_BEGIN
+    check_model(m);
+    if (!params || count != m->np) fail(QE_ERR_ARG, "params must hold exactly the parameter count");
+    QE_CUDA(cudaStreamSynchronize(m->stream));
+    QE_CUDA(cudaMemcpy(params, m->params, sizeof(float) * m->np, cudaMemcpyDeviceToHost));
+    QE_API_END
+}
+
+int qe_cost_model_set_params(qe_cost_model* m, const float* params, int count) {
+    QE_API_BEGIN
+    check_model(m);
+    if (!params || count != m->np) fail(QE_ERR_ARG, "params must hold exactly the parameter count");
+    for (int i = 0; i < count; ++i)
+        if (!std::isfinite(params[i])) fail(QE_ERR_ARG, "non-finite parameter");
+    QE_CUDA(cudaStreamSynchronize(m->stream));
+    QE_CUDA(cudaMemcpy(m->params, params, sizeof(float) * m->np, cudaMemcpyHostToDevice));
+    QE_CUDA(cudaMemset(m->mom1, 0, sizeof(float) * m->np));
+    QE_CUDA(cudaMemset(m->mom2, 0, sizeof(float) * m->np));
+    m->step = 0;
+    QE_API_END
+}
+
+static void check_samples(const float* X, const float* t, int n) {
+    if (n < 1 || !X) fail(QE_ERR_ARG, "need n >= 1 samples");
+    for (long i = 0; i < (long)n * kCostFeatures; ++i)
+        if (!std::isfinite(X[i])) fail(QE_ERR_ARG, "non-finite feature");
+    if (t)
+        for (int i = 0; i < n; ++i)
+            if (!std::isfinite(t[i])) fail(QE_ERR_ARG, "non-finite target");
+}
+
+int qe_cost_model_gradient(qe_cost_model* m, const float* X, const float* t, int n, float* grad,
+                           float* loss) {
+    QE_API_BEGIN
+    check_model(m);
+    check_samples(X, t, n);
+    if (!t || !grad) fail(QE_ERR_ARG, "targets and grad are required");
+    const float l = mlp_gradient(m, X, t, n, grad);
+    if (loss) *loss = l;
+    QE_API_END
+}
+
+int qe_cost_model_train(qe_cost_model* m, const float* X, const float* t, int n, int epochs,
+                        float lr, float* loss) {
+    QE_API_BEGIN
+    check_model(m);
+    check_samples(X, t, n);
+    if (!t || epochs < 0 || !(lr > 0.f)) fail(QE_ERR_ARG, "bad training arguments");
+    const float l = mlp_train(m, X, t, n, epochs, lr);
+    if (loss) *loss = l;
+    QE_API_END
+}
+
+int qe_cost_model_predict(qe_cost_model* m, const float* X, int n, float* y) {
+    QE_API_BEGIN
+    check_model(m);
+    check_samples(X, nullptr, n);
+    if (!y) fail(QE_ERR_ARG, "y is NULL");
+    mlp_predict(m, X, n, y);
+    QE_API_END
+}
+
+int qe_cost_model_free(qe_cost_model* m) {
+    QE_API_BEGIN
+    if (!m) return QE_OK;
+    check_model(m);
+    mlp_destroy(m);
+    m->magic = 0;
+    delete m;
+    QE_API_END
+}
+
+int qe_cost_features(int op, int n, int dtype, int k, int lo, int hi, int m, uint64_t c, float* f) {
+    QE_API_BEGIN
+    if (!f || op < 0 || op > 4 || n < 1 || n > 34) fail(QE_ERR_ARG, "bad feature request");
+    cost_features(op, n, dtype, k, lo, hi, m, c, f);
+    QE_API_END
+}
+
+int qe_set_cost_model(qe_state* s, qe_cost_model* model) {
+    QE_API_BEGIN
+    check_state(s);
+    if (model) check_model(model);
+    flush(s);
+    s->model = model;
+    QE_API_END
+}
+
+int qe_planned_fusion_width(qe_state* s, int* k) {
+    QE_API_BEGIN
+    check_state(s);
+    if (!k) fail(QE_ERR_ARG, "k is NULL");
+    *k = choose_fusion_width(s, s->queue);
     QE_API_END
 }
 

@@ -12,6 +12,7 @@
 // whose controls are set, a single-entry diagonal (e.g. CR(theta),
 // Sec. III-B) one amplitude per group, permutations move bits exactly.
 #include <algorithm>
+#include <vector>
 
 #include "qe_arith.cuh"
 #include "qe_internal.h"
@@ -119,9 +120,10 @@ __global__ void __launch_bounds__(kThreads) k_gate_dense(const __grid_constant__
 #pragma unroll
             for (int j = 0; j < K; ++j) r |= (((uint32_t)i >> a.pos[j]) & 1u) << j;
             const uint32_t b = (uint32_t)i & ~gmask;
-            auto acc = P::zero();
+            typename P::A acc;
+            P::mac_first(acc, Us[r], tile[b]);
 #pragma unroll
-            for (int c = 0; c < D; ++c) P::mac(acc, Us[c * D + r], tile[b | dep[c]]);
+            for (int c = 1; c < D; ++c) P::mac(acc, Us[c * D + r], tile[b | dep[c]]);
             a.x[base + (i & lowmask) + hoff[i >> a.L]] = P::out(acc);
         }
         __syncthreads();
@@ -207,9 +209,10 @@ __global__ void __launch_bounds__(kThreads) k_gate_direct(const __grid_constant_
             if (g0 + j * stride >= a.ngroups) break;
 #pragma unroll
             for (int r = 0; r < D; ++r) {
-                auto acc = P::zero();
+                typename P::A acc;
+                P::mac_first(acc, a.U[r * D], v[j][0]);
 #pragma unroll
-                for (int c = 0; c < D; ++c) P::mac(acc, a.U[r * D + c], v[j][c]);
+                for (int c = 1; c < D; ++c) P::mac(acc, a.U[r * D + c], v[j][c]);
                 a.x[base[j] + a.dep[r]] = P::out(acc);
             }
         }
@@ -233,7 +236,7 @@ void direct_impl(qe_state* s, const int* qubits, const cd* U) {
         a.dep[c] = o;
     }
     for (int i = 0; i < D * D; ++i) a.U[i] = to_m<P>(U[i]);
-    constexpr int G = (K <= 2) ? 2 : 1;
+    constexpr int G = (K <= 2 && sizeof(typename P::V) < 16) ? 2 : 1;
     auto fn = k_gate_direct<P, K, G>;
     unsigned grid = persistent_grid((const void*)fn, kThreads, 0, (a.ngroups + kThreads * G - 1) / (kThreads * G));
     static const char* names[] = {"", "gate_direct_k1", "gate_direct_k2", "gate_direct_k3"};
@@ -258,8 +261,8 @@ __global__ void __launch_bounds__(kThreads) k_gate_diag(const __grid_constant__ 
          i += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t r = 0;
         for (int j = 0; j < a.k; ++j) r |= (uint32_t)((i >> a.q[j]) & 1u) << j;
-        auto acc = P::zero();
-        P::mac(acc, a.d[r], P::load(a.x[i]));
+        typename P::A acc;
+        P::mac_first(acc, a.d[r], P::load(a.x[i]));
         a.x[i] = P::out(acc);
     }
 }
@@ -289,8 +292,9 @@ __global__ void __launch_bounds__(kThreads) k_controlled(const __grid_constant__
         typename P::V v[4];
         for (int c = 0; c < D; ++c) v[c] = P::load(a.x[base + a.tdep[c]]);
         for (int r = 0; r < D; ++r) {
-            auto acc = P::zero();
-            for (int c = 0; c < D; ++c) P::mac(acc, a.U[r * D + c], v[c]);
+            typename P::A acc;
+            P::mac_first(acc, a.U[r * D], v[0]);
+            for (int c = 1; c < D; ++c) P::mac(acc, a.U[r * D + c], v[c]);
             a.x[base + a.tdep[r]] = P::out(acc);
         }
     }
@@ -388,6 +392,22 @@ void diag_impl(qe_state* s, int k, const int* qubits, const cd* d) {
     } while (0)
 
 void launch_gate_dense(qe_state* s, int k, const int* qubits, const cd* U) {
+    if (s->dtype == QE_C64 && s->tensor_cores && !s->force_tile && s->n >= 12 && k >= 4) {
+        if (k == 5) {
+            launch_gate_tc5(s, qubits, U);
+            return;
+        }
+        // widen a 4-qubit block by one idle qubit: U5 = 1_2 (x) U4 (new bit 4)
+        int q5[5] = {qubits[0], qubits[1], qubits[2], qubits[3], 0};
+        for (int c = 0; c < s->n; ++c)
+            if (c != q5[0] && c != q5[1] && c != q5[2] && c != q5[3]) { q5[4] = c; break; }
+        std::vector<cd> U5(32 * 32, cd(0.0));
+        for (int hb = 0; hb < 2; ++hb)
+            for (int r = 0; r < 16; ++r)
+                for (int c = 0; c < 16; ++c) U5[(r | (hb << 4)) * 32 + (c | (hb << 4))] = U[r * 16 + c];
+        launch_gate_tc5(s, q5, U5.data());
+        return;
+    }
     QE_DISPATCH(s, dense_k, s, k, qubits, U);
 }
 

@@ -6,8 +6,10 @@
 // speedup is n * FLOPS_achieved / B_mem (Sec. IV-C).  On one GPU the network
 // terms drop out.  The constants below are this device's measured copy
 // bandwidth and the FP32-pipe throughput that the FFT butterflies use.
+#include <algorithm>
 #include <cmath>
 
+#include "qe_mlp.h"
 #include "qe_plan.h"
 
 namespace qe {
@@ -53,17 +55,31 @@ double analytic_add_emulate(const qe_state* s, int m) {
     return 2.0 * N * B / kBandwidth;
 }
 
+// Learned choice: predicted log-times of the two paths.
+static bool model_prefers_first(qe_state* s, int op_a, int op_b, int lo, int hi, int m, uint64_t c) {
+    float X[2 * kCostFeatures], y[2];
+    cost_features(op_a, s->n, s->dtype, 0, lo, hi, m, c, X);
+    cost_features(op_b, s->n, s->dtype, 0, lo, hi, m, c, X + kCostFeatures);
+    mlp_predict(s->model, X, 2, y);
+    return y[0] <= y[1];
+}
+
 bool choose_emulate_qft(qe_state* s, int lo, int m) {
-    (void)lo;
     if (s->policy == QE_POLICY_EMULATE) return true;
     if (s->policy == QE_POLICY_SIMULATE) return false;
+    if (s->policy == QE_POLICY_AUTO && s->model)
+        return model_prefers_first(s, kOpQftEmulate, kOpQftSimulate, lo, lo + m - 1, m, 0);
     return analytic_qft_emulate(s, m) <= analytic_qft_simulate(s, m);
 }
 
 bool choose_emulate_add(qe_state* s, int m, const int* qubits, uint64_t c) {
-    (void)qubits;
     if (s->policy == QE_POLICY_EMULATE) return true;
     if (s->policy == QE_POLICY_SIMULATE) return false;
+    if (s->policy == QE_POLICY_AUTO && s->model) {
+        int lo = qubits[0], hi = qubits[0];
+        for (int j = 1; j < m; ++j) { lo = std::min(lo, qubits[j]); hi = std::max(hi, qubits[j]); }
+        return model_prefers_first(s, kOpAddEmulate, kOpAddSimulate, lo, hi, m, c);
+    }
     return analytic_add_emulate(s, m) <= analytic_add_simulate(s, m, c);
 }
 

@@ -114,6 +114,7 @@ __device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df{-b.h, -b.
 //   A        accumulator of a complex dot product
 //   load(S) -> V, store(V) -> S, mat(re, im) -> M on the host,
 //   from_d(re, im) -> M on the device, zero() -> A, mac(A&, M, V),
+//   mac_first(A&, M, V) (the first term of a dot product, A uninitialised),
 //   out(A) -> S, add/sub(V, V) -> V, cmul(M, V) -> V.
 struct F32 {
     using S = float2;
@@ -135,6 +136,10 @@ struct F32 {
         a.re = __fmaf_rn(-u.y, v.y, a.re);
         a.im = __fmaf_rn(u.x, v.y, a.im);
         a.im = __fmaf_rn(u.y, v.x, a.im);
+    }
+    __device__ __forceinline__ static void mac_first(A& a, M u, V v) {
+        a.re = __fmaf_rn(-u.y, v.y, fmul(u.x, v.x));
+        a.im = __fmaf_rn(u.y, v.x, fmul(u.x, v.y));
     }
     __device__ __forceinline__ static S out(const A& a) { return make_float2(a.re, a.im); }
     __device__ __forceinline__ static V add(V a, V b) { return make_float2(fadd(a.x, b.x), fadd(a.y, b.y)); }
@@ -160,6 +165,10 @@ struct F64 {
         a.re = __fma_rn(-u.y, v.y, a.re);
         a.im = __fma_rn(u.x, v.y, a.im);
         a.im = __fma_rn(u.y, v.x, a.im);
+    }
+    __device__ __forceinline__ static void mac_first(A& a, M u, V v) {
+        a.re = __fma_rn(-u.y, v.y, __dmul_rn(u.x, v.x));
+        a.im = __fma_rn(u.y, v.x, __dmul_rn(u.x, v.y));
     }
     __device__ __forceinline__ static S out(const A& a) { return make_double2(a.re, a.im); }
     __device__ __forceinline__ static V add(V a, V b) { return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)); }
@@ -191,9 +200,17 @@ struct DF {
         df_acc(a.is, a.ie, u.re, v.im);
         df_acc(a.is, a.ie, u.im, v.re);
     }
+    // first product of a dot product: no addition, so no TwoSum
+    __device__ __forceinline__ static void mac_first(A& a, const M& u, const V& v) {
+        df_first(a.rs, a.re_, u.re, v.re);
+        df_acc_neg(a.rs, a.re_, u.im, v.im);
+        df_first(a.is, a.ie, u.re, v.im);
+        df_acc(a.is, a.ie, u.im, v.re);
+    }
+    // (s, e) need no normalisation: one FP64 addition of the exactly
+    // widened parts rounds s + e correctly
     __device__ __forceinline__ static S out(const A& a) {
-        df r = df_norm(a.rs, a.re_), i = df_norm(a.is, a.ie);
-        return make_double2(df2d(r.h, r.l), df2d(i.h, i.l));
+        return make_double2(df2d(a.rs, a.re_), df2d(a.is, a.ie));
     }
     __device__ __forceinline__ static V add(const V& a, const V& b) { return V{df_add(a.re, b.re), df_add(a.im, b.im)}; }
     __device__ __forceinline__ static V sub(const V& a, const V& b) { return V{df_sub(a.re, b.re), df_sub(a.im, b.im)}; }

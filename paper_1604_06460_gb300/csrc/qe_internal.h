@@ -54,6 +54,8 @@ struct qe_state {
     int max_k = 4;
     int c128_native = 0;          // 1: native FP64 arithmetic for complex128
     int force_tile = 0;           // 1: dense gates always through shared-memory tiles
+    int tensor_cores = 1;         // complex64 blocks of 4-5 qubits on tcgen05 (n >= 12)
+    qe_cost_model* model = nullptr;   // learned cost model (borrowed), used by QE_POLICY_AUTO
     std::vector<qe::PendingGate> queue;
     // device scratch for reductions, grown on demand
     void* scratch = nullptr;
@@ -94,6 +96,8 @@ void launch_scale(qe_state* s, double factor);
 
 // dense k-qubit gate (1 <= k <= 5) through shared-memory tiles
 void launch_gate_dense(qe_state* s, int k, const int* qubits, const cd* U);
+// 5-qubit block on a complex64 state with tcgen05 tensor cores (n >= 12)
+void launch_gate_tc5(qe_state* s, const int* qubits, const cd* U);
 // diagonal gate: amplitude x *= d[row(x)] for all x
 void launch_gate_diag(qe_state* s, int k, const int* qubits, const cd* d);
 // amplitudes with (x & mask) == value are multiplied by phase
@@ -110,6 +114,16 @@ void launch_bitrev(qe_state* s, int lo, int m);
 
 // register + c mod 2^m, register bit j <-> qubits[j]
 void launch_add_const(qe_state* s, int m, const int* qubits, uint64_t c);
+
+// batch of ansatz circuits (struct qe_batch is defined in batch.cu)
+void batch_create(qe_batch* b);
+void batch_run(qe_batch* b, double* energies);
+void batch_set_plan(qe_batch* b, int T, int tiles_per_item, int threads);
+void batch_destroy(qe_batch* b);
+
+// planner
+void flush(qe_state* s);
+int choose_fusion_width(qe_state* s, const std::vector<PendingGate>& queue);
 
 // reductions (synchronise the stream)
 double reduce_norm2(qe_state* s);

@@ -60,6 +60,23 @@ SIGNATURES = {
     "qe_profile_enable": (_i, [_vp, _i]),
     "qe_profile_read": (_i, [_vp, C.POINTER(KernelProfile), _i, C.POINTER(_i)]),
     "qe_probs_noalloc": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp]),
+    "qe_batch_create": (_i, [_i, _vp, _i, _vp, C.c_double, _i, _vp, C.POINTER(_vp)]),
+    "qe_batch_run": (_i, [_vp, _vp]),
+    "qe_batch_tune": (_i, [_vp, _i, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)]),
+    "qe_batch_set_plan": (_i, [_vp, _i, _i, _i]),
+    "qe_batch_info": (_i, [_vp, C.POINTER(C.c_double), C.POINTER(_i)]),
+    "qe_batch_free": (_i, [_vp]),
+    "qe_cost_model_create": (_i, [_i, _i, _u64, C.POINTER(_vp)]),
+    "qe_cost_model_param_count": (_i, [_vp, C.POINTER(_i)]),
+    "qe_cost_model_get_params": (_i, [_vp, _vp, _i]),
+    "qe_cost_model_set_params": (_i, [_vp, _vp, _i]),
+    "qe_cost_model_gradient": (_i, [_vp, _vp, _vp, _i, _vp, C.POINTER(C.c_float)]),
+    "qe_cost_model_train": (_i, [_vp, _vp, _vp, _i, _i, C.c_float, C.POINTER(C.c_float)]),
+    "qe_cost_model_predict": (_i, [_vp, _vp, _i, _vp]),
+    "qe_cost_model_free": (_i, [_vp]),
+    "qe_cost_features": (_i, [_i, _i, _i, _i, _i, _i, _i, _u64, _vp]),
+    "qe_set_cost_model": (_i, [_vp, _vp]),
+    "qe_planned_fusion_width": (_i, [_vp, C.POINTER(_i)]),
     "qe_last_error": (C.c_char_p, []),
 }
 
@@ -235,6 +252,16 @@ class State:
             max_k = 2 if self._dt == C128 else 4
         _check(load().qe_set_policy(self._h, int(policy), int(max_k)))
 
+    def set_cost_model(self, model):
+        """Attach a CostModel (or None): QE_POLICY_AUTO then lets it choose."""
+        _check(load().qe_set_cost_model(self._h, model._h if model is not None else None))
+        self._model = model
+
+    def planned_fusion_width(self):
+        k = C.c_int()
+        _check(load().qe_planned_fusion_width(self._h, C.byref(k)))
+        return k.value
+
     def stats(self):
         st = Stats()
         _check(load().qe_get_stats(self._h, C.byref(st)))
@@ -253,3 +280,135 @@ class State:
         _check(load().qe_profile_read(self._h, buf, 64, C.byref(cnt)))
         return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms, buf[i].bytes)
                 for i in range(min(cnt.value, 64))}
+
+
+class Batch:
+    """Many hardware-efficient-ansatz circuits run by one persistent kernel
+    replayed as a CUDA graph; ``run()`` returns each circuit's TFIM energy.
+
+    ``nqubits``: qubit count per circuit; ``angles``: per circuit an array of
+    shape (layers, n, 2) holding (theta_RY, phi_RZ); ``hx``: transverse field.
+    """
+
+    def __init__(self, nqubits, angles, hx=0.7, dtype="c128", stream=None):
+        import torch
+
+        lib = load()
+        nq = np.ascontiguousarray(np.asarray(nqubits, dtype=np.int32))
+        layers = {int(np.asarray(a).shape[0]) for a in angles}
+        if len(layers) != 1:
+            raise ValueError("all circuits need the same number of layers")
+        self.layers = layers.pop()
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(a, dtype=np.float64).reshape(-1)
+                                                    for a in angles]))
+        self.count = nq.size
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(lib.qe_batch_create(nq.size, _ptr(nq), self.layers, _ptr(flat), float(hx),
+                                   C128 if dtype == "c128" else C64,
+                                   C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self._h = h
+
+    def run(self):
+        out = np.empty(self.count, dtype=np.float64)
+        _check(load().qe_batch_run(self._h, _ptr(out)))
+        return out
+
+    def tune(self, reps=2):
+        t, p, th = C.c_int(), C.c_int(), C.c_int()
+        _check(load().qe_batch_tune(self._h, int(reps), C.byref(t), C.byref(p), C.byref(th)))
+        return {"tile_bits": t.value, "tiles_per_item": p.value, "threads": th.value}
+
+    def set_plan(self, tile_bits, tiles_per_item, threads):
+        _check(load().qe_batch_set_plan(self._h, int(tile_bits), int(tiles_per_item), int(threads)))
+
+    def info(self):
+        b, i = C.c_double(), C.c_int()
+        _check(load().qe_batch_info(self._h, C.byref(b), C.byref(i)))
+        return {"hbm_bytes": b.value, "items": i.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(load().qe_batch_free(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+OP_GATE, OP_QFT_EMULATE, OP_QFT_SIMULATE, OP_ADD_EMULATE, OP_ADD_SIMULATE = range(5)
+N_FEATURES = 16
+
+
+def cost_features(op, n, dtype, k=0, lo=0, hi=0, m=0, c=0):
+    f = np.empty(N_FEATURES, dtype=np.float32)
+    _check(load().qe_cost_features(int(op), int(n), C128 if dtype == "c128" else C64, int(k),
+                                   int(lo), int(hi), int(m), int(c) & ((1 << 64) - 1), _ptr(f)))
+    return f
+
+
+class CostModel:
+    """The learned cost model (log-milliseconds from 16 features), trained and
+    evaluated by the library's own GPU kernels."""
+
+    def __init__(self, hidden1=32, hidden2=32, seed=0):
+        h = C.c_void_p()
+        _check(load().qe_cost_model_create(int(hidden1), int(hidden2), int(seed), C.byref(h)))
+        self._h = h
+        self.hidden = (hidden1, hidden2)
+
+    def param_count(self):
+        c = C.c_int()
+        _check(load().qe_cost_model_param_count(self._h, C.byref(c)))
+        return c.value
+
+    def params(self):
+        p = np.empty(self.param_count(), dtype=np.float32)
+        _check(load().qe_cost_model_get_params(self._h, _ptr(p), p.size))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(np.asarray(p, dtype=np.float32))
+        _check(load().qe_cost_model_set_params(self._h, _ptr(p), p.size))
+
+    def gradient(self, X, t):
+        X = np.ascontiguousarray(np.asarray(X, dtype=np.float32))
+        t = np.ascontiguousarray(np.asarray(t, dtype=np.float32))
+        g = np.empty(self.param_count(), dtype=np.float32)
+        loss = C.c_float()
+        _check(load().qe_cost_model_gradient(self._h, _ptr(X), _ptr(t), t.size, _ptr(g), C.byref(loss)))
+        return loss.value, g
+
+    def train(self, X, t, epochs=2000, lr=3e-3):
+        X = np.ascontiguousarray(np.asarray(X, dtype=np.float32))
+        t = np.ascontiguousarray(np.asarray(t, dtype=np.float32))
+        loss = C.c_float()
+        _check(load().qe_cost_model_train(self._h, _ptr(X), _ptr(t), t.size, int(epochs), float(lr),
+                                          C.byref(loss)))
+        return loss.value
+
+    def predict(self, X):
+        X = np.ascontiguousarray(np.asarray(X, dtype=np.float32))
+        y = np.empty(X.shape[0], dtype=np.float32)
+        _check(load().qe_cost_model_predict(self._h, _ptr(X), X.shape[0], _ptr(y)))
+        return y
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(load().qe_cost_model_free(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

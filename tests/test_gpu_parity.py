@@ -394,3 +394,36 @@ def test_invalid_arguments_leave_state_untouched(qe):
                 bad()
             assert ei.value.status == -1
         assert np.array_equal(st.get(), psi)
+
+
+# ------------------------------------------- tensor cores (complex64, k = 4, 5)
+@pytest.mark.parametrize("qubits", [[0, 1, 2, 3, 4], [10, 11, 12, 13, 14], [4, 0, 15, 7, 12],
+                                    [2, 9, 5, 14], [15, 14, 13, 12]])
+def test_tensor_core_blocks_c64(qe, qubits):
+    # 3xTF32 products accumulated in FP32: about FP32 accuracy
+    n = 16
+    U = rand_unitary(1 << len(qubits), np.random.default_rng(sum(qubits)))
+    psi = I.random_state(n, 12).astype(np.complex64)
+    with make(qe, n, "c64", psi=psi, max_k=5) as st:
+        st.reset_stats()
+        st.apply_gate(qubits, U)
+        got = st.get().astype(np.complex128)
+        launches = st.stats()["launches"]
+    ref = oracle.apply_gate(psi.astype(np.complex128), qubits, U)
+    assert launches == 1
+    assert np.max(np.abs(got - ref)) < 2e-6
+    assert oracle.fidelity(ref, got) > 1 - 1e-10
+
+
+def test_tensor_core_fused_circuit_c64(qe):
+    n = 14
+    gates = I.random_circuit(n, 8, seed=21)
+    ref = oracle.zero_state(n)
+    for g in gates:
+        ref = oracle.apply_gate(ref, g.qubits, g.matrix)
+    with make(qe, n, "c64", max_k=5) as st:
+        for g in gates:
+            st.apply(g)
+        got = st.get().astype(np.complex128)
+    assert np.max(np.abs(got - ref)) < 2e-5
+    assert oracle.fidelity(ref, got) > 1 - 1e-8

@@ -368,3 +368,35 @@ def test_gaussian_state_normalised_and_slices():
     big = oracle.gaussian_slice(99, 1 << 40, 1 << 16)
     assert abs(np.mean(big.real ** 2) - 1) < 0.03 and abs(np.mean(big.imag ** 2) - 1) < 0.03
     assert abs(np.mean(big.real)) < 0.02 and abs(np.mean(big.imag)) < 0.02
+
+
+# --- the cost model's network: pinned by finite differences -------------------
+def test_mlp_gradient_matches_finite_differences():
+    rng = np.random.default_rng(3)
+    d, h1, h2, n = 5, 7, 4, 9
+    npar = oracle.mlp_param_count(d, h1, h2)
+    assert npar == h1 * d + h1 + h2 * h1 + h2 + h2 + 1
+    p = rng.standard_normal(npar) * 0.5
+    X = rng.standard_normal((n, d))
+    t = rng.standard_normal(n)
+    loss, g = oracle.mlp_grad(p, X, t, h1, h2)
+    y = oracle.mlp_forward(p, X, h1, h2)
+    assert abs(loss - np.mean((y - t) ** 2)) < 1e-14
+    eps = 1e-6
+    fd = np.empty(npar)
+    for k in range(npar):
+        pp, pm = p.copy(), p.copy()
+        pp[k] += eps
+        pm[k] -= eps
+        fd[k] = (np.mean((oracle.mlp_forward(pp, X, h1, h2) - t) ** 2)
+                 - np.mean((oracle.mlp_forward(pm, X, h1, h2) - t) ** 2)) / (2 * eps)
+    assert np.max(np.abs(fd - g)) < 1e-8
+
+
+def test_mlp_forward_closed_form():
+    # one hidden unit per layer, identity-like weights: y = w3 tanh(w2 tanh(w1 x + b1) + b2) + b3
+    d, h1, h2 = 1, 1, 1
+    p = np.array([0.3, -0.2, 1.5, 0.1, -2.0, 0.25])
+    x = np.array([[0.7]])
+    want = -2.0 * np.tanh(1.5 * np.tanh(0.3 * 0.7 - 0.2) + 0.1) + 0.25
+    assert abs(oracle.mlp_forward(p, x, h1, h2)[0] - want) < 1e-15
