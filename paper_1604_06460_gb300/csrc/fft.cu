@@ -25,7 +25,7 @@ namespace qe {
 
 namespace {
 
-constexpr int kFftThreads = 512;
+constexpr int kFftThreads = 256;
 
 template <class P>
 __global__ void k_twiddles(typename P::M* fine, typename P::M* coarse, int m, int h, int sign) {
@@ -66,6 +66,45 @@ __device__ __forceinline__ typename P::M root(const FftArgs<P>& a, uint64_t e) {
     return P::cmul(a.coarse[e >> a.h], a.fine[e & ((1ull << a.h) - 1ull)]);
 }
 
+// G radix-2 DIF stages s_hi, s_hi-1, ..., s_hi-G+1 of the tile's groups, in
+// registers.  Element j (G bits) of a thread's set sits at local index
+// base | (j << (P0 + s_lo)); its in-group index is gp = (local >> P0) & (R-1)
+// and stage s multiplies the difference by roots[2^s - 1 + (gp mod 2^s)].
+template <class P, int G>
+__device__ __forceinline__ void stage_group(typename P::V* tile, const typename P::M* roots, int Tn, int P0,
+                                            int s_hi) {
+    using V = typename P::V;
+    constexpr int E = 1 << G;
+    const int s_lo = s_hi - G + 1;
+    const int sh = P0 + s_lo;
+    const uint32_t below = (1u << sh) - 1u;
+    const int nbase = Tn >> G;
+    for (int b = threadIdx.x; b < nbase; b += blockDim.x) {
+        const uint32_t base = (((uint32_t)b & ~below) << G) | ((uint32_t)b & below);
+        V v[E];
+#pragma unroll
+        for (int j = 0; j < E; ++j) v[j] = tile[base | ((uint32_t)j << sh)];
+        const uint32_t gp0 = base >> P0;   // the thread's fixed in-group bits (group bits zero)
+#pragma unroll
+        for (int t = G - 1; t >= 0; --t) {
+            const int s = s_lo + t;
+            const uint32_t smask = (1u << s) - 1u;
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                if (j & (1 << t)) continue;
+                const int j2 = j | (1 << t);
+                const uint32_t p = (gp0 | ((uint32_t)j << s_lo)) & smask;
+                const typename P::M w = roots[(1u << s) - 1u + p];
+                const V u = v[j], x = v[j2];
+                v[j] = P::add(u, x);
+                v[j2] = P::cmul(w, P::sub(u, x));
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < E; ++j) tile[base | ((uint32_t)j << sh)] = v[j];
+    }
+}
+
 template <class P>
 __global__ void __launch_bounds__(kFftThreads) k_fft_pass(const __grid_constant__ FftArgs<P> a) {
     using V = typename P::V;
@@ -104,17 +143,16 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pass(const __grid_constant_
             tile[i] = P::load(a.x[base + (i & lowmask) + offA[hi & 63] + offB[hi >> 6]]);
         }
         __syncthreads();
-        for (int s = a.r - 1; s >= 0; --s) {
-            const int bitpos = a.P0 + s;
-            const uint32_t below = (1u << bitpos) - 1u;
-            for (int beta = tid; beta < Tn / 2; beta += nth) {
-                const uint32_t u = (((uint32_t)beta & ~below) << 1) | ((uint32_t)beta & below);
-                const uint32_t v = u | (1u << bitpos);
-                const uint32_t p = (u >> a.P0) & ((1u << s) - 1u);
-                const M w = roots[(1 << s) - 1 + p];
-                const V U = tile[u], W = tile[v];
-                tile[u] = P::add(U, W);
-                tile[v] = P::cmul(w, P::sub(U, W));
+        // radix-2 DIF stages from the top pass bit down, up to four at a time in
+        // registers: a thread owns the 2^g elements that differ in the g bits
+        // of the group, so each group costs one shared-memory round trip
+        for (int s_hi = a.r - 1; s_hi >= 0; s_hi -= 4) {
+            const int g = s_hi + 1 < 4 ? s_hi + 1 : 4;
+            switch (g) {
+                case 4: stage_group<P, 4>(tile, roots, Tn, a.P0, s_hi); break;
+                case 3: stage_group<P, 3>(tile, roots, Tn, a.P0, s_hi); break;
+                case 2: stage_group<P, 2>(tile, roots, Tn, a.P0, s_hi); break;
+                default: stage_group<P, 1>(tile, roots, Tn, a.P0, s_hi); break;
             }
             __syncthreads();
         }

@@ -169,12 +169,27 @@ __global__ void __launch_bounds__(kTcThreads) k_gate_tc5(const __grid_constant__
         s_col[l] = (uint8_t)c;
     }
     __syncthreads();
+    // each thread moves 16 amplitudes of a tile: l = tid + 256 * i
+    constexpr int kPer = 4096 / kTcThreads;
+    float2 cur[kPer], nxt[kPer];
+    auto load_tile = [&](uint64_t t, float2* dst) {
+        const uint64_t gb = insert_zero_bits(t << a.L, a.hq, a.kh);
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const uint32_t l = (uint32_t)tid + (uint32_t)kTcThreads * i;
+            dst[i] = a.x[gb + (l & lowmask) + hoff[l >> a.L]];
+        }
+    };
     uint32_t phase = 0;
-    for (uint64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+    uint64_t t = blockIdx.x;
+    if (t < a.ntiles) load_tile(t, cur);
+    for (; t < a.ntiles; t += gridDim.x) {
         const uint64_t gbase = insert_zero_bits(t << a.L, a.hq, a.kh);
-        // 1. load, split into TF32 hi/lo, store swizzled
-        for (uint32_t l = tid; l < 4096u; l += blockDim.x) {
-            const float2 v = a.x[gbase + (l & lowmask) + hoff[l >> a.L]];
+        // 1. split into TF32 hi/lo and store the operand, swizzled
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const uint32_t l = (uint32_t)tid + (uint32_t)kTcThreads * i;
+            const float2 v = cur[i];
             const int r = s_row[l], c = s_col[l];
             const float rh = tf32_hi(v.x), ih = tf32_hi(v.y);
             *reinterpret_cast<float*>(sA_hi + sw128_offset(r, c, kRows)) = rh;
@@ -201,6 +216,9 @@ __global__ void __launch_bounds__(kTcThreads) k_gate_tc5(const __grid_constant__
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_u32(&mbar)));
         }
+        // prefetch the next tile while the tensor cores work
+        const uint64_t tn = t + gridDim.x;
+        if (tn < a.ntiles) load_tile(tn, nxt);
         // 3. wait for the accumulator (bounded), read it, stage and store
         if (!mbar_wait(smem_u32(&mbar), phase, a.spin_limit)) {
             atomicExch(a.status, 1u);
@@ -228,7 +246,8 @@ __global__ void __launch_bounds__(kTcThreads) k_gate_tc5(const __grid_constant__
             asm volatile("tcgen05.wait::ld.sync.aligned;");
         }
         // row r = TMEM lane; output element c of row r sits at the tile-local
-        // index with row bits r and gate bits c
+        // index with row bits r and gate bits c; the staging buffer pads one
+        // element per 32 so that a warp's 32 rows hit different banks
         {
             const uint32_t r = (uint32_t)(warp & 3) * 32u + (uint32_t)lane;
             uint32_t lrow = 0;
@@ -238,12 +257,21 @@ __global__ void __launch_bounds__(kTcThreads) k_gate_tc5(const __grid_constant__
             float* st = reinterpret_cast<float*>(stage);
             const int comp = (warp < 4) ? 0 : 1;
 #pragma unroll
-            for (int c = 0; c < 32; ++c) st[2 * (lrow | cpos[c]) + comp] = __uint_as_float(v[c]);
+            for (int c = 0; c < 32; ++c) {
+                const uint32_t l = lrow | cpos[c];
+                st[2 * (l + (l >> 5)) + comp] = __uint_as_float(v[c]);
+            }
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
-        for (uint32_t l = tid; l < 4096u; l += blockDim.x) a.x[gbase + (l & lowmask) + hoff[l >> a.L]] = stage[l];
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const uint32_t l = (uint32_t)tid + (uint32_t)kTcThreads * i;
+            a.x[gbase + (l & lowmask) + hoff[l >> a.L]] = stage[l + (l >> 5)];
+        }
         __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) cur[i] = nxt[i];
     }
     // free tensor memory (all MMAs of this CTA have completed or timed out)
     asm volatile("tcgen05.fence::before_thread_sync;");

@@ -59,10 +59,10 @@ def test_learned_fusion_width_beats_analytic_rule(qe):
     is slow; a model trained on the emulator's own timings picks a narrower
     width.  Both produce the same state."""
     from paper_1604_06460_gb300 import costmodel
-    X, y = costmodel.sweep_gate_passes([20, 21, 22], dtypes=("c128",), seed=0)
+    X, y = costmodel.sweep_gate_passes([22, 23, 24], dtypes=("c128",), seed=0)
     model, loss = costmodel.train(X, y, epochs=3000, lr=3e-3, seed=0)
     assert loss < 0.05
-    n = 22
+    n = 24
     gates = I.random_circuit(n, 6, seed=2)
     import torch
     times, states = {}, {}
