@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--depth", type=int, default=20)
     ap.add_argument("--max-k", type=int, default=0, help="fusion width (0: planner default)")
     ap.add_argument("--quick", action="store_true", help="skip e2e, CPU baseline and the comparison")
+    ap.add_argument("--only", default="", choices=["", "batch", "tensor_cores", "config4", "qft"],
+                    help="run one secondary configuration alone (sizes from --n) and print its JSON")
+    ap.add_argument("--dtype", default="c128", choices=["c128", "c64"], help="state type for --only qft")
     return ap.parse_args()
 
 
@@ -186,12 +189,44 @@ def source_hash():
     return hs.hexdigest()[:16]
 
 
+def aggregate_over_ranks(ms, nbytes, world):
+    """Replicas: the slowest rank's time and the bytes of all ranks (the
+    only collective is this bookkeeping, none on the data path)."""
+    if world <= 1:
+        return ms, nbytes
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    b = torch.tensor([nbytes], dtype=torch.float64, device=dev)
+    dist.all_reduce(b)
+    return float(t.item()), float(b.item())
+
+
 # ------------------------------------------------------------------- ours
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     import torch
+    if args.only:
+        torch.cuda.set_device(0)
+        from paper_1604_06460_gb300 import build as B
+        from paper_1604_06460_gb300 import inputs as I
+        from paper_1604_06460_gb300 import qe
+        B.build()
+        qe.load()
+        if args.only == "batch":
+            res = bench_batch(qe, I)
+        elif args.only == "qft":
+            res = bench_qft(qe, args.n, args.dtype)
+        elif args.only == "tensor_cores":
+            res = bench_tensor_cores(qe, I, n=args.n, n_err=min(args.n, 24))
+        else:
+            res = bench_config4(qe, I, n=args.n)
+        print(json.dumps({"only": args.only, "n": args.n, **res}), flush=True)
+        return 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -251,15 +286,7 @@ def main():
     stats = st.stats()
     prof = st.profile_read()
     st.profile(False)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        b = torch.tensor([stats["algorithmic_bytes"]], device="cuda", dtype=torch.float64)
-        dist.all_reduce(b)
-        total_bytes = float(b.item())
-    else:
-        total_bytes = stats["algorithmic_bytes"]
+    ms, total_bytes = aggregate_over_ranks(ms, stats["algorithmic_bytes"], world)
     value = total_bytes / (ms * 1e-3) / 1e9
 
     # dominant kernel: the largest share of event time among full passes
@@ -300,8 +327,8 @@ def main():
     st.close()
     if rank == 0 and not args.quick:
         torch.cuda.empty_cache()
-        for key, fn in (("batch_config3", bench_batch), ("tensor_core_config2", bench_tensor_cores),
-                        ("config4_and_cost_model", bench_config4)):
+        for key, fn in (("config0_gate_by_gate", bench_config0), ("batch_config3", bench_batch),
+                        ("tensor_core_config2", bench_tensor_cores), ("config4_and_cost_model", bench_config4)):
             try:
                 line[key] = fn(qe, I)
             except Exception as exc:   # report, keep the headline line
@@ -384,6 +411,60 @@ def compare(st, qe, n, reg, cconst):
 def _events():
     import torch
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def bench_qft(qe, n, dtype, reps=3):
+    """Emulated QFT on all n qubits of a random normalised state."""
+    with qe.State(n, dtype) as st:
+        st.set_policy(qe.POLICY_EMULATE, 1)
+        st.init_random(5)
+        st.apply_qft(0, n)
+        ts = []
+        for _ in range(reps):
+            e0, e1 = _events()
+            e0.record(st.stream)
+            st.apply_qft(0, n)
+            e1.record(st.stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        st.reset_stats()
+        st.apply_qft(0, n)
+        stats = st.stats()
+    ms = float(np.median(ts))
+    return {"dtype": dtype, "emulated_ms": ms, "passes": stats["passes"],
+            "GB_per_s": stats["algorithmic_bytes"] / ms / 1e6}
+
+
+def bench_config0(qe, I, n=20, layers=10, seed=0):
+    """n=20 complex128 from |0..0>, 10 layers of (20 Haar U(2) + 10 CNOT),
+    gate by gate without fusion (L2-resident: launch-bound, not HBM-bound);
+    gates/s, time to solution and the error against the oracle."""
+    import torch
+    import oracle
+    gates = I.random_circuit(n, layers, seed)
+    with qe.State(n, "c128") as st:
+        st.set_policy(qe.POLICY_AUTO, 1)
+        for g in gates:
+            st.apply(g)
+        st.flush()
+        ts = []
+        for _ in range(5):
+            st.init_basis(0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for g in gates:
+                st.apply(g)
+            st.sync()
+            ts.append(time.perf_counter() - t0)
+        got = st.get()
+    ref = oracle.zero_state(n)
+    for g in gates:
+        ref = oracle.apply_gate(ref, g.qubits, g.matrix)
+    dt = float(np.median(ts))
+    return {"n": n, "gates": len(gates), "time_to_solution_ms": dt * 1e3, "gates_per_s": len(gates) / dt,
+            "max_abs_vs_oracle": float(np.max(np.abs(got - ref))),
+            "fidelity_vs_oracle": float(abs(np.vdot(ref, got)) ** 2 / (np.vdot(ref, ref).real * np.vdot(got, got).real)),
+            "note": "host-timed through the public API (enqueue + kernels + sync); 32 MB state is L2-resident"}
 
 
 def bench_batch(qe, I, count=4096, layers=8, seed=3):

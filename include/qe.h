@@ -175,7 +175,7 @@ int qe_reset_stats(qe_state* s);
  * one CTA's shared memory, builds the work queue and captures the graph.
  * qe_batch_run replays it and writes count energies to host memory.
  * qe_batch_tune times the candidate tile schedules (tile bits, tiles per work
- * item, threads per CTA) reps times each and keeps the fastest; the chosen
+ * item, threads per CTA: 128 or 256) reps times each and keeps the fastest; the chosen
  * plan is returned through the optional pointers.  qe_batch_info reports
  * the algorithmic HBM bytes of one run and the number of work items. */
 typedef struct qe_batch qe_batch;

@@ -747,7 +747,7 @@ int qe_batch_tune(qe_batch* b, int reps, int* tile_bits, int* tiles_per_item, in
     for (int T = tmax - 1; T <= tmax; ++T) {
         if (2 * T - 1 < nmax) continue;
         for (int per : {1, 4, 16})
-            for (int th : {256, 512}) {
+            for (int th : {128, 256, 512}) {
                 batch_set_plan(b, T, per, th);
                 batch_run(b, nullptr);   // warm-up
                 QE_CUDA(cudaEventRecord(e0, b->stream));

@@ -68,6 +68,7 @@ struct BatchArgs {
     double2* partials;     // (zz sum, x sum) per energy slot
     double* energies;
     long long spin_limit;
+    int gmax;              // single-qubit gates per register group
 };
 
 template <class P>
@@ -137,24 +138,66 @@ __device__ __forceinline__ DF::V neg_v<DF>(const DF::V& v) {
     return DF::V{df{-v.re.h, -v.re.l}, df{-v.im.h, -v.im.l}};
 }
 
-// Apply the 2x2 matrix U (row-major) on tile-local bit b to the 2^T tile.
-template <class P>
-__device__ void tile_gate(typename P::V* tile, int T, int b, const typename P::M* U) {
-    const typename P::M u00 = U[0], u01 = U[1], u10 = U[2], u11 = U[3];
-    const uint32_t below = (1u << b) - 1u;
-    for (uint32_t i = threadIdx.x; i < (1u << (T - 1)); i += blockDim.x) {
-        const uint32_t lo = ((i & ~below) << 1) | (i & below);
-        const uint32_t hi = lo | (1u << b);
-        const typename P::V x0 = tile[lo], x1 = tile[hi];
-        typename P::A a0, a1;
-        P::mac_first(a0, u00, x0);
-        P::mac(a0, u01, x1);
-        P::mac_first(a1, u10, x0);
-        P::mac(a1, u11, x1);
-        tile[lo] = outv<P>(a0);
-        tile[hi] = outv<P>(a1);
+// Shared-memory slot of tile element i (one pad slot per 16 elements keeps
+// the 16-element strides of register groups on distinct banks).
+__device__ __forceinline__ uint32_t pad16(uint32_t i) { return i + (i >> 4); }
+
+// Apply the G single-qubit matrices of tile-local bits b0 .. b0+G-1
+// (U + 4*t for bit b0+t) in registers: a thread owns the 2^G elements that
+// differ in those bits, so G gates cost one shared-memory round trip.
+template <class P, int G>
+__device__ void tile_gates_reg(typename P::V* tile, int T, int b0, const typename P::M* U) {
+    using V = typename P::V;
+    constexpr int E = 1 << G;
+    typename P::M u[G][4];
+#pragma unroll
+    for (int t = 0; t < G; ++t)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) u[t][k] = U[4 * t + k];
+    const uint32_t below = (1u << b0) - 1u;
+    const int nbase = 1 << (T - G);
+    for (int b = threadIdx.x; b < nbase; b += blockDim.x) {
+        const uint32_t base = (((uint32_t)b & ~below) << G) | ((uint32_t)b & below);
+        V v[E];
+#pragma unroll
+        for (int j = 0; j < E; ++j) v[j] = tile[pad16(base | ((uint32_t)j << b0))];
+#pragma unroll
+        for (int t = 0; t < G; ++t)
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                if (j & (1 << t)) continue;
+                const int j2 = j | (1 << t);
+                typename P::A a0, a1;
+                P::mac_first(a0, u[t][0], v[j]);
+                P::mac(a0, u[t][1], v[j2]);
+                P::mac_first(a1, u[t][2], v[j]);
+                P::mac(a1, u[t][3], v[j2]);
+                v[j] = outv<P>(a0);
+                v[j2] = outv<P>(a1);
+            }
+#pragma unroll
+        for (int j = 0; j < E; ++j) tile[pad16(base | ((uint32_t)j << b0))] = v[j];
     }
     __syncthreads();
+}
+
+// Gates on the tile-local bits [b0, b0 + cnt), whose matrices are U + 4*i.
+template <class P>
+__device__ void tile_gates(typename P::V* tile, int T, int b0, int cnt, const typename P::M* U, int gmax_arg) {
+    // register budget: 16 complex64 or 8 double-float values per thread
+    const int gmax = gmax_arg;
+    while (cnt > 0) {
+        const int g = cnt >= gmax ? gmax : cnt;
+        switch (g) {
+            case 4: tile_gates_reg<P, 4>(tile, T, b0, U); break;
+            case 3: tile_gates_reg<P, 3>(tile, T, b0, U); break;
+            case 2: tile_gates_reg<P, 2>(tile, T, b0, U); break;
+            default: tile_gates_reg<P, 1>(tile, T, b0, U); break;
+        }
+        b0 += g;
+        cnt -= g;
+        U += 4 * g;
+    }
 }
 
 // Block-wide double-float sum of (s, e) pairs; result valid in thread 0.
@@ -213,25 +256,26 @@ __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ BatchArgs
         if (it.kind == 0) {
             // ------------------------------------------------ small circuit
             const uint32_t N = 1u << n;
-            for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) tile[i] = (i == 0) ? one_v<P>() : zero_v<P>();
+            for (uint32_t i = threadIdx.x; i < N; i += blockDim.x)
+                tile[pad16(i)] = (i == 0) ? one_v<P>() : zero_v<P>();
             __syncthreads();
             for (int l = 0; l < a.layers; ++l) {
-                for (int q = 0; q < n; ++q) tile_gate<P>(tile, n, q, U + ((size_t)l * n + q) * 4);
+                tile_gates<P>(tile, n, 0, n, U + (size_t)l * n * 4, a.gmax);
                 for (uint32_t i = threadIdx.x; i < N; i += blockDim.x)
-                    if (__popc(i & (i >> 1)) & 1) tile[i] = neg_v<P>(tile[i]);
+                    if (__popc(i & (i >> 1)) & 1) tile[pad16(i)] = neg_v<P>(tile[pad16(i)]);
                 __syncthreads();
             }
             const uint32_t zmask = (n > 1) ? ((1u << (n - 1)) - 1u) : 0u;
             for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
                 float h, l;
-                sq(tile[i], h, l);
+                sq(tile[pad16(i)], h, l);
                 const float f = (float)((n - 1) - 2 * __popc((i ^ (i >> 1)) & zmask));
                 float p = fmul(h, f);
                 float pe = __fmaf_rn(h, f, -p);
                 acc2(zs, ze, p, __fmaf_rn(l, f, pe));
                 for (int q = 0; q < n; ++q)
                     if (!((i >> q) & 1u)) {
-                        re_dot(tile[i | (1u << q)], tile[i], h, l);
+                        re_dot(tile[pad16(i | (1u << q))], tile[pad16(i)], h, l);
                         acc2(xs, xe, h, l);
                     }
             }
@@ -255,18 +299,18 @@ __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ BatchArgs
             const uint32_t TN = 1u << T;
             if (it.kind == 1 && it.layer == 0) {
                 for (uint32_t l = threadIdx.x; l < TN; l += blockDim.x)
-                    tile[l] = (t == 0 && l == 0) ? one_v<P>() : zero_v<P>();
+                    tile[pad16(l)] = (t == 0 && l == 0) ? one_v<P>() : zero_v<P>();
             } else {
-                for (uint32_t l = threadIdx.x; l < TN; l += blockDim.x) tile[l] = P::load(st[gidx(l)]);
+                for (uint32_t l = threadIdx.x; l < TN; l += blockDim.x) tile[pad16(l)] = P::load(st[gidx(l)]);
             }
             __syncthreads();
             if (it.kind == 1) {
-                for (int q = 0; q < T; ++q) tile_gate<P>(tile, T, q, U + ((size_t)it.layer * n + q) * 4);
+                tile_gates<P>(tile, T, 0, T, U + (size_t)it.layer * n * 4, a.gmax);
             } else if (it.kind == 2) {
-                for (int q = T; q < n; ++q) tile_gate<P>(tile, T, L + (q - T), U + ((size_t)it.layer * n + q) * 4);
+                tile_gates<P>(tile, T, L, n - T, U + ((size_t)it.layer * n + T) * 4, a.gmax);
                 for (uint32_t l = threadIdx.x; l < TN; l += blockDim.x) {
                     const uint64_t x = gidx(l);
-                    if (__popcll(x & (x >> 1)) & 1) tile[l] = neg_v<P>(tile[l]);
+                    if (__popcll(x & (x >> 1)) & 1) tile[pad16(l)] = neg_v<P>(tile[pad16(l)]);
                 }
                 __syncthreads();
             }
@@ -274,7 +318,7 @@ __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ BatchArgs
                 for (uint32_t l = threadIdx.x; l < TN; l += blockDim.x) {
                     const uint64_t x = gidx(l);
                     float h, lo;
-                    sq(tile[l], h, lo);
+                    sq(tile[pad16(l)], h, lo);
                     const float f = (float)((n - 1) - 2 * __popcll((x ^ (x >> 1)) & zmask));
                     float p = fmul(h, f);
                     float pe = __fmaf_rn(h, f, -p);
@@ -282,7 +326,7 @@ __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ BatchArgs
                     for (int q = T; q < n; ++q) {
                         const int b = L + (q - T);
                         if (!((l >> b) & 1u)) {
-                            re_dot(tile[l | (1u << b)], tile[l], h, lo);
+                            re_dot(tile[pad16(l | (1u << b))], tile[pad16(l)], h, lo);
                             acc2(xs, xe, h, lo);
                         }
                     }
@@ -293,11 +337,11 @@ __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ BatchArgs
                     for (int q = 0; q < T; ++q)
                         if (!((l >> q) & 1u)) {
                             float h, lo;
-                            re_dot(tile[l | (1u << q)], tile[l], h, lo);
+                            re_dot(tile[pad16(l | (1u << q))], tile[pad16(l)], h, lo);
                             acc2(xs, xe, h, lo);
                         }
             } else {
-                for (uint32_t l = threadIdx.x; l < TN; l += blockDim.x) st[gidx(l)] = P::store(tile[l]);
+                for (uint32_t l = threadIdx.x; l < TN; l += blockDim.x) st[gidx(l)] = P::store(tile[pad16(l)]);
             }
             __syncthreads();
         }
@@ -477,7 +521,9 @@ void capture(qe_batch* b) {
     a.partials = b->partials;
     a.energies = b->energies;
     a.spin_limit = 1ll << 24;   // ~4 s of 256 ns sleeps
-    const size_t smem = sizeof(typename P::V) << b->plan.T;
+    // gates per register group, measured best on GB300: 2 (double-float), 4 (FP32)
+    a.gmax = sizeof(typename P::V) >= 16 ? 2 : 4;
+    const size_t smem = (sizeof(typename P::V) << b->plan.T) + (sizeof(typename P::V) << b->plan.T) / 16;
     auto fn = k_batch<P>;
     QE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;

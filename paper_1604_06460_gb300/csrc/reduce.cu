@@ -12,6 +12,7 @@
 // The native-FP64 policy accumulates in FP64 directly.
 #include <algorithm>
 #include <type_traits>
+#include <vector>
 
 #include "qe_arith.cuh"
 #include "qe_internal.h"
@@ -39,9 +40,18 @@ __device__ __forceinline__ Acc acc_merge(Acc a, Acc b) {
 }
 
 // |v|^2 and Re(conj(w) v i^ny) as unevaluated (hi, lo) float pairs.
+// FP32 inputs: exact products by TwoProd (no low parts to cross).
+__device__ __forceinline__ void two_prod_sum(float a, float b, float c, float d, float& h, float& l) {
+    // a*b + c*d with both products exact and one TwoSum
+    const float p = fmul(a, b), pe = __fmaf_rn(a, b, -p);
+    const float q = fmul(c, d), qe = __fmaf_rn(c, d, -q);
+    const float s = fadd(p, q), bb = fsub(s, p);
+    const float e = fadd(fsub(p, fsub(s, bb)), fsub(q, bb));
+    h = s;
+    l = fadd(e, fadd(pe, qe));
+}
 __device__ __forceinline__ void abs2(const float2& v, float& h, float& l) {
-    df_first(h, l, df{v.x, 0.f}, df{v.x, 0.f});
-    df_acc(h, l, df{v.y, 0.f}, df{v.y, 0.f});
+    two_prod_sum(v.x, v.x, v.y, v.y, h, l);
 }
 __device__ __forceinline__ void abs2(const DF::V& v, float& h, float& l) {
     df_first(h, l, v.re, v.re);
@@ -49,14 +59,8 @@ __device__ __forceinline__ void abs2(const DF::V& v, float& h, float& l) {
 }
 // Re(conj(w) * v * i^ny):  conj(w) v = (w.re v.re + w.im v.im) + i (w.re v.im - w.im v.re)
 __device__ __forceinline__ void corr(const float2& w, const float2& v, int ny, float& h, float& l) {
-    df wr{w.x, 0.f}, wi{w.y, 0.f}, vr{v.x, 0.f}, vi{v.y, 0.f};
-    if ((ny & 1) == 0) {
-        df_first(h, l, wr, vr);
-        df_acc(h, l, wi, vi);
-    } else {
-        df_first(h, l, wr, vi);
-        df_acc_neg(h, l, wi, vr);
-    }
+    if ((ny & 1) == 0) two_prod_sum(w.x, v.x, w.y, v.y, h, l);
+    else two_prod_sum(w.x, v.y, -w.y, v.x, h, l);
     if (ny == 1 || ny == 2) { h = -h; l = -l; }
 }
 __device__ __forceinline__ void corr(const DF::V& w, const DF::V& v, int ny, float& h, float& l) {
@@ -153,62 +157,124 @@ __global__ void k_sum_partials(const double2* __restrict__ partial, uint64_t nou
 }
 
 // ---------------------------------------------------------- expectation
-// Up to NT Pauli terms per launch.  For term t and amplitude index x:
-//   xm == 0: |alpha_x|^2 (-1)^popc(x & zm)
-//   xm != 0: over x with the lowest bit of xm clear,
-//            2 Re(conj(alpha_{x^xm}) alpha_x i^ny) (-1)^popc(x & zm)
-constexpr int kNT = 8;
+// Terms are evaluated on shared-memory tiles.  A launch covers one tile
+// layout: the chunk bits [0, L) plus a set of higher qubits (hq); every term
+// it evaluates has its X/Y qubits inside the layout, so the partner
+// amplitude alpha_{x ^ xm} is in the same tile.  Z-only terms of equal weight
+// share one integer count of odd parities per amplitude:
+//     sum_t w (-1)^popc(x & z_t) = w (N_g - 2 #{t : popc(x & z_t) odd}).
+// Terms with X/Y parts accumulate 2 Re(conj(alpha_{x^xm}) alpha_x i^ny)
+// (-1)^popc(x & zm) over the x whose lowest xm bit is clear.
+constexpr int kZW = 4;     // Z-only weight groups per launch
+constexpr int kZT = 64;    // Z-only masks per launch
+constexpr int kXT = 12;    // terms with X/Y parts per launch
 template <class S>
 struct ExpArgs {
     const S* x;
-    uint64_t count;            // 2^n
-    int nt;
-    uint64_t xm[kNT], zm[kNT];
-    int ny[kNT];
-    double w[kNT];
+    uint64_t ntiles;
+    int L, T, kh;
+    uint8_t hq[16];
+    int nzg;                   // weight groups
+    int zg_end[kZW];           // end of group g in zm[]
+    double zw[kZW];
+    uint64_t zm[kZT];
+    int nxt;
+    uint32_t xloc[kXT];        // xm mapped to tile-local bits
+    uint64_t xz[kXT];          // zm (global)
+    int xny[kXT];
+    double xw[kXT];
     double2* partial;          // one per block
 };
 
 template <class S>
-__global__ void __launch_bounds__(kRThreads) k_expect_partial(const __grid_constant__ ExpArgs<S> a) {
+__global__ void __launch_bounds__(kRThreads) k_expect_tile(const __grid_constant__ ExpArgs<S> a) {
+    using V = decltype(rview(S{}));
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* tile = reinterpret_cast<V*>(smem_raw);
     __shared__ Acc sh[32];
-    Acc acc[kNT];
+    __shared__ uint64_t offA[64], offB[64];
+    const int tid = threadIdx.x;
+    if (tid < 64) {
+        uint64_t oa = 0, ob = 0;
+        for (int j = 0; j < 6 && j < a.kh; ++j)
+            if ((tid >> j) & 1) oa |= 1ull << a.hq[j];
+        for (int j = 6; j < a.kh; ++j)
+            if ((tid >> (j - 6)) & 1) ob |= 1ull << a.hq[j];
+        offA[tid] = oa;
+        offB[tid] = ob;
+    }
+    __syncthreads();
+    Acc zacc[kZW], xacc[kXT];
 #pragma unroll
-    for (int t = 0; t < kNT; ++t) acc[t] = Acc{0.f, 0.f};
-    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < a.count;
-         x += (uint64_t)gridDim.x * blockDim.x) {
-        const auto v = rview(a.x[x]);
-        float ph = 0.f, pl = 0.f;
-        bool have_p = false;
+    for (int g = 0; g < kZW; ++g) zacc[g] = Acc{0.f, 0.f};
 #pragma unroll
-        for (int t = 0; t < kNT; ++t) {
-            if (t >= a.nt) break;
-            const uint64_t xm = a.xm[t];
-            const bool neg = __popcll(x & a.zm[t]) & 1;
-            float h, l;
-            if (xm == 0) {
-                if (!have_p) { abs2(v, ph, pl); have_p = true; }
-                h = ph; l = pl;
-            } else {
-                if (x & (xm & (~xm + 1ull))) continue;   // lowest bit of xm must be 0
-                corr(rview(a.x[x ^ xm]), v, a.ny[t], h, l);
-                h *= 2.f; l *= 2.f;
-            }
-            if (neg) { h = -h; l = -l; }
-            acc_add(acc[t], h, l);
+    for (int t = 0; t < kXT; ++t) xacc[t] = Acc{0.f, 0.f};
+    const uint32_t Tn = 1u << a.T, lowmask = (1u << a.L) - 1u;
+    for (uint64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const uint64_t base = insert_zero_bits(t << a.L, a.hq, a.kh);
+        for (uint32_t l = tid; l < Tn; l += blockDim.x) {
+            const uint32_t h = l >> a.L;
+            tile[l] = rview(a.x[base + (l & lowmask) + offA[h & 63] + offB[h >> 6]]);
         }
+        __syncthreads();
+        if (a.nzg > 0) {
+            for (uint32_t l = tid; l < Tn; l += blockDim.x) {
+                const uint32_t h = l >> a.L;
+                const uint64_t x = base + (l & lowmask) + offA[h & 63] + offB[h >> 6];
+                float ph, pl;
+                abs2(tile[l], ph, pl);
+                int t0 = 0;
+#pragma unroll
+                for (int g = 0; g < kZW; ++g) {
+                    if (g >= a.nzg) break;
+                    int odd = 0;
+                    for (int k = t0; k < a.zg_end[g]; ++k) odd += __popcll(x & a.zm[k]) & 1;
+                    const float f = (float)((a.zg_end[g] - t0) - 2 * odd);
+                    t0 = a.zg_end[g];
+                    const float p = fmul(ph, f);
+                    acc_add(zacc[g], p, __fmaf_rn(pl, f, __fmaf_rn(ph, f, -p)));
+                }
+            }
+        }
+        // terms with X/Y parts: one thread per pair (l, l ^ xm) with the
+        // lowest xm bit of l clear, so no lane idles
+#pragma unroll
+        for (int k = 0; k < kXT; ++k) {
+            if (k >= a.nxt) break;
+            const uint32_t xl = a.xloc[k];
+            const uint32_t below = (xl & (~xl + 1u)) - 1u;
+            for (uint32_t i = tid; i < Tn / 2; i += blockDim.x) {
+                const uint32_t l = ((i & ~below) << 1) | (i & below);
+                const uint32_t h = l >> a.L;
+                const uint64_t x = base + (l & lowmask) + offA[h & 63] + offB[h >> 6];
+                float hh, ll;
+                corr(tile[l ^ xl], tile[l], a.xny[k], hh, ll);
+                if (__popcll(x & a.xz[k]) & 1) { hh = -hh; ll = -ll; }
+                acc_add(xacc[k], 2.f * hh, 2.f * ll);
+            }
+        }
+        __syncthreads();
     }
     double s = 0.0, c = 0.0;
 #pragma unroll
-    for (int t = 0; t < kNT; ++t) {
-        if (t >= a.nt) break;
-        Acc r = block_reduce(acc[t], sh);
-        if (threadIdx.x == 0) {
+    for (int g = 0; g < kZW; ++g) {
+        if (g >= a.nzg) break;
+        Acc r = block_reduce(zacc[g], sh);
+        if (tid == 0) {
             df d = df_norm(r.s, r.e);
-            neumaier(s, c, df2d(d.h, d.l) * a.w[t]);
+            neumaier(s, c, df2d(d.h, d.l) * a.zw[g]);
         }
     }
-    if (threadIdx.x == 0) a.partial[blockIdx.x] = make_double2(s, c);
+#pragma unroll
+    for (int k = 0; k < kXT; ++k) {
+        if (k >= a.nxt) break;
+        Acc r = block_reduce(xacc[k], sh);
+        if (tid == 0) {
+            df d = df_norm(r.s, r.e);
+            neumaier(s, c, df2d(d.h, d.l) * a.xw[k]);
+        }
+    }
+    if (tid == 0) a.partial[blockIdx.x] = make_double2(s, c);
 }
 
 // Native FP64 variants (baseline policy).
@@ -280,34 +346,217 @@ void probs_impl(qe_state* s, int m, const int* qubits, double* host_out) {
     QE_CUDA(cudaStreamSynchronize(s->stream));
 }
 
+// Terms whose X/Y qubits do not fit one tile layout: grid-stride over x with
+// the partner amplitude read from global memory.
+template <class S>
+struct WideArgs {
+    const S* x;
+    uint64_t count;
+    int nt;
+    uint64_t xm[kXT], zm[kXT];
+    int ny[kXT];
+    double w[kXT];
+    double2* partial;
+};
+
+template <class S>
+__global__ void __launch_bounds__(kRThreads) k_expect_wide(const __grid_constant__ WideArgs<S> a) {
+    __shared__ Acc sh[32];
+    Acc acc[kXT];
+#pragma unroll
+    for (int t = 0; t < kXT; ++t) acc[t] = Acc{0.f, 0.f};
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < a.count;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const auto v = rview(a.x[x]);
+#pragma unroll
+        for (int t = 0; t < kXT; ++t) {
+            if (t >= a.nt) break;
+            const uint64_t xm = a.xm[t];
+            if (x & (xm & (~xm + 1ull))) continue;
+            float h, l;
+            corr(rview(a.x[x ^ xm]), v, a.ny[t], h, l);
+            if (__popcll(x & a.zm[t]) & 1) { h = -h; l = -l; }
+            acc_add(acc[t], 2.f * h, 2.f * l);
+        }
+    }
+    double s = 0.0, c = 0.0;
+#pragma unroll
+    for (int t = 0; t < kXT; ++t) {
+        if (t >= a.nt) break;
+        Acc r = block_reduce(acc[t], sh);
+        if (threadIdx.x == 0) {
+            df d = df_norm(r.s, r.e);
+            neumaier(s, c, df2d(d.h, d.l) * a.w[t]);
+        }
+    }
+    if (threadIdx.x == 0) a.partial[blockIdx.x] = make_double2(s, c);
+}
+
 template <class S>
 double expect_impl(qe_state* s, int nterms, const uint64_t* xm, const uint64_t* zm, const double* cf) {
+    const int n = s->n;
+    const int Tmax = std::min(n, sizeof(S) >= 16 ? 11 : 12);
+    const int Lh = std::min(5, Tmax);                        // chunk bits of the high layouts
+    const uint64_t nmask = (n >= 64) ? ~0ull : ((1ull << n) - 1ull);
+    // --- layouts: 0 = contiguous tiles of 2^Tmax; others = chunk + high set
+    struct Layout {
+        int L = 0;
+        std::vector<int> high;   // sorted qubits >= L
+        std::vector<int> xterms;
+    };
+    std::vector<Layout> lay(1);
+    lay[0].L = Tmax;
+    std::vector<int> zterms, wide;
+    for (int t = 0; t < nterms; ++t) {
+        if (xm[t] == 0) { zterms.push_back(t); continue; }
+        if ((xm[t] >> Tmax) == 0) { lay[0].xterms.push_back(t); continue; }
+        const uint64_t hb = xm[t] & nmask & ~((1ull << Lh) - 1ull);
+        if (__builtin_popcountll(hb) > Tmax - Lh) { wide.push_back(t); continue; }
+        bool placed = false;
+        for (size_t j = 1; j < lay.size() && !placed; ++j) {
+            uint64_t cur = 0;
+            for (int q : lay[j].high) cur |= 1ull << q;
+            if (__builtin_popcountll(cur | hb) <= Tmax - Lh) {
+                for (int q = 0; q < n; ++q)
+                    if (((hb >> q) & 1ull) && !((cur >> q) & 1ull)) lay[j].high.push_back(q);
+                std::sort(lay[j].high.begin(), lay[j].high.end());
+                lay[j].xterms.push_back(t);
+                placed = true;
+            }
+        }
+        if (!placed) {
+            Layout L;
+            L.L = Lh;
+            for (int q = 0; q < n; ++q)
+                if ((hb >> q) & 1ull) L.high.push_back(q);
+            L.xterms.push_back(t);
+            lay.push_back(L);
+        }
+    }
+    // Z-only terms grouped by weight
+    std::vector<double> wv;
+    std::vector<std::vector<int>> wg;
+    for (int t : zterms) {
+        size_t g = std::find(wv.begin(), wv.end(), cf[t]) - wv.begin();
+        if (g == wv.size()) { wv.push_back(cf[t]); wg.emplace_back(); }
+        wg[g].push_back(t);
+    }
+    // --- launches
+    std::vector<std::pair<int, std::vector<int>>> zchunks;   // (group, masks) pieces of <= kZT
+    for (size_t g = 0; g < wg.size(); ++g)
+        for (size_t i = 0; i < wg[g].size(); i += kZT)
+            zchunks.push_back({(int)g, std::vector<int>(wg[g].begin() + i,
+                                                        wg[g].begin() + std::min(wg[g].size(), i + kZT))});
     static thread_local ExpArgs<S> a;
     a.x = reinterpret_cast<const S*>(s->d);
-    a.count = dim(s);
-    const int launches = (nterms + kNT - 1) / kNT;
-    unsigned grid = (unsigned)std::min<uint64_t>((a.count + kRThreads - 1) / kRThreads,
-                                                 (uint64_t)num_sms() * 8);
-    char* scr = (char*)ensure_scratch(s, (size_t)launches * grid * sizeof(double2) + 64);
-    double2* partial = (double2*)scr;
-    double* dout = (double*)(scr + (size_t)launches * grid * sizeof(double2));
-    for (int L = 0; L < launches; ++L) {
-        a.nt = std::min(kNT, nterms - L * kNT);
-        for (int t = 0; t < a.nt; ++t) {
-            const int g = L * kNT + t;
-            a.xm[t] = xm[g];
-            a.zm[t] = zm[g];
-            a.ny[t] = __builtin_popcountll(xm[g] & zm[g]) & 3;
-            a.w[t] = cf[g];
+    const size_t smem = sizeof(decltype(rview(S{}))) << Tmax;
+    QE_CUDA(cudaFuncSetAttribute(k_expect_tile<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    QE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_expect_tile<S>, kRThreads, smem));
+    // count launches first to size the scratch
+    struct Plan { int layout; std::vector<std::pair<int, std::vector<int>>> z; std::vector<int> x; };
+    std::vector<Plan> plans;
+    {
+        // layout 0 carries the Z groups; every layout splits its X terms by kXT
+        size_t zi = 0;
+        for (size_t j = 0; j < lay.size(); ++j) {
+            size_t xi = 0;
+            const auto& xs = lay[j].xterms;
+            do {
+                Plan p;
+                p.layout = (int)j;
+                if (j == 0) {
+                    int masks = 0;
+                    while (zi < zchunks.size() && (int)p.z.size() < kZW &&
+                           masks + (int)zchunks[zi].second.size() <= kZT) {
+                        masks += (int)zchunks[zi].second.size();
+                        p.z.push_back(zchunks[zi++]);
+                    }
+                }
+                for (; xi < xs.size() && (int)p.x.size() < kXT; ++xi) p.x.push_back(xs[xi]);
+                if (!p.z.empty() || !p.x.empty()) plans.push_back(p);
+            } while (xi < xs.size() || (j == 0 && zi < zchunks.size()));
         }
-        a.partial = partial + (size_t)L * grid;
-        Launch Lz(s, "expect_partial", (double)dim(s) * amp_bytes(s));
-        k_expect_partial<S><<<grid, kRThreads, 0, s->stream>>>(a);
+    }
+    const int nwide = (int)((wide.size() + kXT - 1) / kXT);
+    if (plans.empty() && nwide == 0) return 0.0;
+    uint64_t max_grid = (uint64_t)num_sms() * 8;
+    std::vector<unsigned> grids(plans.size());
+    for (size_t i = 0; i < plans.size(); ++i) {
+        const Layout& L = lay[plans[i].layout];
+        const int T = L.L + (int)L.high.size();
+        const uint64_t ntiles = 1ull << (n - T);
+        grids[i] = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)num_sms() * std::max(occ, 1));
+        max_grid = std::max<uint64_t>(max_grid, grids[i]);
+    }
+    const size_t nlaunch = plans.size() + (size_t)nwide;
+    char* scr = (char*)ensure_scratch(s, nlaunch * max_grid * sizeof(double2) + 64);
+    double2* partial = (double2*)scr;
+    double* dout = (double*)(scr + nlaunch * max_grid * sizeof(double2));
+    for (int w = 0; w < nwide; ++w) {
+        static thread_local WideArgs<S> b;
+        b.x = reinterpret_cast<const S*>(s->d);
+        b.count = dim(s);
+        b.nt = std::min(kXT, (int)wide.size() - w * kXT);
+        for (int j = 0; j < b.nt; ++j) {
+            const int t = wide[w * kXT + j];
+            b.xm[j] = xm[t];
+            b.zm[j] = zm[t];
+            b.ny[j] = __builtin_popcountll(xm[t] & zm[t]) & 3;
+            b.w[j] = cf[t];
+        }
+        b.partial = partial + (plans.size() + w) * max_grid;
+        QE_CUDA(cudaMemsetAsync(b.partial, 0, max_grid * sizeof(double2), s->stream));
+        const unsigned g = (unsigned)std::min<uint64_t>((dim(s) + kRThreads - 1) / kRThreads, max_grid);
+        Launch Lw(s, "expect_wide", (double)dim(s) * amp_bytes(s));
+        k_expect_wide<S><<<g, kRThreads, 0, s->stream>>>(b);
+        QE_CUDA(cudaGetLastError());
+    }
+    for (size_t i = 0; i < plans.size(); ++i) {
+        const Plan& p = plans[i];
+        const Layout& L = lay[p.layout];
+        a.L = L.L;
+        a.kh = (int)L.high.size();
+        a.T = a.L + a.kh;
+        if (a.kh > 12) fail(QE_ERR_UNSUPPORTED, "expectation layout too wide");
+        for (int j = 0; j < a.kh; ++j) a.hq[j] = (uint8_t)L.high[j];
+        a.ntiles = 1ull << (n - a.T);
+        a.nzg = (int)p.z.size();
+        int k = 0;
+        for (int g = 0; g < a.nzg; ++g) {
+            a.zw[g] = wv[p.z[g].first];
+            for (int t : p.z[g].second) a.zm[k++] = zm[t];
+            a.zg_end[g] = k;
+        }
+        a.nxt = (int)p.x.size();
+        for (int j = 0; j < a.nxt; ++j) {
+            const int t = p.x[j];
+            uint32_t loc = 0;
+            for (int q = 0; q < n; ++q) {
+                if (!((xm[t] >> q) & 1ull)) continue;
+                int pos = -1;
+                if (q < a.L) pos = q;
+                else
+                    for (int h = 0; h < a.kh; ++h)
+                        if (L.high[h] == q) pos = a.L + h;
+                if (pos < 0) fail(QE_ERR_STATE, "expectation term outside its layout");
+                loc |= 1u << pos;
+            }
+            a.xloc[j] = loc;
+            a.xz[j] = zm[t];
+            a.xny[j] = __builtin_popcountll(xm[t] & zm[t]) & 3;
+            a.xw[j] = cf[t];
+        }
+        a.partial = partial + i * max_grid;
+        // unused partial slots of this launch read as zero
+        QE_CUDA(cudaMemsetAsync(a.partial, 0, max_grid * sizeof(double2), s->stream));
+        Launch Lz(s, "expect_tile", (double)dim(s) * amp_bytes(s));
+        k_expect_tile<S><<<grids[i], kRThreads, smem, s->stream>>>(a);
         QE_CUDA(cudaGetLastError());
     }
     {
         Launch Lz(s, "sum_partials", 0.0, false);
-        k_sum_partials<<<1, 1, 0, s->stream>>>(partial, 1, (uint64_t)launches * grid, nullptr, dout);
+        k_sum_partials<<<1, 1, 0, s->stream>>>(partial, 1, (uint64_t)nlaunch * max_grid, nullptr, dout);
         QE_CUDA(cudaGetLastError());
     }
     double out = 0.0;

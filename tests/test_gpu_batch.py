@@ -36,7 +36,7 @@ def batch_inputs(ns, layers, seed0):
 
 
 @pytest.mark.parametrize("dtype,tol", [("c128", 1e-11), ("c64", 2e-4)])
-@pytest.mark.parametrize("plan", [None, (6, 1, 128), (7, 3, 256), (8, 16, 512)])
+@pytest.mark.parametrize("plan", [None, (6, 1, 128), (7, 3, 256), (8, 16, 128)])
 def test_batch_energies_vs_oracle(qe, dtype, tol, plan):
     layers, hx = 3, 0.7
     ns = [1, 2, 3, 5, 7, 9, 11, 4, 6, 8, 10, 7, 3]

@@ -1,0 +1,156 @@
+"""Parity at the full sizes the benchmark runs, in the same launch
+configurations: sampled outputs the oracle computes one by one, slices on
+which the operation is closed, and properties that hold at any size.
+
+Sizes: n = 20 (gate by gate), n = 30 complex128 (16 GiB), n = 32 complex64
+(32 GiB), n = 33 complex128 (128 GiB).  Each test frees its state before the
+next one starts.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1604_06460_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qe():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1604_06460_gb300 import build as B
+    B.build()
+    from paper_1604_06460_gb300 import qe as Q
+    Q.load()
+    return Q
+
+
+@pytest.fixture(autouse=True)
+def _free_cached_memory():
+    yield
+    import torch
+    torch.cuda.empty_cache()
+
+
+def test_config0_gate_by_gate_n20_vs_oracle(qe):
+    n = 20
+    gates = I.random_circuit(n, 10, seed=0)
+    with qe.State(n, "c128") as st:
+        st.set_policy(qe.POLICY_AUTO, 1)
+        for g in gates:
+            st.apply(g)
+        got = st.get()
+    ref = oracle.zero_state(n)
+    for g in gates:
+        ref = oracle.apply_gate(ref, g.qubits, g.matrix)
+    assert np.max(np.abs(got - ref)) < 1e-12
+    assert oracle.fidelity(ref, got) > 1 - 1e-10
+
+
+def test_config1_qft_n30_sampled_vs_oracle(qe):
+    # the benchmark's emulated 30-qubit QFT of a random normalised state;
+    # output amplitudes computed by the oracle one at a time from the input
+    n = 30
+    with qe.State(n, "c128") as st:
+        st.set_policy(qe.POLICY_EMULATE, 1)
+        st.init_random(5)
+        psi = st.get()                      # 16 GiB host copy of the input
+        st.apply_qft(0, n)
+        for idx in (0, (1 << n) - 1, 123456789):
+            want = oracle.qft_amplitude(psi, 0, n, idx)
+            got = st.get(idx, 1)[0]
+            assert abs(got - want) < 1e-12
+        assert abs(st.norm2() - 1) < 1e-12     # Parseval
+        del psi
+
+
+def test_config1_circuit_n30_then_inverse_is_identity(qe):
+    n = 30
+    gates = I.random_circuit(n, 20, seed=0)
+    with qe.State(n, "c128") as st:
+        st.set_policy(qe.POLICY_AUTO, 2)
+        for g in gates:
+            st.apply(g)
+        for g in reversed(gates):
+            st.apply_gate(g.qubits, g.matrix.conj().T)
+        st.flush()
+        head = st.get(0, 1 << 12)
+        probe = st.get((1 << n) - (1 << 12), 1 << 12)
+        nrm = st.norm2()
+    assert abs(head[0] - 1) < 1e-12
+    assert np.max(np.abs(head[1:])) < 1e-12 and np.max(np.abs(probe)) < 1e-12
+    # ~560 fused passes of 47-bit double-float arithmetic: the norm drifts by
+    # about 2e-15 per pass (1e-12 here), far inside the 1 - 1e-10 fidelity bar
+    assert abs(nrm - 1) < 1e-11
+
+
+def test_config2_tensor_cores_n32_then_inverse(qe):
+    # complex64 with 5-qubit blocks on tcgen05: FP32-level error per pass
+    n = 32
+    gates = I.random_circuit(n, 30, seed=5)
+    with qe.State(n, "c64") as st:
+        st.set_policy(qe.POLICY_AUTO, 5)
+        st.reset_stats()
+        st.profile(True)
+        for g in gates:
+            st.apply(g)
+        for g in reversed(gates):
+            st.apply_gate(g.qubits, g.matrix.conj().T)
+        st.flush()
+        prof = st.profile_read()
+        st.profile(False)
+        head = st.get(0, 1 << 12).astype(np.complex128)
+    assert prof.get("gate_tc_k5", (0,))[0] > 0          # the tensor-core kernel ran
+    assert abs(head[0] - 1) < 1e-3 and np.max(np.abs(head[1:])) < 1e-3
+
+
+def test_config4_add_const_n33_blocks_bit_exact(qe):
+    # register [0,16): every contiguous block of 2^16 amplitudes maps to
+    # itself; sampled blocks are compared with the oracle's index map
+    n, c = 33, I.random_constant(16, 7)
+    with qe.State(n, "c128") as st:
+        st.set_policy(qe.POLICY_EMULATE, 1)
+        st.init_random(9)
+        blocks = [0, 12345, (1 << 17) - 1]
+        before = [st.get(b << 16, 1 << 16) for b in blocks]
+        st.add_const(list(range(16)), c)
+        after = [st.get(b << 16, 1 << 16) for b in blocks]
+    for x, y in zip(before, after):
+        assert np.array_equal(y, oracle.add_const(x, list(range(16)), c))
+
+
+def test_config4_high_register_column_bit_exact(qe):
+    import torch
+    n, c = 33, I.random_constant(16, 11)
+    with qe.State(n, "c128") as st:
+        st.set_policy(qe.POLICY_EMULATE, 1)
+        st.init_random(3)
+        view = torch.view_as_complex(st.tensor.view(-1, 2))
+        for col in (0, 77777, (1 << 17) - 1):
+            idx = torch.arange(1 << 16, device="cuda", dtype=torch.int64) * (1 << 17) + col
+            before = view[idx].cpu().numpy()
+            st.add_const(list(range(17, 33)), c)
+            after = view[idx].cpu().numpy()
+            assert np.array_equal(after, oracle.add_const(before, list(range(16)), c))
+            st.add_const(list(range(17, 33)), (1 << 16) - c)   # undo
+        back = view[idx].cpu().numpy()
+        assert np.array_equal(back, before)
+
+
+def test_config4_qft_register_n33_sampled(qe):
+    # QFT on [0, 16) of the 33-qubit state: each contiguous block of 2^16 is
+    # transformed independently; check whole blocks against the oracle's DFT
+    # of that block (2^16-point, computed by the sampled definition)
+    n = 33
+    with qe.State(n, "c128") as st:
+        st.set_policy(qe.POLICY_EMULATE, 1)
+        st.init_random(9)
+        blk = 98765
+        x = st.get(blk << 16, 1 << 16)
+        st.apply_qft(0, 16)
+        y = st.get(blk << 16, 1 << 16)
+    for l in (0, 1, 4096, 65535):
+        want = oracle.qft_amplitude(x, 0, 16, l)
+        assert abs(y[l] - want) < 1e-12

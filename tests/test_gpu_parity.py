@@ -427,3 +427,33 @@ def test_tensor_core_fused_circuit_c64(qe):
         got = st.get().astype(np.complex128)
     assert np.max(np.abs(got - ref)) < 2e-5
     assert oracle.fidelity(ref, got) > 1 - 1e-8
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-12), ("c64", 1e-5)])
+def test_many_pauli_terms_all_layouts(qe, dtype, tol):
+    # Z-only terms in several weight groups (more than fit one launch), X/Y
+    # terms inside the low tile, with high qubits, and wider than one tile
+    n = 15
+    rng = np.random.default_rng(77)
+    xm, zm, cf = [], [], []
+    for t in range(90):                      # Z-only, 6 distinct weights
+        xm.append(0)
+        zm.append(int(rng.integers(0, 1 << n)))
+        cf.append([1.0, -0.5, 0.25, 2.0, 0.7, -1.3][t % 6])
+    for t in range(20):                      # low X/Y terms
+        xm.append(int(rng.integers(1, 1 << 8)))
+        zm.append(int(rng.integers(0, 1 << n)))
+        cf.append(float(rng.standard_normal()))
+    for q in range(n):                       # single high X
+        xm.append(1 << q)
+        zm.append(0)
+        cf.append(0.7)
+    for t in range(6):                       # wide X/Y strings
+        xm.append(int(rng.integers(1 << 10, 1 << n)) | 0x7F00)
+        zm.append(int(rng.integers(0, 1 << n)))
+        cf.append(float(rng.standard_normal()))
+    xm, zm, cf = (np.array(xm, dtype=np.uint64), np.array(zm, dtype=np.uint64), np.array(cf))
+    psi = I.random_state(n, 5)
+    with make(qe, n, dtype, psi=psi) as st:
+        e = st.expectation(xm, zm, cf)
+    assert abs(e - oracle.expectation(psi, xm, zm, cf)) < tol
