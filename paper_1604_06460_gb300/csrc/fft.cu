@@ -112,14 +112,11 @@ __device__ __forceinline__ void stage_group(typename P::V* tile, const typename 
             for (int j = 0; j < E; ++j) {
                 if (j & (1 << t)) continue;
                 const int j2 = j | (1 << t);
+                const uint32_t p = (gp0 | ((uint32_t)j << s_lo)) & smask;
+                const typename P::M w = roots[(1u << s) - 1u + p];
                 const V u = v[j], x = v[j2];
                 v[j] = P::add(u, x);
-                if (s == 0) {
-                    v[j2] = P::sub(u, x);   // the last stage's twiddle is exactly 1
-                } else {
-                    const uint32_t p = (gp0 | ((uint32_t)j << s_lo)) & smask;
-                    v[j2] = P::cmul(roots[(1u << s) - 1u + p], P::sub(u, x));
-                }
+                v[j2] = P::cmul(w, P::sub(u, x));
             }
         }
 #pragma unroll

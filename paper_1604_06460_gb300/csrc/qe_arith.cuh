@@ -96,16 +96,13 @@ __device__ __forceinline__ void df_first(float& s, float& e, df a, df b) {
     e = __fmaf_rn(a.h, b.l, e);
     e = __fmaf_rn(a.l, b.h, e);
 }
-// a + b and a - b for double-floats (TwoSum of the leading parts).  The pair
-// is left unnormalised (|lo| may exceed ulp(hi)/2): products (df_acc) and the
-// final join (df2d, one correctly rounded FP64 addition) take hi and lo
-// separately, so normalising here would only cost instructions.
+// a + b and a - b for double-floats (TwoSum of the leading parts).
 __device__ __forceinline__ df df_add(df a, df b) {
     float s = fadd(a.h, b.h);
     float bb = fsub(s, a.h);
     float e = fadd(fsub(a.h, fsub(s, bb)), fsub(b.h, bb));
     e = fadd(e, fadd(a.l, b.l));
-    return df{s, e};
+    return df_norm(s, e);
 }
 __device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df{-b.h, -b.l}); }
 

@@ -12,12 +12,15 @@
 //
 // Per tile (128 groups = 4096 amplitudes, 12 tile-local index bits: the 5
 // gate qubits and 7 others, chunks of >= 2^L contiguous amplitudes):
-//   1. all threads load the tile, split each value and store In_hi / In_lo
-//      into shared memory in the K-major 128-byte-swizzled operand layout;
+//   1. thread t loads 4 column quads of group row t % 128 (a warp reads 32
+//      consecutive rows), splits each value and stores In_hi / In_lo as
+//      16-byte chunks of the K-major 128-byte-swizzled operand layout (no
+//      bank conflicts: 8 consecutive rows hit 8 different chunks);
 //   2. one thread issues 24 tcgen05.mma (M=128, N=64, K=8, kind::tf32) into a
 //      64-column tensor-memory accumulator and commits them to an mbarrier;
 //   3. all threads wait on the mbarrier (bounded), read the accumulator with
-//      tcgen05.ld, stage the results in shared memory and store the tile.
+//      tcgen05.ld and store the outputs straight from registers (TMEM lane =
+//      group row, so a warp's stores cover consecutive rows).
 // W_hi / W_lo (64x64 each) are loaded once per CTA.  Waits that exceed their
 // limit set a status word and end the kernel after freeing tensor memory.
 #include <algorithm>
@@ -115,12 +118,10 @@ __global__ void __launch_bounds__(kTcThreads) k_gate_tc5(const __grid_constant__
     unsigned char* sA_lo = sA_hi + kRows * kK * 4;
     unsigned char* sW_hi = sA_lo + kRows * kK * 4;
     unsigned char* sW_lo = sW_hi + kN * kK * 4;
-    float2* stage = reinterpret_cast<float2*>(sA_hi);   // reused after the MMAs complete
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     __shared__ uint64_t hoff[32];
     __shared__ uint32_t cpos[32];
-    __shared__ uint8_t s_row[4096], s_col[4096];   // tile-local index -> (group row, matrix column)
     __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -158,44 +159,60 @@ __global__ void __launch_bounds__(kTcThreads) k_gate_tc5(const __grid_constant__
     const uint32_t tmem = tmem_base;
     const uint32_t gmask = cpos[31];
     const uint32_t lowmask = (1u << a.L) - 1u;
-    // row of a tile-local index: its 7 non-gate bits in order; column: its gate bits
-    for (uint32_t l = tid; l < 4096u; l += blockDim.x) {
-        uint32_t r = 0, c = 0;
+    // Load side: lane <-> group row (rows r = tid % 128, consecutive across a
+    // warp), each thread owns the column quads q = tid / 128 + 2 j, j < 4, so
+    // it writes whole 16-byte chunks of the swizzled operand.
+    const int lr = tid & (kRows - 1);
+    const int qbase = tid >> 7;
+    // Epilogue side: TMEM lane quarter of this warp, and which 16 columns of
+    // the real (0..31) and imaginary (32..63) halves it reads
+    const uint32_t equarter = (uint32_t)(warp & 3) * 32u;
+    const uint32_t ehalf = (uint32_t)(warp >> 2) * 16u;
+    const int er = (int)equarter + lane;
+    auto rowbits = [&](int r) {
+        uint32_t l = 0;
         int j = 0;
         for (int b = 0; b < 12; ++b)
-            if (!((gmask >> b) & 1u)) r |= ((l >> b) & 1u) << (j++);
-        for (int q = 0; q < 5; ++q) c |= ((l >> a.gpos[q]) & 1u) << q;
-        s_row[l] = (uint8_t)r;
-        s_col[l] = (uint8_t)c;
-    }
-    __syncthreads();
-    // each thread moves 16 amplitudes of a tile: l = tid + 256 * i
-    constexpr int kPer = 4096 / kTcThreads;
-    float2 cur[kPer], nxt[kPer];
+            if (!((gmask >> b) & 1u)) l |= (((uint32_t)r >> (j++)) & 1u) << b;
+        return l;
+    };
+    const uint32_t lrow_load = rowbits(lr);
+    const uint32_t lrow_out = rowbits(er);
+    auto goff = [&](uint32_t l) -> uint64_t { return (l & lowmask) + hoff[l >> a.L]; };
+    float2 cur[16], nxt[16];
     auto load_tile = [&](uint64_t t, float2* dst) {
         const uint64_t gb = insert_zero_bits(t << a.L, a.hq, a.kh);
 #pragma unroll
-        for (int i = 0; i < kPer; ++i) {
-            const uint32_t l = (uint32_t)tid + (uint32_t)kTcThreads * i;
-            dst[i] = a.x[gb + (l & lowmask) + hoff[l >> a.L]];
-        }
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = 4 * (qbase + 2 * j) + u;
+                dst[4 * j + u] = a.x[gb + goff(lrow_load | cpos[c])];
+            }
     };
     uint32_t phase = 0;
     uint64_t t = blockIdx.x;
     if (t < a.ntiles) load_tile(t, cur);
     for (; t < a.ntiles; t += gridDim.x) {
         const uint64_t gbase = insert_zero_bits(t << a.L, a.hq, a.kh);
-        // 1. split into TF32 hi/lo and store the operand, swizzled
+        // 1. split into TF32 hi/lo; 16-byte chunks of 4 consecutive K values
 #pragma unroll
-        for (int i = 0; i < kPer; ++i) {
-            const uint32_t l = (uint32_t)tid + (uint32_t)kTcThreads * i;
-            const float2 v = cur[i];
-            const int r = s_row[l], c = s_col[l];
-            const float rh = tf32_hi(v.x), ih = tf32_hi(v.y);
-            *reinterpret_cast<float*>(sA_hi + sw128_offset(r, c, kRows)) = rh;
-            *reinterpret_cast<float*>(sA_hi + sw128_offset(r, 32 + c, kRows)) = ih;
-            *reinterpret_cast<float*>(sA_lo + sw128_offset(r, c, kRows)) = __fsub_rn(v.x, rh);
-            *reinterpret_cast<float*>(sA_lo + sw128_offset(r, 32 + c, kRows)) = __fsub_rn(v.y, ih);
+        for (int j = 0; j < 4; ++j) {
+            const int q = qbase + 2 * j;
+            float4 rh, ih, rl, il;
+            float* prh = &rh.x; float* pih = &ih.x; float* prl = &rl.x; float* pil = &il.x;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float2 v = cur[4 * j + u];
+                prh[u] = tf32_hi(v.x);
+                pih[u] = tf32_hi(v.y);
+                prl[u] = __fsub_rn(v.x, prh[u]);
+                pil[u] = __fsub_rn(v.y, pih[u]);
+            }
+            *reinterpret_cast<float4*>(sA_hi + sw128_offset(lr, 4 * q, kRows)) = rh;
+            *reinterpret_cast<float4*>(sA_hi + sw128_offset(lr, 32 + 4 * q, kRows)) = ih;
+            *reinterpret_cast<float4*>(sA_lo + sw128_offset(lr, 4 * q, kRows)) = rl;
+            *reinterpret_cast<float4*>(sA_lo + sw128_offset(lr, 32 + 4 * q, kRows)) = il;
         }
         asm volatile("fence.proxy.async.shared::cta;");
         __syncthreads();
@@ -219,7 +236,8 @@ __global__ void __launch_bounds__(kTcThreads) k_gate_tc5(const __grid_constant__
         // prefetch the next tile while the tensor cores work
         const uint64_t tn = t + gridDim.x;
         if (tn < a.ntiles) load_tile(tn, nxt);
-        // 3. wait for the accumulator (bounded), read it, stage and store
+        // 3. wait for the accumulator (bounded), then write the outputs
+        //    straight from the tensor-memory registers
         if (!mbar_wait(smem_u32(&mbar), phase, a.spin_limit)) {
             atomicExch(a.status, 1u);
             s_abort = 1;
@@ -228,50 +246,34 @@ __global__ void __launch_bounds__(kTcThreads) k_gate_tc5(const __grid_constant__
         if (s_abort) break;
         phase ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        uint32_t v[32];
+        uint32_t re[16], im[16];
         {
-            const uint32_t quarter = (uint32_t)(warp & 3) * 32u;
-            const uint32_t col = (warp < 4) ? 0u : 32u;
-            const uint32_t taddr = tmem + (quarter << 16) + col;
+            const uint32_t taddr = tmem + (equarter << 16) + ehalf;
             asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-                "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                  "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                  "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
-                  "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
-                  "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]), "=r"(re[6]),
+                  "=r"(re[7]), "=r"(re[8]), "=r"(re[9]), "=r"(re[10]), "=r"(re[11]), "=r"(re[12]), "=r"(re[13]),
+                  "=r"(re[14]), "=r"(re[15])
                 : "r"(taddr));
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]), "=r"(im[6]),
+                  "=r"(im[7]), "=r"(im[8]), "=r"(im[9]), "=r"(im[10]), "=r"(im[11]), "=r"(im[12]), "=r"(im[13]),
+                  "=r"(im[14]), "=r"(im[15])
+                : "r"(taddr + 32u));
             asm volatile("tcgen05.wait::ld.sync.aligned;");
         }
-        // row r = TMEM lane; output element c of row r sits at the tile-local
-        // index with row bits r and gate bits c; the staging buffer pads one
-        // element per 32 so that a warp's 32 rows hit different banks
-        {
-            const uint32_t r = (uint32_t)(warp & 3) * 32u + (uint32_t)lane;
-            uint32_t lrow = 0;
-            int j = 0;
-            for (int b = 0; b < 12; ++b)
-                if (!((gmask >> b) & 1u)) lrow |= ((r >> (j++)) & 1u) << b;
-            float* st = reinterpret_cast<float*>(stage);
-            const int comp = (warp < 4) ? 0 : 1;
-#pragma unroll
-            for (int c = 0; c < 32; ++c) {
-                const uint32_t l = lrow | cpos[c];
-                st[2 * (l + (l >> 5)) + comp] = __uint_as_float(v[c]);
-            }
-        }
         asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
 #pragma unroll
-        for (int i = 0; i < kPer; ++i) {
-            const uint32_t l = (uint32_t)tid + (uint32_t)kTcThreads * i;
-            a.x[gbase + (l & lowmask) + hoff[l >> a.L]] = stage[l + (l >> 5)];
+        for (int c = 0; c < 16; ++c) {
+            const uint32_t l = lrow_out | cpos[ehalf + c];
+            a.x[gbase + goff(l)] = make_float2(__uint_as_float(re[c]), __uint_as_float(im[c]));
         }
         __syncthreads();
 #pragma unroll
-        for (int i = 0; i < kPer; ++i) cur[i] = nxt[i];
+        for (int i = 0; i < 16; ++i) cur[i] = nxt[i];
     }
     // free tensor memory (all MMAs of this CTA have completed or timed out)
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -341,6 +343,7 @@ void launch_gate_tc5(qe_state* s, const int* qubits, const cd* U) {
     a.spin_limit = 1ll << 26;
     const size_t smem = 1024 + (size_t)2 * kRows * kK * 4 + (size_t)2 * kN * kK * 4;
     QE_CUDA(cudaFuncSetAttribute(k_gate_tc5, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    QE_CUDA(cudaFuncSetAttribute(k_gate_tc5, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     int occ = 0;
     QE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gate_tc5, kTcThreads, smem));
     const uint64_t grid = std::min<uint64_t>(a.ntiles, (uint64_t)num_sms() * std::max(occ, 1));
