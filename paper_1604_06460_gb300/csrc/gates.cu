@@ -392,9 +392,15 @@ void diag_impl(qe_state* s, int k, const int* qubits, const cd* d) {
     } while (0)
 
 void launch_gate_dense(qe_state* s, int k, const int* qubits, const cd* U) {
-    if (s->dtype == QE_C64 && s->tensor_cores && !s->force_tile && s->n >= 12 && k >= 4) {
+    const bool tc64 = s->dtype == QE_C64;
+    const bool tc128 = s->dtype == QE_C128 && !s->c128_native;
+    if ((tc64 || tc128) && s->tensor_cores && !s->force_tile && s->n >= 12 && k >= 4) {
+        auto run = [&](const int* q5, const cd* U5) {
+            if (tc64) launch_gate_tc5(s, q5, U5);
+            else launch_gate_tc5_c128(s, q5, U5);
+        };
         if (k == 5) {
-            launch_gate_tc5(s, qubits, U);
+            run(qubits, U);
             return;
         }
         // widen a 4-qubit block by one idle qubit: U5 = 1_2 (x) U4 (new bit 4)
@@ -405,7 +411,7 @@ void launch_gate_dense(qe_state* s, int k, const int* qubits, const cd* U) {
         for (int hb = 0; hb < 2; ++hb)
             for (int r = 0; r < 16; ++r)
                 for (int c = 0; c < 16; ++c) U5[(r | (hb << 4)) * 32 + (c | (hb << 4))] = U[r * 16 + c];
-        launch_gate_tc5(s, q5, U5.data());
+        run(q5, U5.data());
         return;
     }
     QE_DISPATCH(s, dense_k, s, k, qubits, U);

@@ -98,6 +98,7 @@ void launch_scale(qe_state* s, double factor);
 void launch_gate_dense(qe_state* s, int k, const int* qubits, const cd* U);
 // 5-qubit block on a complex64 state with tcgen05 tensor cores (n >= 12)
 void launch_gate_tc5(qe_state* s, const int* qubits, const cd* U);
+void launch_gate_tc5_c128(qe_state* s, const int* qubits, const cd* U);
 // diagonal gate: amplitude x *= d[row(x)] for all x
 void launch_gate_diag(qe_state* s, int k, const int* qubits, const cd* d);
 // amplitudes with (x & mask) == value are multiplied by phase

@@ -74,6 +74,28 @@ __device__ __forceinline__ void corr(const DF::V& w, const DF::V& v, int ny, flo
     if (ny == 1 || ny == 2) { h = -h; l = -l; }
 }
 
+// -v, and acc += Re (im = false) or Im (im = true) of conj(w) v, accumulated
+// with exact products and TwoSum (no intermediate rounding of the pair).
+__device__ __forceinline__ float2 vneg(float2 v) { return make_float2(-v.x, -v.y); }
+__device__ __forceinline__ DF::V vneg(const DF::V& v) {
+    return DF::V{df{-v.re.h, -v.re.l}, df{-v.im.h, -v.im.l}};
+}
+__device__ __forceinline__ void corr_acc(Acc& a, const float2& w, const float2& v, bool im) {
+    float h, l;
+    if (!im) two_prod_sum(w.x, v.x, w.y, v.y, h, l);
+    else two_prod_sum(w.x, v.y, -w.y, v.x, h, l);
+    acc_add(a, h, l);
+}
+__device__ __forceinline__ void corr_acc(Acc& a, const DF::V& w, const DF::V& v, bool im) {
+    if (!im) {
+        df_acc(a.s, a.e, w.re, v.re);
+        df_acc(a.s, a.e, w.im, v.im);
+    } else {
+        df_acc(a.s, a.e, w.re, v.im);
+        df_acc_neg(a.s, a.e, w.im, v.re);
+    }
+}
+
 __device__ __forceinline__ Acc block_reduce(Acc a, Acc* sh) {
     for (int o = 16; o > 0; o >>= 1) {
         Acc b{__shfl_down_sync(0xffffffffu, a.s, o), __shfl_down_sync(0xffffffffu, a.e, o)};
@@ -160,11 +182,17 @@ __global__ void k_sum_partials(const double2* __restrict__ partial, uint64_t nou
 // Terms are evaluated on shared-memory tiles.  A launch covers one tile
 // layout: the chunk bits [0, L) plus a set of higher qubits (hq); every term
 // it evaluates has its X/Y qubits inside the layout, so the partner
-// amplitude alpha_{x ^ xm} is in the same tile.  Z-only terms of equal weight
-// share one integer count of odd parities per amplitude:
-//     sum_t w (-1)^popc(x & z_t) = w (N_g - 2 #{t : popc(x & z_t) odd}).
-// Terms with X/Y parts accumulate 2 Re(conj(alpha_{x^xm}) alpha_x i^ny)
-// (-1)^popc(x & zm) over the x whose lowest xm bit is clear.
+// amplitude alpha_{x ^ xm} is in the same tile.  An index is x = base + l,
+// base the tile's offset (zero at the layout's bits) and l the tile-local
+// index, so every parity splits as popc(x & z) = popc(l & z_loc) +
+// popc(base & z_out): the second part is one bit per tile, computed once by
+// the first warp.  Z-only terms of equal weight share one integer count of
+// odd parities per amplitude:
+//     sum_t w (-1)^popc(x & z_t) = w (N_g - 2 #{t : popc(x & z_t) odd});
+// masks with no bit in the layout contribute a per-tile constant.  Terms with
+// X/Y parts accumulate Re or Im of conj(alpha_{x^xm}) alpha_x, signed by
+// (-1)^popc(x & zm), over the x whose lowest xm bit is clear; the factor 2 and
+// the sign of i^ny sit in the coefficient.
 constexpr int kZW = 4;     // Z-only weight groups per launch
 constexpr int kZT = 64;    // Z-only masks per launch
 constexpr int kXT = 12;    // terms with X/Y parts per launch
@@ -175,25 +203,37 @@ struct ExpArgs {
     int L, T, kh;
     uint8_t hq[16];
     int nzg;                   // weight groups
-    int zg_end[kZW];           // end of group g in zm[]
+    int zg_loc_end[kZW];       // group g: masks [begin, zg_loc_end) touch the layout,
+    int zg_end[kZW];           //          [zg_loc_end, zg_end) lie outside it
     double zw[kZW];
-    uint64_t zm[kZT];
+    int nz;
+    uint32_t zl[kZT];          // mask bits inside the layout, at tile-local positions
+    uint64_t zo[kZT];          // mask bits outside the layout (global positions)
     int nxt;
-    uint32_t xloc[kXT];        // xm mapped to tile-local bits
-    uint64_t xz[kXT];          // zm (global)
-    int xny[kXT];
-    double xw[kXT];
+    uint32_t xloc[kXT];        // X/Y mask at tile-local positions
+    uint32_t xzl[kXT];         // Z mask inside the layout (tile-local positions)
+    uint64_t xzo[kXT];         // Z mask outside the layout
+    int ximag[kXT];            // 1: Im(conj(alpha_{x^xm}) alpha_x), 0: Re
+    double xw[kXT];            // 2 * coefficient * (+-1 from i^ny)
     double2* partial;          // one per block
 };
+
+// Amplitudes per thread in one tile (the tile has at most 2^Tmax amplitudes).
+template <class S>
+constexpr int kPer = (sizeof(S) >= 16 ? (1 << 11) : (1 << 12)) / kRThreads;
 
 template <class S>
 __global__ void __launch_bounds__(kRThreads) k_expect_tile(const __grid_constant__ ExpArgs<S> a) {
     using V = decltype(rview(S{}));
+    constexpr int PER = kPer<S>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* tile = reinterpret_cast<V*>(smem_raw);
     __shared__ Acc sh[32];
     __shared__ uint64_t offA[64], offB[64];
-    const int tid = threadIdx.x;
+    __shared__ uint32_t s_zl[kZT];       // zl with the tile's outside parity in bit 31
+    __shared__ int s_zout[kZW];          // per group: odd outside-only masks of this tile
+    __shared__ uint32_t s_xflip;         // bit k: outside parity of X/Y term k's Z mask
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid < 64) {
         uint64_t oa = 0, ob = 0;
         for (int j = 0; j < 6 && j < a.kh; ++j)
@@ -216,41 +256,89 @@ __global__ void __launch_bounds__(kRThreads) k_expect_tile(const __grid_constant
             const uint32_t h = l >> a.L;
             tile[l] = rview(a.x[base + (l & lowmask) + offA[h & 63] + offB[h >> 6]]);
         }
+        if (warp == 0) {
+            // outside parities of this tile: Z-only masks, then X/Y terms
+            uint32_t b0 = 0, b1 = 0;
+            {
+                const int k0 = lane, k1 = lane + 32;
+                const uint32_t p0 = (k0 < a.nz) ? (uint32_t)(__popcll(base & a.zo[k0]) & 1) : 0u;
+                const uint32_t p1 = (k1 < a.nz) ? (uint32_t)(__popcll(base & a.zo[k1]) & 1) : 0u;
+                if (k0 < a.nz) s_zl[k0] = a.zl[k0] | (p0 << 31);
+                if (k1 < a.nz) s_zl[k1] = a.zl[k1] | (p1 << 31);
+                b0 = __ballot_sync(0xffffffffu, p0);
+                b1 = __ballot_sync(0xffffffffu, p1);
+            }
+            const uint32_t px = (lane < a.nxt) ? (uint32_t)(__popcll(base & a.xzo[lane]) & 1) : 0u;
+            const uint32_t xb = __ballot_sync(0xffffffffu, px);
+            if (lane == 0) {
+                s_xflip = xb;
+                const uint64_t bits = ((uint64_t)b1 << 32) | b0;
+                int begin = 0;
+                for (int g = 0; g < a.nzg; ++g) {
+                    const int lo = a.zg_loc_end[g], hi = a.zg_end[g];
+                    const uint64_t m = (hi > lo) ? ((hi - lo >= 64 ? ~0ull : ((1ull << (hi - lo)) - 1ull)) << lo) : 0ull;
+                    s_zout[g] = __popcll(bits & m);
+                    begin = hi;
+                }
+                (void)begin;
+            }
+        }
         __syncthreads();
         if (a.nzg > 0) {
-            for (uint32_t l = tid; l < Tn; l += blockDim.x) {
-                const uint32_t h = l >> a.L;
-                const uint64_t x = base + (l & lowmask) + offA[h & 63] + offB[h >> 6];
-                float ph, pl;
-                abs2(tile[l], ph, pl);
-                int t0 = 0;
+            constexpr int C = PER < 8 ? PER : 8;    // amplitudes per chunk
+#pragma unroll 1
+            for (int j0 = 0; j0 < PER; j0 += C) {
+                float ph[C], pl[C];
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    const uint32_t l = tid + (uint32_t)(j0 + j) * kRThreads;
+                    if (l < Tn) abs2(tile[l], ph[j], pl[j]);
+                    else ph[j] = pl[j] = 0.f;
+                }
+                int begin = 0;
 #pragma unroll
                 for (int g = 0; g < kZW; ++g) {
                     if (g >= a.nzg) break;
-                    int odd = 0;
-                    for (int k = t0; k < a.zg_end[g]; ++k) odd += __popcll(x & a.zm[k]) & 1;
-                    const float f = (float)((a.zg_end[g] - t0) - 2 * odd);
-                    t0 = a.zg_end[g];
-                    const float p = fmul(ph, f);
-                    acc_add(zacc[g], p, __fmaf_rn(pl, f, __fmaf_rn(ph, f, -p)));
+                    int odd[C];
+#pragma unroll
+                    for (int j = 0; j < C; ++j) odd[j] = s_zout[g];
+                    for (int k = begin; k < a.zg_loc_end[g]; ++k) {
+                        const uint32_t zk = s_zl[k];
+#pragma unroll
+                        for (int j = 0; j < C; ++j)
+                            odd[j] += __popc(((uint32_t)tid + (uint32_t)(j0 + j) * kRThreads + 0x80000000u) & zk) & 1;
+                    }
+                    const int ng = a.zg_end[g] - begin;
+                    begin = a.zg_end[g];
+#pragma unroll
+                    for (int j = 0; j < C; ++j) {
+                        const float f = (float)(ng - 2 * odd[j]);
+                        const float p = fmul(ph[j], f);
+                        acc_add(zacc[g], p, __fmaf_rn(pl[j], f, __fmaf_rn(ph[j], f, -p)));
+                    }
                 }
             }
         }
         // terms with X/Y parts: one thread per pair (l, l ^ xm) with the
-        // lowest xm bit of l clear, so no lane idles
+        // lowest xm bit of l clear
+        const uint32_t xflip = s_xflip;
 #pragma unroll
         for (int k = 0; k < kXT; ++k) {
             if (k >= a.nxt) break;
-            const uint32_t xl = a.xloc[k];
+            const uint32_t xl = a.xloc[k], zlk = a.xzl[k];
             const uint32_t below = (xl & (~xl + 1u)) - 1u;
-            for (uint32_t i = tid; i < Tn / 2; i += blockDim.x) {
+            const bool signed_term = (zlk != 0u) || ((xflip >> k) & 1u);
+            const uint32_t flip = (xflip >> k) & 1u;
+            const bool im = a.ximag[k] != 0;
+#pragma unroll
+            for (int j = 0; j < PER / 2; ++j) {
+                const uint32_t i = tid + (uint32_t)j * kRThreads;
+                if (i >= Tn / 2) break;
                 const uint32_t l = ((i & ~below) << 1) | (i & below);
-                const uint32_t h = l >> a.L;
-                const uint64_t x = base + (l & lowmask) + offA[h & 63] + offB[h >> 6];
-                float hh, ll;
-                corr(tile[l ^ xl], tile[l], a.xny[k], hh, ll);
-                if (__popcll(x & a.xz[k]) & 1) { hh = -hh; ll = -ll; }
-                acc_add(xacc[k], 2.f * hh, 2.f * ll);
+                V w = tile[l ^ xl];
+                const V v = tile[l];
+                if (signed_term && ((__popc(l & zlk) ^ flip) & 1u)) w = vneg(w);
+                corr_acc(xacc[k], w, v, im);
             }
         }
         __syncthreads();
@@ -522,30 +610,42 @@ double expect_impl(qe_state* s, int nterms, const uint64_t* xm, const uint64_t* 
         for (int j = 0; j < a.kh; ++j) a.hq[j] = (uint8_t)L.high[j];
         a.ntiles = 1ull << (n - a.T);
         a.nzg = (int)p.z.size();
+        // layout bits: [0, L) and the high qubits
+        uint64_t inside = (a.L >= 64) ? ~0ull : ((1ull << a.L) - 1ull);
+        for (int j = 0; j < a.kh; ++j) inside |= 1ull << L.high[j];
+        auto to_local = [&](uint64_t m) {
+            uint32_t loc = (uint32_t)(m & ((1ull << a.L) - 1ull));
+            for (int h = 0; h < a.kh; ++h)
+                if ((m >> L.high[h]) & 1ull) loc |= 1u << (a.L + h);
+            return loc;
+        };
         int k = 0;
         for (int g = 0; g < a.nzg; ++g) {
             a.zw[g] = wv[p.z[g].first];
-            for (int t : p.z[g].second) a.zm[k++] = zm[t];
+            for (int pass = 0; pass < 2; ++pass) {          // masks touching the layout first
+                for (int t : p.z[g].second) {
+                    const bool touches = (zm[t] & inside) != 0;
+                    if (touches != (pass == 0)) continue;
+                    a.zl[k] = to_local(zm[t]);
+                    a.zo[k] = zm[t] & ~inside;
+                    ++k;
+                }
+                if (pass == 0) a.zg_loc_end[g] = k;
+            }
             a.zg_end[g] = k;
         }
+        a.nz = k;
         a.nxt = (int)p.x.size();
         for (int j = 0; j < a.nxt; ++j) {
             const int t = p.x[j];
-            uint32_t loc = 0;
-            for (int q = 0; q < n; ++q) {
-                if (!((xm[t] >> q) & 1ull)) continue;
-                int pos = -1;
-                if (q < a.L) pos = q;
-                else
-                    for (int h = 0; h < a.kh; ++h)
-                        if (L.high[h] == q) pos = a.L + h;
-                if (pos < 0) fail(QE_ERR_STATE, "expectation term outside its layout");
-                loc |= 1u << pos;
-            }
-            a.xloc[j] = loc;
-            a.xz[j] = zm[t];
-            a.xny[j] = __builtin_popcountll(xm[t] & zm[t]) & 3;
-            a.xw[j] = cf[t];
+            if (xm[t] & ~inside) fail(QE_ERR_STATE, "expectation term outside its layout");
+            a.xloc[j] = to_local(xm[t]);
+            a.xzl[j] = to_local(zm[t]);
+            a.xzo[j] = zm[t] & ~inside;
+            // Re(conj(w) v i^ny): ny = 0: +Re, 1: -Im, 2: -Re, 3: +Im
+            const int ny = __builtin_popcountll(xm[t] & zm[t]) & 3;
+            a.ximag[j] = ny & 1;
+            a.xw[j] = 2.0 * cf[t] * ((ny == 1 || ny == 2) ? -1.0 : 1.0);
         }
         a.partial = partial + i * max_grid;
         // unused partial slots of this launch read as zero

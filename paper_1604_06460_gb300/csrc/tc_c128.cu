@@ -1,0 +1,544 @@
+// Fused 5-qubit gates on complex128 states with the 5th-generation tensor
+// cores: error-free integer-digit products on the BF16 tensor pipe (the
+// splitting idea of Ozaki, Ogita, Oishi and Rump, "Error-free transformations
+// of matrix multiplication by using fast routines of matrix multiplication
+// and its applications", Numer. Algorithms 59, 2012), recombined exactly in
+// 64-bit integers.
+//
+// A 5-qubit block acts on each group of 32 amplitudes (Sec. II, gate
+// application); in real arithmetic a group is a 64-vector v = [Re x ; Im x]
+// and the block is W = [[Re U, -Im U], [Im U, Re U]], so a tile of 128 groups
+// is the product Out(128x64) = In(128x64) W^T.
+//
+// Splitting.  Row r of In (one group) is scaled by 2^(48 - E_r), where
+// 2^(E_r - 1) bounds its largest magnitude, and every value becomes the
+// integer X = round(|v| 2^(48 - E_r)) <= 2^47, written in base 256 with
+// balanced digits: X = sum_i a_i 256^(6 - i), a_1 in [0, 128], a_2..a_6 in
+// [-128, 127]; the value's sign multiplies every digit.  W's rows get scales
+// 2^F_n and digits b_j the same way on the host.  Every digit is an integer
+// of magnitude <= 128 and exact in BF16.
+//
+// Products.  C_d = sum_{i + j = d} A_i B_j^T for d = 2..8 (26 digit pairs;
+// the dropped pairs i + j >= 9 weigh below 2^-56 of the row scale), one FP32
+// tensor-memory accumulator per d.  One pair adds at most 64 * 128^2 = 2^20
+// in magnitude, so every accumulator is an exact integer below 2^23, and
+// those of d <= 5 (at most four pairs) lie in [-2^22, 2^22].
+//
+// Recombination (per output).  With the integer
+//   Y = C_2 2^40 + C_3 2^32 + C_4 2^24 + C_5 2^16 + C_6 2^8 + round(C_7 + C_8 / 256),
+// |Y| < 2^61, the output is Y 2^(E_r + F_n - 56): one rounding of Y to a
+// double plus an exact exponent shift.  C_2..C_5 become integers with the
+// FP32 magic-number addition (C + 1.5 * 2^23 is exact for |C| <= 2^22 and its
+// bit pattern minus that of 1.5 * 2^23 is C); C_6 and the last term with a
+// float-to-integer conversion.
+//
+// Accuracy: the splitting rounds each input to 2^-48 of its row scale and each
+// matrix entry to 2^-48 of its row's; the result is within a few units of
+// 2^-48 of the group norm, with no FP64 arithmetic but the final conversion.
+// Rows whose largest magnitude is below 2^-920 are flushed to zero.
+//
+// Schedule: sixteen worker warps (four threads per group row) split and
+// recombine, one more warp issues the MMAs.  The 64 outputs of a row are computed as two halves of 32 (16
+// complex columns each) into two tensor-memory accumulator sets X and Y, so
+// the MMAs of one half overlap the epilogue of the other and the splitting of
+// the next tile:
+//   workers: epilogue(t, X) | split(t+1) | epilogue(t, Y) | ...
+//   MMA warp:   MMA(t, Y)   |   ...      | MMA(t+1, X)    | MMA(t+1, Y) ...
+// (104 MMAs of 128x32x16 per half).  The raw amplitudes of tile t+2 stream
+// into a padded staging buffer with cp.async meanwhile.  Hand-offs use
+// mbarriers (digits ready, set Y free: workers arrive; set X / Y done:
+// tcgen05.commit); every wait has an iteration limit and the workers leave
+// their loop together when any of them times out.
+#include <cmath>
+#include <cstring>
+
+#include "qe_arith.cuh"
+#include "qe_internal.h"
+#include "qe_tc.cuh"
+
+namespace qe {
+
+namespace {
+
+using tc::mbar_wait;
+using tc::smem_u32;
+
+constexpr int kWorkers = 512;                // 16 warps: splitting and epilogue
+constexpr int kOzThreads = kWorkers + 32;     // + 1 warp issuing the MMAs
+constexpr int kRows = 128;                    // groups per tile (MMA M)
+constexpr int kK = 64;                        // real K
+constexpr int kN = 64;                        // real N (two halves of 32)
+constexpr int kNH = 32;                       // MMA N
+constexpr int kDigits = 6;
+constexpr int kAcc = 7;                       // accumulators for d = 2..8
+constexpr uint32_t kTmemCols = 512;           // two accumulator sets of 7 x 32 columns
+constexpr uint32_t kSetY = 256;               // column of the second set
+constexpr uint32_t kSliceA = kRows * 128;     // bytes of one digit slice of In (bf16, 128 B per row)
+constexpr uint32_t kSliceB = kN * 128;        // bytes of one digit slice of W
+constexpr uint32_t kStageRow = 32 * 16 + 16;  // staged row of 32 complex128, padded by 16 bytes
+constexpr uint32_t kStackB = kDigits * kNH * 128; // bytes of one half's stack of the six W' digit slices
+constexpr int kFlushExp = 100;                // biased exponent below which a row is flushed
+
+struct OzArgs {
+    double2* x;
+    uint64_t ntiles;
+    int L, kh;
+    uint8_t hq[8];
+    uint8_t gpos[5];
+    uint32_t* status;
+    long long spin_limit;
+    const uint16_t* B;      // [6][64][64] bf16 digits of W': slice j, row n', column k
+    const int* F;           // [64] row scale exponents of W (original row order)
+};
+
+// Byte offset of the 16-byte chunk `ch` (8 bf16 along K) of row r in a
+// K-major operand with 128-byte rows, 128-byte swizzle.
+__device__ __forceinline__ uint32_t sw128_chunk(int r, int ch) {
+    return (uint32_t)(r >> 3) * 1024u + (uint32_t)(r & 7) * 128u + (uint32_t)((ch ^ (r & 7)) * 16);
+}
+
+// D[128 x N] (+)= A[128 x 16] B[N x 16]^T, bf16 inputs, f32 accumulators.
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init_count(uint64_t* mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+__device__ __forceinline__ void workers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kWorkers) : "memory"); }
+// True on every worker thread when p holds on any of them (a barrier of the
+// workers that all reach, so a timed-out wait ends the loop on all of them).
+__device__ __forceinline__ bool workers_any(bool p) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred a, b;\n\t"
+        "setp.ne.u32 a, %1, 0;\n\t"
+        "bar.red.or.pred b, 2, %2, a;\n\t"
+        "selp.u32 %0, 1, 0, b;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)p), "n"(kWorkers)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ long long mad_wide(int a, int b, long long c) {
+    long long d;
+    asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t biased_exp(double v) { return ((uint32_t)__double2hiint(v) >> 20) & 0x7FFu; }
+
+// The six signed digits of v (as floats) for a row whose shift base is
+// base_s = (largest biased exponent of the row) + 5: q = M53 >> (base_s - e),
+// X = (q + 1) >> 1, and the balanced digits come from Z = X + 0x8080808080.
+__device__ __forceinline__ void split_digits(double v, uint32_t base_s, float d[kDigits]) {
+    const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
+    const uint32_t e = (hi >> 20) & 0x7FFu;
+    const uint32_t s = (e == 0u) ? 64u : base_s - e;              // >= 5
+    const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;
+    uint32_t ql, qh;
+    if (s < 32u) {
+        ql = __funnelshift_r(lo, mh, s);
+        qh = mh >> s;
+    } else {
+        ql = (s < 64u) ? (mh >> (s - 32u)) : 0u;
+        qh = 0u;
+    }
+    const uint64_t Z = ((((uint64_t)qh << 32) | ql) + 0x10101010101ull) >> 1;
+    const uint32_t zl = (uint32_t)Z, zh = (uint32_t)(Z >> 32);
+    const uint32_t sign = hi & 0x80000000u;
+    const float sf = __uint_as_float(0x3F800000u | sign);
+    const float c0 = __uint_as_float(0x4B000000u | (sign ^ 0x80000000u));    // -sign * 2^23
+    const float c1 = __uint_as_float(0x4B000080u | (sign ^ 0x80000000u));    // -sign * (2^23 + 128)
+    d[0] = __fmaf_rn(__uint_as_float(__byte_perm(zh, 0x4B000000u, 0x7651u)), sf, c0);
+    d[1] = __fmaf_rn(__uint_as_float(__byte_perm(zh, 0x4B000000u, 0x7650u)), sf, c1);
+    d[2] = __fmaf_rn(__uint_as_float(__byte_perm(zl, 0x4B000000u, 0x7653u)), sf, c1);
+    d[3] = __fmaf_rn(__uint_as_float(__byte_perm(zl, 0x4B000000u, 0x7652u)), sf, c1);
+    d[4] = __fmaf_rn(__uint_as_float(__byte_perm(zl, 0x4B000000u, 0x7651u)), sf, c1);
+    d[5] = __fmaf_rn(__uint_as_float(__byte_perm(zl, 0x4B000000u, 0x7650u)), sf, c1);
+}
+
+// Output value from the seven accumulators (raw FP32 bits); eadj = (E_r +
+// F_n - 56) << 20 shifts the exponent.
+__device__ __forceinline__ double recombine(const uint32_t c[kAcc], int eadj) {
+    const float M = 12582912.0f;   // 1.5 * 2^23; bits 0x4B400000
+    const uint32_t u2 = __float_as_uint(__fadd_rn(__uint_as_float(c[0]), M));
+    const uint32_t u3 = __float_as_uint(__fadd_rn(__uint_as_float(c[1]), M));
+    const int c4 = (int)(__float_as_uint(__fadd_rn(__uint_as_float(c[2]), M)) - 0x4B400000u);
+    const int c5 = (int)(__float_as_uint(__fadd_rn(__uint_as_float(c[3]), M)) - 0x4B400000u);
+    const int c6 = __float2int_rn(__uint_as_float(c[4]));
+    const int c78 = __float2int_rn(__fmaf_rn(__uint_as_float(c[6]), 0.00390625f, __uint_as_float(c[5])));
+    const int H = (int)(u2 * 256u + u3 - 257u * 0x4B400000u);     // C_2 * 256 + C_3, |H| < 2^29
+    long long Y = mad_wide(c6, 256, (long long)c78);
+    Y = mad_wide(c5, 1 << 16, Y);
+    Y = mad_wide(c4, 1 << 24, Y);
+    Y += (long long)H << 32;
+    const double y = __ll2double_rn(Y);
+    const int hi = __double2hiint(y);
+    return __hiloint2double(hi == 0 ? 0 : hi + eadj, __double2loint(y));
+}
+
+// The MMA-issuing thread.  The accumulators of one half lie side by side,
+// C_d at column 32 (d - 2), and each half's W' digit slices are stacked along
+// N (rows 32 (j - 1) + m), so one MMA of A_i against the stacked slices
+// j0..j1 writes C_{i + j0} .. C_{i + j1} at once: the digit products form a
+// convolution.  Per K-step and half: (1,1) and (2,1..6) start the sums, then
+// (1,2..6), (3,1..5), (4,1..4), (5,1..3), (6,1..2) add to them (26 pairs in 7
+// MMAs).  Per tile: wait for the digit slices, issue the first half into set
+// X, wait until set Y is free, issue the second half into Y; each half is
+// committed to its own mbarrier.
+__device__ __noinline__ void issue_mmas(const OzArgs& a, uint32_t tmem, uint32_t a0, uint32_t b0, uint64_t* mbA,
+                                        uint64_t* mbYfree, uint64_t* mbX, uint64_t* mbY) {
+    // (i, j0, j1, starts) in issue order
+    constexpr int kI[7] = {1, 2, 1, 3, 4, 5, 6};
+    constexpr int kJ0[7] = {1, 1, 2, 1, 1, 1, 1};
+    constexpr int kJ1[7] = {1, 6, 6, 5, 4, 3, 2};
+    uint32_t pa = 0, pyf = 0;
+    bool first = true;
+    for (uint64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        if (!mbar_wait(smem_u32(mbA), pa, a.spin_limit)) {
+            atomicExch(a.status, 1u);
+            return;
+        }
+        pa ^= 1u;
+        for (int hh = 0; hh < 2; ++hh) {
+            if (hh == 1 && !first) {
+                if (!mbar_wait(smem_u32(mbYfree), pyf, a.spin_limit)) {
+                    atomicExch(a.status, 1u);
+                    return;
+                }
+                pyf ^= 1u;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t set = tmem + (hh ? kSetY : 0u);
+            const uint32_t stack = b0 + (uint32_t)hh * kStackB;
+#pragma unroll
+            for (int ks = 0; ks < kK / 16; ++ks) {
+#pragma unroll
+                for (int m = 0; m < 7; ++m) {
+                    const int i = kI[m], j0 = kJ0[m], j1 = kJ1[m];
+                    const uint32_t nn = (uint32_t)(j1 - j0 + 1) * kNH;
+                    const uint64_t da = tc::sdesc_sw128(a0 + (uint32_t)(i - 1) * kSliceA + 32u * ks);
+                    const uint64_t db = tc::sdesc_sw128(stack + (uint32_t)(j0 - 1) * (kNH * 128u) + 32u * ks);
+                    const uint32_t dt = set + (uint32_t)(i + j0 - 2) * kNH;
+                    mma_bf16(dt, da, db, tc::idesc(1u, nn, kRows), (ks > 0 || m > 1) ? 1u : 0u);
+                }
+            }
+            tc::mma_commit(hh ? mbY : mbX);
+        }
+        first = false;
+    }
+}
+
+__global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_constant__ OzArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    unsigned char* sA = base;                                   // 6 digit slices of In
+    unsigned char* sB = sA + kDigits * kSliceA;                 // per half: the 6 W' digit slices stacked
+    unsigned char* stage = sB + kDigits * kSliceB;              // raw amplitudes of one tile
+    // mbarriers: A digits ready (workers arrive), accumulator set Y free
+    // (workers arrive), MMAs into set X / set Y complete (tcgen05.commit)
+    __shared__ __align__(8) uint64_t mbA, mbYfree, mbX, mbY;
+    __shared__ uint32_t tmem_base;
+    __shared__ uint64_t hoff[32];
+    __shared__ uint32_t cpos[32];
+    __shared__ uint64_t coloff[32];
+    __shared__ int sF20[kN];
+    __shared__ uint32_t semax[4][kRows];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // W' digits into their swizzled operand layout; W row scales
+#pragma unroll 1
+    for (int i = tid; i < kDigits * kN * 8; i += blockDim.x) {
+        const int j = i / (kN * 8), n = (i / 8) % kN, ch = i % 8;
+        const uint4 v = *reinterpret_cast<const uint4*>(a.B + ((size_t)(j * kN + n) * kK + ch * 8));
+        const int hh = n / kNH, m = n % kNH;
+        *reinterpret_cast<uint4*>(sB + hh * kStackB + sw128_chunk(j * kNH + m, ch)) = v;
+    }
+    if (tid < kN) sF20[tid] = a.F[tid] * (1 << 20);
+    if (tid < (1 << a.kh)) {
+        uint64_t o = 0;
+        for (int j = 0; j < a.kh; ++j)
+            if ((tid >> j) & 1) o |= 1ull << a.hq[j];
+        hoff[tid] = o;
+    }
+    if (tid < 32) {
+        uint32_t o = 0;
+        for (int j = 0; j < 5; ++j)
+            if ((tid >> j) & 1) o |= 1u << a.gpos[j];
+        cpos[tid] = o;
+    }
+    if (tid == 0) {
+        mbar_init_count(&mbA, kWorkers);
+        mbar_init_count(&mbYfree, kWorkers);
+        mbar_init_count(&mbX, 1);
+        mbar_init_count(&mbY, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == kWorkers / 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid < 32) {
+        const uint32_t l = cpos[tid];
+        coloff[tid] = 16ull * ((l & ((1u << a.L) - 1u)) + hoff[l >> a.L]);   // bytes
+    }
+    __syncthreads();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == kWorkers / 32) {
+        // ---------------------------------------------------- MMA issuer
+        if (lane == 0) issue_mmas(a, tmem, smem_u32(sA), smem_u32(sB), &mbA, &mbYfree, &mbX, &mbY);
+        __syncwarp();
+    } else {
+        // ------------------------------------------ splitting and epilogue
+        const uint32_t gmask = cpos[31];
+        const int r = ((warp & 3) << 5) | lane;   // group row = TMEM lane
+        const int qq = warp >> 2;                 // complex columns [8 qq, 8 qq + 8)
+        uint32_t lrow = 0;
+        {
+            int j = 0;
+            for (int b = 0; b < 12; ++b)
+                if (!((gmask >> b) & 1u)) lrow |= (((uint32_t)r >> (j++)) & 1u) << b;
+        }
+        const uint64_t rowoff = 16ull * ((lrow & ((1u << a.L) - 1u)) + hoff[lrow >> a.L]);   // bytes
+        char* const xb = reinterpret_cast<char*>(a.x);
+        auto tile_base = [&](uint64_t t) { return xb + 16ull * insert_zero_bits(t << a.L, a.hq, a.kh) + rowoff; };
+        const uint32_t my_stage = smem_u32(stage + r * kStageRow + qq * 128);
+        auto prefetch = [&](uint64_t t) {
+            const char* gb = tile_base(t);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) cp_async16(my_stage + 16u * c, gb + coloff[8 * qq + c]);
+            cp_async_commit();
+        };
+        // digits of this thread's 16 values into the six operand slices
+        // (chunk qq: real parts, chunk 4 + qq: imaginary parts); returns
+        // (E_r - 56) << 20
+        auto split_tile = [&]() -> int {
+            cp_async_wait_all();
+            const double2* srow = reinterpret_cast<const double2*>(stage + r * kStageRow + qq * 128);
+            uint32_t em = 0;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const double2 v = srow[c];
+                em = max(em, max(biased_exp(v.x), biased_exp(v.y)));
+            }
+            semax[qq][r] = em;
+            workers_sync();
+            em = max(max(semax[0][r], semax[1][r]), max(semax[2][r], semax[3][r]));
+            const uint32_t base_s = (em < (uint32_t)kFlushExp) ? 0x10000u : em + 5u;
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {
+                uint32_t w[kDigits][4];      // packed bf16 pairs: slice i, values 2p, 2p + 1
+#pragma unroll
+                for (int p2 = 0; p2 < 4; ++p2) {
+                    float d0[kDigits], d1[kDigits];
+                    const double2 va = srow[2 * p2], vb = srow[2 * p2 + 1];
+                    split_digits(part ? va.y : va.x, base_s, d0);
+                    split_digits(part ? vb.y : vb.x, base_s, d1);
+#pragma unroll
+                    for (int i = 0; i < kDigits; ++i) w[i][p2] = pack_bf16x2(d0[i], d1[i]);
+                }
+                const uint32_t off = sw128_chunk(r, part * 4 + qq);
+#pragma unroll
+                for (int i = 0; i < kDigits; ++i)
+                    *reinterpret_cast<uint4*>(sA + i * kSliceA + off) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;");
+            return ((int)em - 1021 - 56) * (1 << 20);
+        };
+        // outputs of accumulator set hh: this thread's 4 complex columns
+        // 16 hh + 4 qq + [0, 4); set column m < 16 is the real part of complex
+        // column 16 hh + m, m >= 16 the imaginary part of 16 hh + m - 16
+        const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        auto epilogue = [&](int hh, char* gb, int eterm) {
+            const uint32_t set = lane_base + (hh ? kSetY : 0u);
+            const int m0 = 4 * qq;
+#pragma unroll
+            for (int u0 = 0; u0 < 4; u0 += 2) {
+                uint32_t re[kAcc][2], im[kAcc][2];
+#pragma unroll
+                for (int k = 0; k < kAcc; ++k) {
+                    const uint32_t ta = set + (uint32_t)(k * kNH + m0 + u0);
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+                                 : "=r"(re[k][0]), "=r"(re[k][1])
+                                 : "r"(ta));
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+                                 : "=r"(im[k][0]), "=r"(im[k][1])
+                                 : "r"(ta + 16u));
+                }
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int c = 16 * hh + m0 + u0 + u;
+                    uint32_t cr[kAcc], ci[kAcc];
+#pragma unroll
+                    for (int k = 0; k < kAcc; ++k) {
+                        cr[k] = re[k][u];
+                        ci[k] = im[k][u];
+                    }
+                    const double yr = recombine(cr, eterm + sF20[c]);
+                    const double yi = recombine(ci, eterm + sF20[32 + c]);
+                    *reinterpret_cast<double2*>(gb + coloff[c]) = make_double2(yr, yi);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+        };
+        uint32_t px = 0, py = 0;
+        uint64_t t = blockIdx.x;
+        int eterm = 0;
+        if (t < a.ntiles) {
+            prefetch(t);
+            eterm = split_tile();
+            mbar_arrive(&mbA);
+            if (t + gridDim.x < a.ntiles) prefetch(t + gridDim.x);
+        }
+        for (; t < a.ntiles; t += gridDim.x) {
+            const uint64_t tn = t + gridDim.x;
+            char* gb = tile_base(t);
+            // outputs of the first half (set X)
+            if (workers_any(!mbar_wait(smem_u32(&mbX), px, a.spin_limit))) {
+                atomicExch(a.status, 1u);
+                break;
+            }
+            px ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            epilogue(0, gb, eterm);
+            // second-half MMAs done: the digit slices are free
+            if (workers_any(!mbar_wait(smem_u32(&mbY), py, a.spin_limit))) {
+                atomicExch(a.status, 1u);
+                break;
+            }
+            py ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            int eterm_next = 0;
+            if (tn < a.ntiles) {
+                eterm_next = split_tile();
+                mbar_arrive(&mbA);
+                if (tn + gridDim.x < a.ntiles) prefetch(tn + gridDim.x);
+            }
+            epilogue(1, gb, eterm);
+            mbar_arrive(&mbYfree);
+            eterm = eterm_next;
+        }
+        cp_async_wait_all();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == kWorkers / 32) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    }
+}
+
+// Balanced base-256 digits of one row of W (host side, same rule as the
+// device splitting): returns the scale exponent F and fills digits[j][k].
+int split_row_host(const double* w, int16_t digits[kDigits][kK]) {
+    int emax = 0;
+    for (int k = 0; k < kK; ++k) {
+        uint64_t b;
+        std::memcpy(&b, &w[k], 8);
+        emax = std::max(emax, (int)((b >> 52) & 0x7FF));
+    }
+    if (emax < kFlushExp) {
+        std::memset(digits, 0, sizeof(int16_t) * kDigits * kK);
+        return 0;
+    }
+    const int F = emax - 1021;
+    for (int k = 0; k < kK; ++k) {
+        const uint64_t X = (uint64_t)std::llround(std::ldexp(std::fabs(w[k]), 48 - F));   // <= 2^47, exact scaling
+        const uint64_t Z = X + 0x8080808080ull;
+        const int sg = std::signbit(w[k]) ? -1 : 1;
+        digits[0][k] = (int16_t)(sg * (int)(Z >> 40));
+        for (int j = 1; j < kDigits; ++j) digits[j][k] = (int16_t)(sg * ((int)((Z >> (8 * (5 - j))) & 0xFF) - 128));
+    }
+    return F;
+}
+
+}  // namespace
+
+// Apply a 5-qubit block to a complex128 state with the tensor cores.
+void launch_gate_tc5_c128(qe_state* s, const int* qubits, const cd* U) {
+    if (s->dtype != QE_C128) fail(QE_ERR_UNSUPPORTED, "this tensor-core path is for complex128 states");
+    if (s->n < 12) fail(QE_ERR_UNSUPPORTED, "tensor-core gates need n >= 12");
+    const tc::Geometry g = tc::tile_geometry(qubits);
+    OzArgs a;
+    a.x = reinterpret_cast<double2*>(s->d);
+    a.L = g.L;
+    a.kh = g.kh;
+    std::memcpy(a.hq, g.hq, sizeof(a.hq));
+    std::memcpy(a.gpos, g.gpos, sizeof(a.gpos));
+    a.ntiles = 1ull << (s->n - 12);
+    // W = [[Re U, -Im U], [Im U, Re U]], row n (output), column k (input)
+    struct HostW {
+        uint16_t B[kDigits * kN * kK];
+        int F[kN];
+    };
+    static thread_local HostW hw;
+    for (int n = 0; n < kN; ++n) {
+        double w[kK];
+        for (int k = 0; k < kK; ++k) {
+            const cd u = U[(n & 31) * 32 + (k & 31)];
+            w[k] = (n < 32) ? ((k < 32) ? u.real() : -u.imag()) : ((k < 32) ? u.imag() : u.real());
+        }
+        int16_t dg[kDigits][kK];
+        hw.F[n] = split_row_host(w, dg);
+        // operand row n' of W' (two halves of 32 rows, see the epilogue)
+        const int c = n & 31, hh = c >> 4, m = (c & 15) + ((n >> 5) << 4);
+        const int np = hh * kNH + m;
+        for (int j = 0; j < kDigits; ++j)
+            for (int k = 0; k < kK; ++k) {
+                const float f = (float)dg[j][k];       // |digit| <= 128: exact in bf16
+                uint32_t bits;
+                std::memcpy(&bits, &f, 4);
+                hw.B[((size_t)j * kN + np) * kK + k] = (uint16_t)(bits >> 16);
+            }
+    }
+    char* scr = (char*)ensure_scratch(s, 256 + sizeof(HostW));
+    uint32_t* status = (uint32_t*)scr;
+    QE_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), s->stream));
+    QE_CUDA(cudaMemcpyAsync(scr + 256, &hw, sizeof(HostW), cudaMemcpyHostToDevice, s->stream));
+    a.status = status;
+    a.B = reinterpret_cast<const uint16_t*>(scr + 256);
+    a.F = reinterpret_cast<const int*>(scr + 256 + sizeof(hw.B));
+    a.spin_limit = 1ll << 26;
+    const size_t smem = 1024 + (size_t)kDigits * (kSliceA + kSliceB) + (size_t)kRows * kStageRow;
+    QE_CUDA(cudaFuncSetAttribute(k_gate_tc5_c128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const uint64_t grid = std::min<uint64_t>(a.ntiles, (uint64_t)num_sms());
+    {
+        Launch Lc(s, "gate_tc_k5_c128", 2.0 * dim(s) * amp_bytes(s));
+        k_gate_tc5_c128<<<(unsigned)grid, kOzThreads, smem, s->stream>>>(a);
+        QE_CUDA(cudaGetLastError());
+    }
+    uint32_t host_status = 0;
+    QE_CUDA(cudaMemcpyAsync(&host_status, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s->stream));
+    QE_CUDA(cudaStreamSynchronize(s->stream));
+    if (host_status) fail(QE_ERR_TIMEOUT, "tensor-core gate: an mbarrier wait exceeded its limit");
+}
+
+}  // namespace qe

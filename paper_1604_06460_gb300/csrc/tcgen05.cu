@@ -28,10 +28,14 @@
 
 #include "qe_arith.cuh"
 #include "qe_internal.h"
+#include "qe_tc.cuh"
 
 namespace qe {
 
 namespace {
+
+using tc::smem_u32;
+using tc::mbar_wait;
 
 constexpr int kTcThreads = 256;
 constexpr int kRows = 128;           // groups per tile (MMA M)
@@ -50,10 +54,6 @@ struct TcArgs {
     const float* W;           // [2][kN * kK]: hi, lo parts of W, row n, column k
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
 // Round an FP32 value to TF32 (10 explicit mantissa bits, nearest, ties
 // away from zero) with integer instructions.
 __device__ __forceinline__ float tf32_hi(float x) {
@@ -71,22 +71,7 @@ __device__ __forceinline__ uint32_t sw128_offset(int r, int k, int rows) {
            chunk * 16u + (uint32_t)(kk & 3) * 4u;
 }
 
-// Shared-memory matrix descriptor: start >> 4, leading offset (unused for
-// swizzled K-major) 16 bytes, stride between 8-row groups 1024 bytes,
-// descriptor version 1, layout SWIZZLE_128B (2).
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)(16u >> 4) << 16;
-    d |= (uint64_t)(1024u >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
-
-// Instruction descriptor: D f32, A/B tf32, both K-major, N = 64, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kN >> 3) << 17) |
-                            ((uint32_t)(kRows >> 4) << 24);
+constexpr uint32_t kIdesc = tc::idesc(2u, kN, kRows);   // tf32 x tf32 -> f32, M = 128, N = 64
 
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
     asm volatile(
@@ -94,20 +79,6 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
         "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, long long limit) {
-    for (long long i = 0; i < limit; ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.b32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(mbar), "r"(phase));
-        if (done) return true;
-    }
-    return false;
 }
 
 __global__ void __launch_bounds__(kTcThreads) k_gate_tc5(const __grid_constant__ TcArgs a) {
@@ -145,8 +116,7 @@ __global__ void __launch_bounds__(kTcThreads) k_gate_tc5(const __grid_constant__
     }
     if (tid == 0) {
         s_abort = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
-        asm volatile("fence.mbarrier_init.release.cluster;");
+        tc::mbar_init(&mbar);
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -225,13 +195,12 @@ __global__ void __launch_bounds__(kTcThreads) k_gate_tc5(const __grid_constant__
             for (int ks = 0; ks < kK / 8; ++ks) {
                 const uint32_t aoff = (uint32_t)(ks >> 2) * kRows * 128u + (uint32_t)(ks & 3) * 32u;
                 const uint32_t boff = (uint32_t)(ks >> 2) * kN * 128u + (uint32_t)(ks & 3) * 32u;
-                mma_tf32(tmem, sdesc(ah + aoff), sdesc(wh + boff), acc);
+                mma_tf32(tmem, tc::sdesc_sw128(ah + aoff), tc::sdesc_sw128(wh + boff), acc);
                 acc = 1;
-                mma_tf32(tmem, sdesc(ah + aoff), sdesc(wl + boff), 1);
-                mma_tf32(tmem, sdesc(al + aoff), sdesc(wh + boff), 1);
+                mma_tf32(tmem, tc::sdesc_sw128(ah + aoff), tc::sdesc_sw128(wl + boff), 1);
+                mma_tf32(tmem, tc::sdesc_sw128(al + aoff), tc::sdesc_sw128(wh + boff), 1);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&mbar)));
+            tc::mma_commit(&mbar);
         }
         // prefetch the next tile while the tensor cores work
         const uint64_t tn = t + gridDim.x;
@@ -291,30 +260,12 @@ void launch_gate_tc5(qe_state* s, const int* qubits, const cd* U) {
     if (s->dtype != QE_C64) fail(QE_ERR_UNSUPPORTED, "tensor-core gates are complex64 only");
     if (s->n < 12) fail(QE_ERR_UNSUPPORTED, "tensor-core gates need n >= 12");
     TcArgs a;
-    // tile geometry: 12 local bits, the 5 gate qubits among them
-    int srt[5];
-    for (int j = 0; j < 5; ++j) srt[j] = qubits[j];
-    std::sort(srt, srt + 5);
-    int L = -1, kh = 0;
-    for (int l = 12; l >= 0; --l) {
-        int h = 0;
-        for (int j = 0; j < 5; ++j) h += srt[j] >= l;
-        if (l + h <= 12) { L = l; kh = h; break; }
-    }
-    if (L < 0) fail(QE_ERR_ARG, "no tensor-core tile geometry");
+    const tc::Geometry g = tc::tile_geometry(qubits);
     a.x = reinterpret_cast<float2*>(s->d);
-    a.L = L;
-    a.kh = kh;
-    int h = 0;
-    for (int j = 0; j < 5; ++j)
-        if (srt[j] >= L) a.hq[h++] = (uint8_t)srt[j];
-    for (int j = 0; j < 5; ++j) {
-        int q = qubits[j], pos = q;
-        if (q >= L)
-            for (int i = 0; i < kh; ++i)
-                if (a.hq[i] == q) pos = L + i;
-        a.gpos[j] = (uint8_t)pos;
-    }
+    a.L = g.L;
+    a.kh = g.kh;
+    std::memcpy(a.hq, g.hq, sizeof(a.hq));
+    std::memcpy(a.gpos, g.gpos, sizeof(a.gpos));
     a.ntiles = 1ull << (s->n - 12);
     // W = [[Re U, -Im U], [Im U, Re U]], row n (output), column k (input)
     static thread_local float W[2 * kN * kK];

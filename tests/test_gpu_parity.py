@@ -360,6 +360,28 @@ def test_general_pauli_terms(qe):
     assert abs(e - oracle.expectation(psi, xm, zm, cf)) < 1e-12
 
 
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-12), ("c64", 1e-5)])
+def test_expectation_parities_outside_the_tile(qe, dtype, tol):
+    # n = 16 > the 11/12-qubit tile: nearest-neighbour ZZ masks inside,
+    # straddling and entirely outside the tile; Z strings on high qubits only;
+    # X/Y terms whose Z parts lie inside, outside, or both
+    n = 16
+    xm, zm, cf = [], [], []
+    for i in range(n - 1):
+        xm.append(0); zm.append((1 << i) | (1 << (i + 1))); cf.append(1.0)
+    for mask in (1 << 15, (1 << 13) | (1 << 15), (1 << 2) | (1 << 12) | (1 << 14), 0b111 << 11):
+        xm.append(0); zm.append(mask); cf.append(-0.3)
+    for q, z in ((0, 1 << 14), (3, (1 << 4) | (1 << 15)), (5, 1 << 5), (12, 1 << 1), (15, (1 << 3) | (1 << 13))):
+        xm.append(1 << q); zm.append(z); cf.append(0.45)
+    for q in range(n):
+        xm.append(1 << q); zm.append(0); cf.append(0.7)
+    xm, zm, cf = (np.array(xm, dtype=np.uint64), np.array(zm, dtype=np.uint64), np.array(cf))
+    psi = I.random_state(n, 44)
+    with make(qe, n, dtype, psi=psi) as st:
+        e = st.expectation(xm, zm, cf)
+    assert abs(e - oracle.expectation(psi, xm, zm, cf)) < tol
+
+
 @pytest.mark.parametrize("qubits", [[0], [3, 0], [11, 2, 6], [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11]])
 def test_probs(qe, qubits):
     n = 12
@@ -427,6 +449,79 @@ def test_tensor_core_fused_circuit_c64(qe):
         got = st.get().astype(np.complex128)
     assert np.max(np.abs(got - ref)) < 2e-5
     assert oracle.fidelity(ref, got) > 1 - 1e-8
+
+
+# ------------------------------------------ tensor cores (complex128, k = 4, 5)
+# Exact integer-digit products on the BF16 tensor pipe: inputs and matrix
+# entries are rounded to 2^-48 of their row scale, so the FP64 bar holds.
+@pytest.mark.parametrize("qubits", [[0, 1, 2, 3, 4], [10, 11, 12, 13, 14], [4, 0, 15, 7, 12],
+                                    [2, 9, 5, 14], [15, 14, 13, 12], [6, 3, 11, 1, 8]])
+def test_tensor_core_blocks_c128(qe, qubits):
+    n = 16
+    U = rand_unitary(1 << len(qubits), np.random.default_rng(100 + sum(qubits)))
+    psi = I.random_state(n, 13)
+    with make(qe, n, "c128", psi=psi, max_k=5) as st:
+        st.reset_stats()
+        st.profile(True)
+        st.apply_gate(qubits, U)
+        got = st.get()
+        prof = st.profile_read()
+        st.profile(False)
+        launches = st.stats()["launches"]
+    ref = oracle.apply_gate(psi, qubits, U)
+    assert launches == 1
+    assert prof.get("gate_tc_k5_c128", (0,))[0] == 1
+    close(got, ref)
+
+
+def test_tensor_core_c128_special_values(qe):
+    # a basis state (all but one amplitude zero), amplitudes that are powers of
+    # two (the splitting's binade edges), +-1 entries, and rows below the flush
+    # threshold next to ordinary ones
+    n = 14
+    qubits = [1, 3, 5, 7, 9]
+    U = rand_unitary(32, np.random.default_rng(5))
+    for case in range(3):
+        if case == 0:
+            psi = np.zeros(1 << n, dtype=np.complex128)
+            psi[12345] = 1.0
+        elif case == 1:
+            rng = np.random.default_rng(8)
+            psi = (np.exp2(-rng.integers(1, 30, 1 << n)) * rng.choice([-1, 1], 1 << n)
+                   + 1j * np.exp2(-rng.integers(1, 30, 1 << n)) * rng.choice([-1, 1], 1 << n))
+            psi[::97] = 1.0 - 1.0j
+        else:
+            psi = I.random_state(n, 21)
+            psi[: 1 << 10] *= 1e-290         # groups far below the flush threshold
+            psi[1 << 10: 1 << 11] *= 1e-200  # small but kept
+        with make(qe, n, "c128", psi=psi, max_k=5) as st:
+            st.apply_gate(qubits, U)
+            got = st.get()
+        ref = oracle.apply_gate(psi, qubits, U)
+        scale = max(1.0, float(np.max(np.abs(psi))))
+        assert np.max(np.abs(got - ref)) <= 1e-12 * scale, case
+        if case == 2:
+            # the kept small groups keep their relative accuracy
+            blk = slice(1 << 10, 1 << 11)
+            rel = np.max(np.abs(got[blk] - ref[blk])) / np.max(np.abs(ref[blk]))
+            assert rel < 1e-12
+
+
+def test_tensor_core_fused_circuit_c128(qe):
+    n = 14
+    gates = I.random_circuit(n, 8, seed=22)
+    ref = oracle.zero_state(n)
+    for g in gates:
+        ref = oracle.apply_gate(ref, g.qubits, g.matrix)
+    with make(qe, n, "c128", max_k=5) as st:
+        st.profile(True)
+        for g in gates:
+            st.apply(g)
+        got = st.get()
+        prof = st.profile_read()
+        st.profile(False)
+    assert prof.get("gate_tc_k5_c128", (0,))[0] > 0
+    close(got, ref)
 
 
 @pytest.mark.parametrize("dtype,tol", [("c128", 1e-12), ("c64", 1e-5)])
