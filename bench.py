@@ -245,8 +245,8 @@ def main():
     qe.load()
     n, depth = args.n, args.depth
     st = qe.State(n, "c128")
-    st.set_policy(qe.POLICY_AUTO, args.max_k or 2)
-    max_k = args.max_k or 2
+    max_k = args.max_k or 5
+    st.set_policy(qe.POLICY_AUTO, max_k)
     gates = I.random_circuit(n, depth, seed=0)
     reg = list(range(min(16, n)))
     cconst = I.random_constant(len(reg), seed=1)
@@ -306,7 +306,9 @@ def main():
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "df64",
-        "arith": "complex128 storage, double-float (f32 pair) arithmetic on the FP32 pipes; FP64 only in reduction sums",
+        "arith": ("complex128 storage; 4-5 qubit blocks as exact fp16-digit products on the tensor cores "
+                  "(48-bit splitting, int64 recombination), smaller blocks and the FFT in double-float "
+                  "(f32 pair) arithmetic; FP64 only in reduction sums and conversions"),
         "data": "synthetic",
         "config": {"workload": workload_desc(n, depth, max_k), "n": n, "depth": depth, "max_k": max_k,
                    "parallelism": "replicas" if world > 1 else "single",

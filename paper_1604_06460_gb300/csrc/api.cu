@@ -403,13 +403,16 @@ int qe_alloc_state(int n, int dtype, void* dev_ptr, size_t bytes, void* stream, 
     s->n = n;
     s->dtype = dtype;
     s->stream = (cudaStream_t)stream;
-    s->max_k = dtype == QE_C128 ? 2 : 4;
     const char* ar = std::getenv("QE_C128_ARITH");
     s->c128_native = (ar && std::strcmp(ar, "f64") == 0) ? 1 : 0;
     const char* tl = std::getenv("QE_DENSE_TILE");
     s->force_tile = (tl && std::strcmp(tl, "1") == 0) ? 1 : 0;
     const char* tc = std::getenv("QE_TENSOR_CORES");
     s->tensor_cores = (tc && std::strcmp(tc, "0") == 0) ? 0 : 1;
+    // default fusion width: 5-qubit blocks where the tensor cores take them
+    // (n >= 12, no native-FP64 baseline), else 2 (complex128) / 4 (complex64)
+    const bool tc_blocks = s->tensor_cores && !s->force_tile && n >= 12 && !(dtype == QE_C128 && s->c128_native);
+    s->max_k = tc_blocks ? 5 : (dtype == QE_C128 ? 2 : 4);
     try {
         if (dev_ptr) {
             if (bytes < need) fail(QE_ERR_ARG, "borrowed buffer too small");

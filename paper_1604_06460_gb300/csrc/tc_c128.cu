@@ -1,5 +1,5 @@
 // Fused 5-qubit gates on complex128 states with the 5th-generation tensor
-// cores: error-free integer-digit products on the BF16 tensor pipe (the
+// cores: error-free integer-digit products on the FP16 tensor pipe (the
 // splitting idea of Ozaki, Ogita, Oishi and Rump, "Error-free transformations
 // of matrix multiplication by using fast routines of matrix multiplication
 // and its applications", Numer. Algorithms 59, 2012), recombined exactly in
@@ -16,7 +16,7 @@
 // balanced digits: X = sum_i a_i 256^(6 - i), a_1 in [0, 128], a_2..a_6 in
 // [-128, 127]; the value's sign multiplies every digit.  W's rows get scales
 // 2^F_n and digits b_j the same way on the host.  Every digit is an integer
-// of magnitude <= 128 and exact in BF16.
+// of magnitude <= 128 and exact in FP16.
 //
 // Products.  C_d = sum_{i + j = d} A_i B_j^T for d = 2..8 (26 digit pairs;
 // the dropped pairs i + j >= 9 weigh below 2^-56 of the row scale), one FP32
@@ -38,17 +38,19 @@
 // Rows whose largest magnitude is below 2^-920 are flushed to zero.
 //
 // Schedule: sixteen worker warps (four threads per group row) split and
-// recombine, one more warp issues the MMAs.  The 64 outputs of a row are computed as two halves of 32 (16
-// complex columns each) into two tensor-memory accumulator sets X and Y, so
+// recombine, one warp issues the MMAs, four warps stream tiles in.  The 64
+// outputs of a row are computed as two halves of 32 (16 complex columns
+// each) into two tensor-memory accumulator sets X and Y, so
 // the MMAs of one half overlap the epilogue of the other and the splitting of
 // the next tile:
 //   workers: epilogue(t, X) | split(t+1) | epilogue(t, Y) | ...
 //   MMA warp:   MMA(t, Y)   |   ...      | MMA(t+1, X)    | MMA(t+1, Y) ...
-// (104 MMAs of 128x32x16 per half).  The raw amplitudes of tile t+2 stream
-// into a padded staging buffer with cp.async meanwhile.  Hand-offs use
-// mbarriers (digits ready, set Y free: workers arrive; set X / Y done:
-// tcgen05.commit); every wait has an iteration limit and the workers leave
-// their loop together when any of them times out.
+// The load warps copy the raw amplitudes of the next tile into a padded
+// staging buffer with cp.async as soon as the workers have split the current
+// one.  Hand-offs use mbarriers (digits ready, set Y free, staging read:
+// workers arrive; set X / Y done: tcgen05.commit; tile staged:
+// cp.async.mbarrier.arrive); every wait has an iteration limit and the
+// workers leave their loop together when any of them times out.
 #include <cmath>
 #include <cstring>
 
@@ -64,7 +66,9 @@ using tc::mbar_wait;
 using tc::smem_u32;
 
 constexpr int kWorkers = 512;                // 16 warps: splitting and epilogue
-constexpr int kOzThreads = kWorkers + 32;     // + 1 warp issuing the MMAs
+constexpr int kLoadWarps = 4;
+constexpr int kOzThreads = kWorkers + 32 + 32 * kLoadWarps;   // + 1 warp issuing the MMAs, 4 loading tiles
+constexpr int kMmaWarp = kWorkers / 32, kLoadWarp0 = kWorkers / 32 + 1;
 constexpr int kRows = 128;                    // groups per tile (MMA M)
 constexpr int kK = 64;                        // real K
 constexpr int kN = 64;                        // real N (two halves of 32)
@@ -73,7 +77,7 @@ constexpr int kDigits = 6;
 constexpr int kAcc = 7;                       // accumulators for d = 2..8
 constexpr uint32_t kTmemCols = 512;           // two accumulator sets of 7 x 32 columns
 constexpr uint32_t kSetY = 256;               // column of the second set
-constexpr uint32_t kSliceA = kRows * 128;     // bytes of one digit slice of In (bf16, 128 B per row)
+constexpr uint32_t kSliceA = kRows * 128;     // bytes of one digit slice of In (fp16, 128 B per row)
 constexpr uint32_t kSliceB = kN * 128;        // bytes of one digit slice of W
 constexpr uint32_t kStageRow = 32 * 16 + 16;  // staged row of 32 complex128, padded by 16 bytes
 constexpr uint32_t kStackB = kDigits * kNH * 128; // bytes of one half's stack of the six W' digit slices
@@ -87,18 +91,18 @@ struct OzArgs {
     uint8_t gpos[5];
     uint32_t* status;
     long long spin_limit;
-    const uint16_t* B;      // [6][64][64] bf16 digits of W': slice j, row n', column k
+    const uint16_t* B;      // [6][64][64] fp16 digits of W': slice j, row n', column k
     const int* F;           // [64] row scale exponents of W (original row order)
 };
 
-// Byte offset of the 16-byte chunk `ch` (8 bf16 along K) of row r in a
+// Byte offset of the 16-byte chunk `ch` (8 fp16 along K) of row r in a
 // K-major operand with 128-byte rows, 128-byte swizzle.
 __device__ __forceinline__ uint32_t sw128_chunk(int r, int ch) {
     return (uint32_t)(r >> 3) * 1024u + (uint32_t)(r & 7) * 128u + (uint32_t)((ch ^ (r & 7)) * 16);
 }
 
-// D[128 x N] (+)= A[128 x 16] B[N x 16]^T, bf16 inputs, f32 accumulators.
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+// D[128 x N] (+)= A[128 x 16] B[N x 16]^T, fp16 inputs, f32 accumulators.
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
@@ -106,17 +110,13 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-    uint32_t r;
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-    return r;
-}
-
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src));
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// Arrive on the mbarrier once this thread's earlier cp.async copies land.
+__device__ __forceinline__ void cp_async_arrive(uint64_t* mbar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
 
 __device__ __forceinline__ void mbar_init_count(uint64_t* mbar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
@@ -148,10 +148,13 @@ __device__ __forceinline__ long long mad_wide(int a, int b, long long c) {
 
 __device__ __forceinline__ uint32_t biased_exp(double v) { return ((uint32_t)__double2hiint(v) >> 20) & 0x7FFu; }
 
-// The six signed digits of v (as floats) for a row whose shift base is
-// base_s = (largest biased exponent of the row) + 5: q = M53 >> (base_s - e),
-// X = (q + 1) >> 1, and the balanced digits come from Z = X + 0x8080808080.
-__device__ __forceinline__ void split_digits(double v, uint32_t base_s, float d[kDigits]) {
+// The balanced-offset integer Z = X + 0x8080808080 of v (as two words) for a
+// row whose shift base is base_s = (largest biased exponent of the row) + 5:
+// q = M53 >> (base_s - e), X = (q + 1) >> 1; and v's sign bit.
+struct Zw {
+    uint32_t zl, zh, sign;
+};
+__device__ __forceinline__ Zw split_z(double v, uint32_t base_s) {
     const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
     const uint32_t e = (hi >> 20) & 0x7FFu;
     const uint32_t s = (e == 0u) ? 64u : base_s - e;              // >= 5
@@ -165,17 +168,34 @@ __device__ __forceinline__ void split_digits(double v, uint32_t base_s, float d[
         qh = 0u;
     }
     const uint64_t Z = ((((uint64_t)qh << 32) | ql) + 0x10101010101ull) >> 1;
-    const uint32_t zl = (uint32_t)Z, zh = (uint32_t)(Z >> 32);
-    const uint32_t sign = hi & 0x80000000u;
-    const float sf = __uint_as_float(0x3F800000u | sign);
-    const float c0 = __uint_as_float(0x4B000000u | (sign ^ 0x80000000u));    // -sign * 2^23
-    const float c1 = __uint_as_float(0x4B000080u | (sign ^ 0x80000000u));    // -sign * (2^23 + 128)
-    d[0] = __fmaf_rn(__uint_as_float(__byte_perm(zh, 0x4B000000u, 0x7651u)), sf, c0);
-    d[1] = __fmaf_rn(__uint_as_float(__byte_perm(zh, 0x4B000000u, 0x7650u)), sf, c1);
-    d[2] = __fmaf_rn(__uint_as_float(__byte_perm(zl, 0x4B000000u, 0x7653u)), sf, c1);
-    d[3] = __fmaf_rn(__uint_as_float(__byte_perm(zl, 0x4B000000u, 0x7652u)), sf, c1);
-    d[4] = __fmaf_rn(__uint_as_float(__byte_perm(zl, 0x4B000000u, 0x7651u)), sf, c1);
-    d[5] = __fmaf_rn(__uint_as_float(__byte_perm(zl, 0x4B000000u, 0x7650u)), sf, c1);
+    return Zw{(uint32_t)Z, (uint32_t)(Z >> 32), hi & 0x80000000u};
+}
+
+__device__ __forceinline__ uint32_t hfma2(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+// The six signed digits of two values a, b as packed fp16 pairs (a in the
+// low half): byte k of Z becomes the fp16 number 1024 + byte (bits 0x64bb),
+// and one f16x2 fused multiply-add gives sign * (byte - 128) (sign * byte for
+// the leading digit) exactly.  Digit 0 is byte 1 of zh, digit 1 byte 0 of zh,
+// digits 2..5 bytes 3..0 of zl.
+__device__ __forceinline__ void digit_pairs(const Zw& A, const Zw& B, uint32_t w[kDigits]) {
+    const uint32_t sg = (A.sign >> 16) | B.sign;                  // sign bits 15 and 31
+    const uint32_t sf = 0x3C003C00u | sg;                         // (+-1, +-1)
+    const uint32_t c0 = 0x64006400u | (sg ^ 0x80008000u);         // -sign * 1024
+    const uint32_t c1 = 0x64806480u | (sg ^ 0x80008000u);         // -sign * 1152
+    auto mag = [](uint32_t xa, uint32_t xb, uint32_t k) {
+        return (__byte_perm(xa, xb, k | ((4u + k) << 8)) & 0x00FF00FFu) | 0x64006400u;
+    };
+    w[0] = hfma2(mag(A.zh, B.zh, 1u), sf, c0);
+    w[1] = hfma2(mag(A.zh, B.zh, 0u), sf, c1);
+    w[2] = hfma2(mag(A.zl, B.zl, 3u), sf, c1);
+    w[3] = hfma2(mag(A.zl, B.zl, 2u), sf, c1);
+    w[4] = hfma2(mag(A.zl, B.zl, 1u), sf, c1);
+    w[5] = hfma2(mag(A.zl, B.zl, 0u), sf, c1);
 }
 
 // Output value from the seven accumulators (raw FP32 bits); eadj = (E_r +
@@ -241,7 +261,7 @@ __device__ __noinline__ void issue_mmas(const OzArgs& a, uint32_t tmem, uint32_t
                     const uint64_t da = tc::sdesc_sw128(a0 + (uint32_t)(i - 1) * kSliceA + 32u * ks);
                     const uint64_t db = tc::sdesc_sw128(stack + (uint32_t)(j0 - 1) * (kNH * 128u) + 32u * ks);
                     const uint32_t dt = set + (uint32_t)(i + j0 - 2) * kNH;
-                    mma_bf16(dt, da, db, tc::idesc(1u, nn, kRows), (ks > 0 || m > 1) ? 1u : 0u);
+                    mma_f16(dt, da, db, tc::idesc(0u, nn, kRows), (ks > 0 || m > 1) ? 1u : 0u);
                 }
             }
             tc::mma_commit(hh ? mbY : mbX);
@@ -257,8 +277,9 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
     unsigned char* sB = sA + kDigits * kSliceA;                 // per half: the 6 W' digit slices stacked
     unsigned char* stage = sB + kDigits * kSliceB;              // raw amplitudes of one tile
     // mbarriers: A digits ready (workers arrive), accumulator set Y free
-    // (workers arrive), MMAs into set X / set Y complete (tcgen05.commit)
-    __shared__ __align__(8) uint64_t mbA, mbYfree, mbX, mbY;
+    // (workers arrive), MMAs into set X / set Y complete (tcgen05.commit),
+    // tile staged (the load warp's copies land), staging read (workers arrive)
+    __shared__ __align__(8) uint64_t mbA, mbYfree, mbX, mbY, mbStage, mbStageFree;
     __shared__ uint32_t tmem_base;
     __shared__ uint64_t hoff[32];
     __shared__ uint32_t cpos[32];
@@ -293,9 +314,11 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
         mbar_init_count(&mbYfree, kWorkers);
         mbar_init_count(&mbX, 1);
         mbar_init_count(&mbY, 1);
+        mbar_init_count(&mbStage, 32 * kLoadWarps);
+        mbar_init_count(&mbStageFree, kWorkers);
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    if (warp == kWorkers / 32) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -311,36 +334,59 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
     __syncthreads();
     const uint32_t tmem = tmem_base;
 
-    if (warp == kWorkers / 32) {
+    const uint32_t gmask = cpos[31];
+    // tile-local row r (a group) <-> index bits: the seven non-gate local bits
+    auto row_bits = [&](int r) {
+        uint32_t l = 0;
+        int j = 0;
+        for (int b = 0; b < 12; ++b)
+            if (!((gmask >> b) & 1u)) l |= (((uint32_t)r >> (j++)) & 1u) << b;
+        return l;
+    };
+    auto row_off = [&](int r) {   // bytes
+        const uint32_t l = row_bits(r);
+        return 16ull * ((l & ((1u << a.L) - 1u)) + hoff[l >> a.L]);
+    };
+    char* const xb = reinterpret_cast<char*>(a.x);
+    auto tile_ptr = [&](uint64_t t) { return xb + 16ull * insert_zero_bits(t << a.L, a.hq, a.kh); };
+    if (warp == kMmaWarp) {
         // ---------------------------------------------------- MMA issuer
         if (lane == 0) issue_mmas(a, tmem, smem_u32(sA), smem_u32(sB), &mbA, &mbYfree, &mbX, &mbY);
         __syncwarp();
+    } else if (warp >= kLoadWarp0) {
+        // ------------------------------------------------------- tile loads
+        // thread <-> group row: 32 16-byte copies into the padded staging
+        // buffer per tile, completion signalled on mbStage
+        const int r = tid - kLoadWarp0 * 32;
+        const uint64_t ro = row_off(r);
+        const uint32_t d = smem_u32(stage) + (uint32_t)r * kStageRow;
+        uint32_t pf = 0;
+        bool first = true;
+        for (uint64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+            if (!first) {
+                if (!mbar_wait(smem_u32(&mbStageFree), pf, a.spin_limit)) {
+                    atomicExch(a.status, 1u);
+                    break;
+                }
+                pf ^= 1u;
+            }
+            first = false;
+            const char* g = tile_ptr(t) + ro;
+#pragma unroll 8
+            for (int c = 0; c < 32; ++c) cp_async16(d + 16u * c, g + coloff[c]);
+            cp_async_arrive(&mbStage);
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
     } else {
         // ------------------------------------------ splitting and epilogue
-        const uint32_t gmask = cpos[31];
         const int r = ((warp & 3) << 5) | lane;   // group row = TMEM lane
         const int qq = warp >> 2;                 // complex columns [8 qq, 8 qq + 8)
-        uint32_t lrow = 0;
-        {
-            int j = 0;
-            for (int b = 0; b < 12; ++b)
-                if (!((gmask >> b) & 1u)) lrow |= (((uint32_t)r >> (j++)) & 1u) << b;
-        }
-        const uint64_t rowoff = 16ull * ((lrow & ((1u << a.L) - 1u)) + hoff[lrow >> a.L]);   // bytes
-        char* const xb = reinterpret_cast<char*>(a.x);
-        auto tile_base = [&](uint64_t t) { return xb + 16ull * insert_zero_bits(t << a.L, a.hq, a.kh) + rowoff; };
-        const uint32_t my_stage = smem_u32(stage + r * kStageRow + qq * 128);
-        auto prefetch = [&](uint64_t t) {
-            const char* gb = tile_base(t);
-#pragma unroll
-            for (int c = 0; c < 8; ++c) cp_async16(my_stage + 16u * c, gb + coloff[8 * qq + c]);
-            cp_async_commit();
-        };
+        const uint64_t rowoff = row_off(r);
+        auto tile_base = [&](uint64_t t) { return tile_ptr(t) + rowoff; };
         // digits of this thread's 16 values into the six operand slices
         // (chunk qq: real parts, chunk 4 + qq: imaginary parts); returns
         // (E_r - 56) << 20
         auto split_tile = [&]() -> int {
-            cp_async_wait_all();
             const double2* srow = reinterpret_cast<const double2*>(stage + r * kStageRow + qq * 128);
             uint32_t em = 0;
 #pragma unroll
@@ -354,15 +400,14 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
             const uint32_t base_s = (em < (uint32_t)kFlushExp) ? 0x10000u : em + 5u;
 #pragma unroll
             for (int part = 0; part < 2; ++part) {
-                uint32_t w[kDigits][4];      // packed bf16 pairs: slice i, values 2p, 2p + 1
+                uint32_t w[kDigits][4];      // packed fp16 pairs: slice i, values 2p, 2p + 1
 #pragma unroll
                 for (int p2 = 0; p2 < 4; ++p2) {
-                    float d0[kDigits], d1[kDigits];
                     const double2 va = srow[2 * p2], vb = srow[2 * p2 + 1];
-                    split_digits(part ? va.y : va.x, base_s, d0);
-                    split_digits(part ? vb.y : vb.x, base_s, d1);
+                    uint32_t d[kDigits];
+                    digit_pairs(split_z(part ? va.y : va.x, base_s), split_z(part ? vb.y : vb.x, base_s), d);
 #pragma unroll
-                    for (int i = 0; i < kDigits; ++i) w[i][p2] = pack_bf16x2(d0[i], d1[i]);
+                    for (int i = 0; i < kDigits; ++i) w[i][p2] = d[i];
                 }
                 const uint32_t off = sw128_chunk(r, part * 4 + qq);
 #pragma unroll
@@ -409,14 +454,21 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
         };
-        uint32_t px = 0, py = 0;
+        uint32_t px = 0, py = 0, ps = 0;
         uint64_t t = blockIdx.x;
         int eterm = 0;
-        if (t < a.ntiles) {
-            prefetch(t);
-            eterm = split_tile();
+        // staged tile -> digits; false when a wait ran out (on every worker)
+        auto split_next = [&](int& et) {
+            if (workers_any(!mbar_wait(smem_u32(&mbStage), ps, a.spin_limit))) return false;
+            ps ^= 1u;
+            et = split_tile();
+            mbar_arrive(&mbStageFree);
             mbar_arrive(&mbA);
-            if (t + gridDim.x < a.ntiles) prefetch(t + gridDim.x);
+            return true;
+        };
+        if (t < a.ntiles && !split_next(eterm)) {
+            atomicExch(a.status, 1u);
+            t = a.ntiles;
         }
         for (; t < a.ntiles; t += gridDim.x) {
             const uint64_t tn = t + gridDim.x;
@@ -437,23 +489,32 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
             py ^= 1u;
             asm volatile("tcgen05.fence::after_thread_sync;");
             int eterm_next = 0;
-            if (tn < a.ntiles) {
-                eterm_next = split_tile();
-                mbar_arrive(&mbA);
-                if (tn + gridDim.x < a.ntiles) prefetch(tn + gridDim.x);
+            if (tn < a.ntiles && !split_next(eterm_next)) {
+                atomicExch(a.status, 1u);
+                break;
             }
             epilogue(1, gb, eterm);
             mbar_arrive(&mbYfree);
             eterm = eterm_next;
         }
-        cp_async_wait_all();
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == kWorkers / 32) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.fence::after_thread_sync;");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
     }
+}
+
+// IEEE binary16 bits of an integer of magnitude below 2048 (exact).
+uint16_t fp16_bits(int d) {
+    if (d == 0) return 0;
+    const uint16_t sign = d < 0 ? 0x8000u : 0u;
+    unsigned m = (unsigned)(d < 0 ? -d : d);
+    int e = 0;
+    while ((m >> (e + 1)) != 0) ++e;                     // m in [2^e, 2^(e+1))
+    const unsigned frac = (m << (10 - e)) & 0x3FFu;
+    return (uint16_t)(sign | ((unsigned)(e + 15) << 10) | frac);
 }
 
 // Balanced base-256 digits of one row of W (host side, same rule as the
@@ -513,10 +574,7 @@ void launch_gate_tc5_c128(qe_state* s, const int* qubits, const cd* U) {
         const int np = hh * kNH + m;
         for (int j = 0; j < kDigits; ++j)
             for (int k = 0; k < kK; ++k) {
-                const float f = (float)dg[j][k];       // |digit| <= 128: exact in bf16
-                uint32_t bits;
-                std::memcpy(&bits, &f, 4);
-                hw.B[((size_t)j * kN + np) * kK + k] = (uint16_t)(bits >> 16);
+                hw.B[((size_t)j * kN + np) * kK + k] = fp16_bits(dg[j][k]);
             }
     }
     char* scr = (char*)ensure_scratch(s, 256 + sizeof(HostW));

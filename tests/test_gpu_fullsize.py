@@ -66,11 +66,14 @@ def test_config1_qft_n30_sampled_vs_oracle(qe):
         del psi
 
 
-def test_config1_circuit_n30_then_inverse_is_identity(qe):
+@pytest.mark.parametrize("max_k", [2, 5])
+def test_config1_circuit_n30_then_inverse_is_identity(qe, max_k):
+    # max_k = 2: double-float gate kernels; max_k = 5: 4- and 5-qubit blocks
+    # on the tensor cores (exact fp16-digit products)
     n = 30
     gates = I.random_circuit(n, 20, seed=0)
     with qe.State(n, "c128") as st:
-        st.set_policy(qe.POLICY_AUTO, 2)
+        st.set_policy(qe.POLICY_AUTO, max_k)
         for g in gates:
             st.apply(g)
         for g in reversed(gates):
