@@ -168,23 +168,42 @@ def peak_hbm():
         return 6800.0, "fallback"
 
 
+# Source files each profiled kernel is built from (its summary's hash covers
+# only these, so an edit elsewhere keeps the counters valid).
+KERNEL_SOURCES = {
+    "gate_tc_k5_c128": ["tc_c128.cu", "qe_tc.cuh", "qe_arith.cuh"],
+    "gate_tc_k5": ["tcgen05.cu", "qe_tc.cuh", "qe_arith.cuh"],
+    "gate_direct": ["gates.cu", "qe_arith.cuh"],
+    "expect": ["reduce.cu", "qe_arith.cuh"],
+    "fft": ["fft.cu", "qe_arith.cuh"],
+}
+
+
 def kernel_traffic(name, bytes_per_launch_now):
     """DRAM traffic per launch for kernel `name` from the committed ncu
-    summary profiles/<name>*.md, if it was taken on the current source."""
+    summary profiles/<name>_n*.md, if it was taken on the kernel's current
+    source."""
     import glob
-    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{name}*.md"))):
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{name}_n*.md"))):
         text = open(path).read()
         m = re.search(r"traffic_bytes_per_launch_full:\s*([0-9.eE+]+)", text)
         h = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
-        if m and h and h.group(1) == source_hash():
+        if m and h and h.group(1) == source_hash(name):
             return float(m.group(1))
     return None
 
 
-def source_hash():
+def source_hash(kernel=None):
+    """sha256 (16 hex digits) of the kernel's source files (all of csrc/ when
+    the kernel is not listed)."""
     d = os.path.join(ROOT, "paper_1604_06460_gb300", "csrc")
+    files = sorted(os.listdir(d))
+    for prefix in sorted(KERNEL_SOURCES, key=len, reverse=True):
+        if kernel and kernel.startswith(prefix):
+            files = KERNEL_SOURCES[prefix]
+            break
     hs = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
+    for f in files:
         hs.update(open(os.path.join(d, f), "rb").read())
     return hs.hexdigest()[:16]
 

@@ -394,7 +394,11 @@ void diag_impl(qe_state* s, int k, const int* qubits, const cd* d) {
 void launch_gate_dense(qe_state* s, int k, const int* qubits, const cd* U) {
     const bool tc64 = s->dtype == QE_C64;
     const bool tc128 = s->dtype == QE_C128 && !s->c128_native;
-    if ((tc64 || tc128) && s->tensor_cores && !s->force_tile && s->n >= 12 && k >= 4) {
+    // complex64 blocks of 4-5 qubits and complex128 blocks of 3-5 qubits run
+    // on the tensor cores (complex128 3-qubit blocks are ALU-bound in
+    // double-float arithmetic)
+    const int kmin = tc64 ? 4 : 3;
+    if ((tc64 || tc128) && s->tensor_cores && !s->force_tile && s->n >= 12 && k >= kmin) {
         auto run = [&](const int* q5, const cd* U5) {
             if (tc64) launch_gate_tc5(s, q5, U5);
             else launch_gate_tc5_c128(s, q5, U5);
@@ -403,14 +407,21 @@ void launch_gate_dense(qe_state* s, int k, const int* qubits, const cd* U) {
             run(qubits, U);
             return;
         }
-        // widen a 4-qubit block by one idle qubit: U5 = 1_2 (x) U4 (new bit 4)
-        int q5[5] = {qubits[0], qubits[1], qubits[2], qubits[3], 0};
-        for (int c = 0; c < s->n; ++c)
-            if (c != q5[0] && c != q5[1] && c != q5[2] && c != q5[3]) { q5[4] = c; break; }
+        // widen the block by 5 - k idle qubits (the lowest ones not in the
+        // block): U5 = 1 (x) U, the idle qubits as the high matrix bits
+        int q5[5];
+        for (int j = 0; j < k; ++j) q5[j] = qubits[j];
+        int w = k;
+        for (int c = 0; c < s->n && w < 5; ++c) {
+            bool used = false;
+            for (int j = 0; j < k; ++j) used |= qubits[j] == c;
+            if (!used) q5[w++] = c;
+        }
+        const int d = 1 << k;
         std::vector<cd> U5(32 * 32, cd(0.0));
-        for (int hb = 0; hb < 2; ++hb)
-            for (int r = 0; r < 16; ++r)
-                for (int c = 0; c < 16; ++c) U5[(r | (hb << 4)) * 32 + (c | (hb << 4))] = U[r * 16 + c];
+        for (int hb = 0; hb < (32 >> k); ++hb)
+            for (int r = 0; r < d; ++r)
+                for (int c = 0; c < d; ++c) U5[(r | (hb << k)) * 32 + (c | (hb << k))] = U[r * d + c];
         run(q5, U5.data());
         return;
     }

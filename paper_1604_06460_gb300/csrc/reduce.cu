@@ -163,18 +163,36 @@ __global__ void __launch_bounds__(kRThreads) k_probs_partial(const __grid_consta
     }
 }
 
-// One thread per output: Neumaier sum of `count` partials (stride 1).
-__global__ void k_sum_partials(const double2* __restrict__ partial, uint64_t nout, uint64_t count,
-                               const double* __restrict__ weight, double* __restrict__ out) {
-    for (uint64_t o = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; o < nout;
-         o += (uint64_t)gridDim.x * blockDim.x) {
+// One block per output (grid-stride over outputs): Neumaier sums of the
+// `count` partials of an output, thread t taking partials t, t + 256, ...;
+// the 256 compensated sums are then combined pairwise in a fixed tree, so the
+// result does not depend on timing.
+constexpr int kSumThreads = 256;
+__global__ void __launch_bounds__(kSumThreads) k_sum_partials(const double2* __restrict__ partial, uint64_t nout,
+                                                              uint64_t count, const double* __restrict__ weight,
+                                                              double* __restrict__ out) {
+    __shared__ double ss[kSumThreads], cs[kSumThreads];
+    for (uint64_t o = blockIdx.x; o < nout; o += gridDim.x) {
         double s = 0.0, c = 0.0;
-        for (uint64_t i = 0; i < count; ++i) {
-            double2 p = partial[o * count + i];
+        for (uint64_t i = threadIdx.x; i < count; i += kSumThreads) {
+            const double2 p = partial[o * count + i];
             neumaier(s, c, p.x);
             neumaier(s, c, p.y);
         }
-        out[o] = (s + c) * (weight ? weight[o] : 1.0);
+        ss[threadIdx.x] = s;
+        cs[threadIdx.x] = c;
+        __syncthreads();
+        for (int h = kSumThreads / 2; h > 0; h >>= 1) {
+            if ((int)threadIdx.x < h) {
+                double a = ss[threadIdx.x], ac = cs[threadIdx.x];
+                neumaier(a, ac, ss[threadIdx.x + h]);
+                ss[threadIdx.x] = a;
+                cs[threadIdx.x] = ac + cs[threadIdx.x + h];
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[o] = (ss[0] + cs[0]) * (weight ? weight[o] : 1.0);
+        __syncthreads();
     }
 }
 
@@ -426,8 +444,8 @@ void probs_impl(qe_state* s, int m, const int* qubits, double* host_out) {
     }
     {
         Launch L(s, "sum_partials", 0.0, false);
-        unsigned g2 = (unsigned)std::min<uint64_t>((bins + 255) / 256, 4096);
-        k_sum_partials<<<g2, 256, 0, s->stream>>>(a.partial, bins, chunks, nullptr, dout);
+        const unsigned g2 = (unsigned)std::min<uint64_t>(bins, 4096);
+        k_sum_partials<<<g2, kSumThreads, 0, s->stream>>>(a.partial, bins, chunks, nullptr, dout);
         QE_CUDA(cudaGetLastError());
     }
     QE_CUDA(cudaMemcpyAsync(host_out, dout, bins * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
@@ -656,7 +674,7 @@ double expect_impl(qe_state* s, int nterms, const uint64_t* xm, const uint64_t* 
     }
     {
         Launch Lz(s, "sum_partials", 0.0, false);
-        k_sum_partials<<<1, 1, 0, s->stream>>>(partial, 1, (uint64_t)nlaunch * max_grid, nullptr, dout);
+        k_sum_partials<<<1, kSumThreads, 0, s->stream>>>(partial, 1, (uint64_t)nlaunch * max_grid, nullptr, dout);
         QE_CUDA(cudaGetLastError());
     }
     double out = 0.0;

@@ -224,48 +224,64 @@ __device__ __forceinline__ double recombine(const uint32_t c[kAcc], int eadj) {
 // j0..j1 writes C_{i + j0} .. C_{i + j1} at once: the digit products form a
 // convolution.  Per K-step and half: (1,1) and (2,1..6) start the sums, then
 // (1,2..6), (3,1..5), (4,1..4), (5,1..3), (6,1..2) add to them (26 pairs in 7
-// MMAs).  Per tile: wait for the digit slices, issue the first half into set
-// X, wait until set Y is free, issue the second half into Y; each half is
-// committed to its own mbarrier.
-__device__ __noinline__ void issue_mmas(const OzArgs& a, uint32_t tmem, uint32_t a0, uint32_t b0, uint64_t* mbA,
-                                        uint64_t* mbYfree, uint64_t* mbX, uint64_t* mbY) {
-    // (i, j0, j1, starts) in issue order
+// MMAs).  Per tile: the first half's K-steps over the real parts start as
+// soon as those digits are split, its imaginary-part K-steps when the rest
+// is; the second half follows once set Y is free; each half is committed to
+// its own mbarrier.
+__device__ __noinline__ void issue_mmas(const OzArgs& a, uint32_t tmem, uint32_t a0, uint32_t b0, uint64_t* mbAre,
+                                        uint64_t* mbA, uint64_t* mbYfree, uint64_t* mbX, uint64_t* mbY) {
+    // (i, j0, j1) in issue order
     constexpr int kI[7] = {1, 2, 1, 3, 4, 5, 6};
     constexpr int kJ0[7] = {1, 1, 2, 1, 1, 1, 1};
     constexpr int kJ1[7] = {1, 6, 6, 5, 4, 3, 2};
-    uint32_t pa = 0, pyf = 0;
+    const uint64_t da0 = tc::sdesc_sw128(a0);      // an offset of b bytes adds b >> 4
+    auto issue = [&](int hh, int ks0, int ks1) {
+        const uint32_t set = tmem + (hh ? kSetY : 0u);
+        const uint64_t db0 = tc::sdesc_sw128(b0 + (uint32_t)hh * kStackB);
+#pragma unroll
+        for (int ks = 0; ks < kK / 16; ++ks) {
+            if (ks < ks0 || ks >= ks1) continue;
+#pragma unroll
+            for (int m = 0; m < 7; ++m) {
+                const int i = kI[m], j0 = kJ0[m], j1 = kJ1[m];
+                const uint32_t nn = (uint32_t)(j1 - j0 + 1) * kNH;
+                const uint64_t da = da0 + (((uint32_t)(i - 1) * kSliceA + 32u * ks) >> 4);
+                const uint64_t db = db0 + (((uint32_t)(j0 - 1) * (kNH * 128u) + 32u * ks) >> 4);
+                const uint32_t dt = set + (uint32_t)(i + j0 - 2) * kNH;
+                mma_f16(dt, da, db, tc::idesc(0u, nn, kRows), (ks > 0 || m > 1) ? 1u : 0u);
+            }
+        }
+    };
+    uint32_t pre = 0, pa = 0, pyf = 0;
     bool first = true;
     for (uint64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        // half X: K-steps 0, 1 (real parts) as soon as they are split
+        if (!mbar_wait(smem_u32(mbAre), pre, a.spin_limit)) {
+            atomicExch(a.status, 1u);
+            return;
+        }
+        pre ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        issue(0, 0, 2);
         if (!mbar_wait(smem_u32(mbA), pa, a.spin_limit)) {
             atomicExch(a.status, 1u);
             return;
         }
         pa ^= 1u;
-        for (int hh = 0; hh < 2; ++hh) {
-            if (hh == 1 && !first) {
-                if (!mbar_wait(smem_u32(mbYfree), pyf, a.spin_limit)) {
-                    atomicExch(a.status, 1u);
-                    return;
-                }
-                pyf ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        issue(0, 2, 4);
+        tc::mma_commit(mbX);
+        // half Y once its accumulators are free
+        if (!first) {
+            if (!mbar_wait(smem_u32(mbYfree), pyf, a.spin_limit)) {
+                atomicExch(a.status, 1u);
+                return;
             }
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t set = tmem + (hh ? kSetY : 0u);
-            const uint32_t stack = b0 + (uint32_t)hh * kStackB;
-#pragma unroll
-            for (int ks = 0; ks < kK / 16; ++ks) {
-#pragma unroll
-                for (int m = 0; m < 7; ++m) {
-                    const int i = kI[m], j0 = kJ0[m], j1 = kJ1[m];
-                    const uint32_t nn = (uint32_t)(j1 - j0 + 1) * kNH;
-                    const uint64_t da = tc::sdesc_sw128(a0 + (uint32_t)(i - 1) * kSliceA + 32u * ks);
-                    const uint64_t db = tc::sdesc_sw128(stack + (uint32_t)(j0 - 1) * (kNH * 128u) + 32u * ks);
-                    const uint32_t dt = set + (uint32_t)(i + j0 - 2) * kNH;
-                    mma_f16(dt, da, db, tc::idesc(0u, nn, kRows), (ks > 0 || m > 1) ? 1u : 0u);
-                }
-            }
-            tc::mma_commit(hh ? mbY : mbX);
+            pyf ^= 1u;
         }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        issue(1, 0, 4);
+        tc::mma_commit(mbY);
         first = false;
     }
 }
@@ -276,10 +292,10 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
     unsigned char* sA = base;                                   // 6 digit slices of In
     unsigned char* sB = sA + kDigits * kSliceA;                 // per half: the 6 W' digit slices stacked
     unsigned char* stage = sB + kDigits * kSliceB;              // raw amplitudes of one tile
-    // mbarriers: A digits ready (workers arrive), accumulator set Y free
+    // mbarriers: A digits ready (real parts; all: workers arrive), accumulator set Y free
     // (workers arrive), MMAs into set X / set Y complete (tcgen05.commit),
     // tile staged (the load warp's copies land), staging read (workers arrive)
-    __shared__ __align__(8) uint64_t mbA, mbYfree, mbX, mbY, mbStage, mbStageFree;
+    __shared__ __align__(8) uint64_t mbAre, mbA, mbYfree, mbX, mbY, mbStage, mbStageFree;
     __shared__ uint32_t tmem_base;
     __shared__ uint64_t hoff[32];
     __shared__ uint32_t cpos[32];
@@ -310,6 +326,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
         cpos[tid] = o;
     }
     if (tid == 0) {
+        mbar_init_count(&mbAre, kWorkers);
         mbar_init_count(&mbA, kWorkers);
         mbar_init_count(&mbYfree, kWorkers);
         mbar_init_count(&mbX, 1);
@@ -351,7 +368,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
     auto tile_ptr = [&](uint64_t t) { return xb + 16ull * insert_zero_bits(t << a.L, a.hq, a.kh); };
     if (warp == kMmaWarp) {
         // ---------------------------------------------------- MMA issuer
-        if (lane == 0) issue_mmas(a, tmem, smem_u32(sA), smem_u32(sB), &mbA, &mbYfree, &mbX, &mbY);
+        if (lane == 0) issue_mmas(a, tmem, smem_u32(sA), smem_u32(sB), &mbAre, &mbA, &mbYfree, &mbX, &mbY);
         __syncwarp();
     } else if (warp >= kLoadWarp0) {
         // ------------------------------------------------------- tile loads
@@ -413,8 +430,10 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
 #pragma unroll
                 for (int i = 0; i < kDigits; ++i)
                     *reinterpret_cast<uint4*>(sA + i * kSliceA + off) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+                // the real parts (K 0..31) go to the tensor cores first
+                asm volatile("fence.proxy.async.shared::cta;");
+                mbar_arrive(part ? &mbA : &mbAre);
             }
-            asm volatile("fence.proxy.async.shared::cta;");
             return ((int)em - 1021 - 56) * (1 << 20);
         };
         // outputs of accumulator set hh: this thread's 4 complex columns
@@ -463,7 +482,6 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
             ps ^= 1u;
             et = split_tile();
             mbar_arrive(&mbStageFree);
-            mbar_arrive(&mbA);
             return true;
         };
         if (t < a.ntiles && !split_next(eterm)) {

@@ -53,11 +53,14 @@ def test_training_fits_a_smooth_target(qe):
     m.close()
 
 
-def test_learned_fusion_width_beats_analytic_rule(qe):
-    """Complex128 passes are ALU-bound in double-float arithmetic for wide
-    blocks, so the memory-only analytic rule (fewest passes = widest blocks)
-    is slow; a model trained on the emulator's own timings picks a narrower
-    width.  Both produce the same state."""
+def test_learned_fusion_width_beats_analytic_rule(qe, monkeypatch):
+    """With the tensor cores switched off (QE_TENSOR_CORES=0), complex128
+    passes are ALU-bound in double-float arithmetic for wide blocks, so the
+    memory-only analytic rule (fewest passes = widest blocks) is slow; a model
+    trained on the emulator's own timings picks a narrower width.  Both
+    produce the same state.  (With the tensor cores on, 5-qubit blocks are the
+    fastest and both choose them.)"""
+    monkeypatch.setenv("QE_TENSOR_CORES", "0")
     from paper_1604_06460_gb300 import costmodel
     X, y = costmodel.sweep_gate_passes([22, 23, 24], dtypes=("c128",), seed=0)
     model, loss = costmodel.train(X, y, epochs=3000, lr=3e-3, seed=0)

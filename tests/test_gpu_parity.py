@@ -455,7 +455,8 @@ def test_tensor_core_fused_circuit_c64(qe):
 # Exact integer-digit products on the BF16 tensor pipe: inputs and matrix
 # entries are rounded to 2^-48 of their row scale, so the FP64 bar holds.
 @pytest.mark.parametrize("qubits", [[0, 1, 2, 3, 4], [10, 11, 12, 13, 14], [4, 0, 15, 7, 12],
-                                    [2, 9, 5, 14], [15, 14, 13, 12], [6, 3, 11, 1, 8]])
+                                    [2, 9, 5, 14], [15, 14, 13, 12], [6, 3, 11, 1, 8],
+                                    [2, 9, 13], [0, 1, 2]])
 def test_tensor_core_blocks_c128(qe, qubits):
     n = 16
     U = rand_unitary(1 << len(qubits), np.random.default_rng(100 + sum(qubits)))
