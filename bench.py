@@ -345,6 +345,7 @@ def main():
         v, dt, desc = cpu_sample()
         line["cpu_baseline"] = {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle",
                                 "sample": desc, "seconds": dt}
+        line["fusion_width_comparison"] = fusion_comparison(st, step, max_k)
     st.close()
     if rank == 0 and not args.quick:
         torch.cuda.empty_cache()
@@ -360,6 +361,30 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def fusion_comparison(st, step, max_k):
+    """The same step with fusion up to 2 qubits (double-float blocks only):
+    more passes, each closer to the copy bandwidth, longer time to solution."""
+    import torch
+    from paper_1604_06460_gb300 import qe as Q
+    out = {}
+    for k in (2, max_k):
+        st.set_policy(Q.POLICY_AUTO, k)
+        step()
+        torch.cuda.synchronize()
+        st.reset_stats()
+        e0, e1 = _events()
+        e0.record(st.stream)
+        step()
+        e1.record(st.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        s = st.stats()
+        out[f"k<={k}"] = {"ms_per_step": ms, "passes": s["passes"],
+                          "GB_per_s": s["algorithmic_bytes"] / ms / 1e6}
+    st.set_policy(Q.POLICY_AUTO, max_k)
+    return out
 
 
 def e2e(st, step, n, args, bytes_per_step):

@@ -145,7 +145,9 @@ int qe_flush(qe_state* s);
 int qe_sync(qe_state* s);
 
 /* Choose the emulate-vs-simulate policy and the largest fused block width
- * (1 <= max_k <= 5) the gate fuser may form. */
+ * (1 <= max_k <= 5) the gate fuser may form; max_k = 0 selects the default
+ * (5 where the tensor cores take 3-5-qubit blocks, i.e. n >= 12, else 2 for
+ * complex128 and 4 for complex64).  QE_ERR_ARG for other values. */
 int qe_set_policy(qe_state* s, int policy, int max_k);
 
 /* Counters since the last reset: kernel launches, full-state passes, and the

@@ -392,6 +392,14 @@ extern "C" {
 
 const char* qe_last_error(void) { return g_last_error.c_str(); }
 
+// Default fusion width: 5-qubit blocks where the tensor cores take them
+// (n >= 12, no native-FP64 baseline), else 2 (complex128) / 4 (complex64).
+static int default_fusion_width(const qe_state* s) {
+    const bool tc_blocks = s->tensor_cores && !s->force_tile && s->n >= 12 &&
+                           !(s->dtype == QE_C128 && s->c128_native);
+    return tc_blocks ? 5 : (s->dtype == QE_C128 ? 2 : 4);
+}
+
 int qe_alloc_state(int n, int dtype, void* dev_ptr, size_t bytes, void* stream, qe_state** out) {
     QE_API_BEGIN
     if (!out) fail(QE_ERR_ARG, "out is NULL");
@@ -409,10 +417,7 @@ int qe_alloc_state(int n, int dtype, void* dev_ptr, size_t bytes, void* stream, 
     s->force_tile = (tl && std::strcmp(tl, "1") == 0) ? 1 : 0;
     const char* tc = std::getenv("QE_TENSOR_CORES");
     s->tensor_cores = (tc && std::strcmp(tc, "0") == 0) ? 0 : 1;
-    // default fusion width: 5-qubit blocks where the tensor cores take them
-    // (n >= 12, no native-FP64 baseline), else 2 (complex128) / 4 (complex64)
-    const bool tc_blocks = s->tensor_cores && !s->force_tile && n >= 12 && !(dtype == QE_C128 && s->c128_native);
-    s->max_k = tc_blocks ? 5 : (dtype == QE_C128 ? 2 : 4);
+    s->max_k = default_fusion_width(s);
     try {
         if (dev_ptr) {
             if (bytes < need) fail(QE_ERR_ARG, "borrowed buffer too small");
@@ -626,10 +631,10 @@ int qe_set_policy(qe_state* s, int policy, int max_k) {
     QE_API_BEGIN
     check_state(s);
     if (policy < QE_POLICY_AUTO || policy > QE_POLICY_SIMULATE) fail(QE_ERR_ARG, "unknown policy");
-    if (max_k < 1 || max_k > 5) fail(QE_ERR_ARG, "max_k must be in [1, 5]");
+    if (max_k < 0 || max_k > 5) fail(QE_ERR_ARG, "max_k must be in [0, 5]");
     flush(s);
     s->policy = policy;
-    s->max_k = max_k;
+    s->max_k = max_k == 0 ? default_fusion_width(s) : max_k;
     QE_API_END
 }
 

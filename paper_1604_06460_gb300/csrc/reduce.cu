@@ -122,6 +122,14 @@ __device__ __forceinline__ void neumaier(double& s, double& c, double x) {
     s = t;
 }
 
+// Asynchronous global -> shared copy of one amplitude (8 or 16 bytes).
+template <int N>
+__device__ __forceinline__ void async_copy(void* dst, const void* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    if (N == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src));
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src));
+}
+
 // Policy views of an amplitude for the reducers.
 __device__ __forceinline__ float2 rview(float2 v) { return v; }
 __device__ __forceinline__ DF::V rview(double2 v) { return DF::load(v); }
@@ -231,7 +239,9 @@ struct ExpArgs {
     uint32_t xloc[kXT];        // X/Y mask at tile-local positions
     uint32_t xzl[kXT];         // Z mask inside the layout (tile-local positions)
     uint64_t xzo[kXT];         // Z mask outside the layout
+    uint32_t xbelow[kXT];      // bits below the lowest X/Y bit (tile-local)
     int ximag[kXT];            // 1: Im(conj(alpha_{x^xm}) alpha_x), 0: Re
+    int xsigned[kXT];          // the term has a Z part (a sign per amplitude)
     double xw[kXT];            // 2 * coefficient * (+-1 from i^ny)
     double2* partial;          // one per block
 };
@@ -244,8 +254,11 @@ template <class S>
 __global__ void __launch_bounds__(kRThreads) k_expect_tile(const __grid_constant__ ExpArgs<S> a) {
     using V = decltype(rview(S{}));
     constexpr int PER = kPer<S>;
+    static_assert(sizeof(V) == sizeof(S), "tiles are converted in place");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V* tile = reinterpret_cast<V*>(smem_raw);
+    // two tiles: the raw amplitudes of the next tile stream in (cp.async)
+    // while the current one is evaluated, then are converted in place
+    V* const tiles = reinterpret_cast<V*>(smem_raw);
     __shared__ Acc sh[32];
     __shared__ uint64_t offA[64], offB[64];
     __shared__ uint32_t s_zl[kZT];       // zl with the tile's outside parity in bit 31
@@ -262,18 +275,31 @@ __global__ void __launch_bounds__(kRThreads) k_expect_tile(const __grid_constant
         offB[tid] = ob;
     }
     __syncthreads();
-    Acc zacc[kZW], xacc[kXT];
+    Acc zacc[kZW], zacc2[kZW], xacc[kXT];
 #pragma unroll
-    for (int g = 0; g < kZW; ++g) zacc[g] = Acc{0.f, 0.f};
+    for (int g = 0; g < kZW; ++g) zacc[g] = zacc2[g] = Acc{0.f, 0.f};
 #pragma unroll
     for (int t = 0; t < kXT; ++t) xacc[t] = Acc{0.f, 0.f};
     const uint32_t Tn = 1u << a.T, lowmask = (1u << a.L) - 1u;
-    for (uint64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-        const uint64_t base = insert_zero_bits(t << a.L, a.hq, a.kh);
+    auto load = [&](uint64_t t, V* buf) {   // this thread's elements, raw
+        const uint64_t b = insert_zero_bits(t << a.L, a.hq, a.kh);
         for (uint32_t l = tid; l < Tn; l += blockDim.x) {
             const uint32_t h = l >> a.L;
-            tile[l] = rview(a.x[base + (l & lowmask) + offA[h & 63] + offB[h >> 6]]);
+            async_copy<sizeof(S)>(buf + l, a.x + (b + (l & lowmask) + offA[h & 63] + offB[h >> 6]));
         }
+        asm volatile("cp.async.commit_group;");
+    };
+    int cur = 0;
+    if (blockIdx.x < a.ntiles) load(blockIdx.x, tiles);
+    for (uint64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const uint64_t base = insert_zero_bits(t << a.L, a.hq, a.kh);
+        V* const tile = tiles + (size_t)cur * Tn;
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        if (sizeof(S) == 16)   // complex128: split into double-float in place
+            for (uint32_t l = tid; l < Tn; l += blockDim.x) tile[l] = rview(*reinterpret_cast<const S*>(tile + l));
+        __syncthreads();
+        if (t + gridDim.x < a.ntiles) load(t + gridDim.x, tiles + (size_t)(cur ^ 1) * Tn);
+        cur ^= 1;
         if (warp == 0) {
             // outside parities of this tile: Z-only masks, then X/Y terms
             uint32_t b0 = 0, b1 = 0;
@@ -332,31 +358,28 @@ __global__ void __launch_bounds__(kRThreads) k_expect_tile(const __grid_constant
                     for (int j = 0; j < C; ++j) {
                         const float f = (float)(ng - 2 * odd[j]);
                         const float p = fmul(ph[j], f);
-                        acc_add(zacc[g], p, __fmaf_rn(pl[j], f, __fmaf_rn(ph[j], f, -p)));
+                        acc_add((j & 1) ? zacc2[g] : zacc[g], p, __fmaf_rn(pl[j], f, __fmaf_rn(ph[j], f, -p)));
                     }
                 }
             }
         }
         // terms with X/Y parts: one thread per pair (l, l ^ xm) with the
-        // lowest xm bit of l clear
+        // lowest xm bit of l clear; the term loop is innermost so that
+        // consecutive updates go to different accumulators
         const uint32_t xflip = s_xflip;
+#pragma unroll 1
+        for (int j = 0; j < PER / 2; ++j) {
+            const uint32_t i = tid + (uint32_t)j * kRThreads;
+            if (i >= Tn / 2) break;
 #pragma unroll
-        for (int k = 0; k < kXT; ++k) {
-            if (k >= a.nxt) break;
-            const uint32_t xl = a.xloc[k], zlk = a.xzl[k];
-            const uint32_t below = (xl & (~xl + 1u)) - 1u;
-            const bool signed_term = (zlk != 0u) || ((xflip >> k) & 1u);
-            const uint32_t flip = (xflip >> k) & 1u;
-            const bool im = a.ximag[k] != 0;
-#pragma unroll
-            for (int j = 0; j < PER / 2; ++j) {
-                const uint32_t i = tid + (uint32_t)j * kRThreads;
-                if (i >= Tn / 2) break;
+            for (int k = 0; k < kXT; ++k) {
+                if (k >= a.nxt) break;
+                const uint32_t xl = a.xloc[k], below = a.xbelow[k];
                 const uint32_t l = ((i & ~below) << 1) | (i & below);
                 V w = tile[l ^ xl];
                 const V v = tile[l];
-                if (signed_term && ((__popc(l & zlk) ^ flip) & 1u)) w = vneg(w);
-                corr_acc(xacc[k], w, v, im);
+                if (a.xsigned[k] && ((__popc(l & a.xzl[k]) ^ (xflip >> k)) & 1u)) w = vneg(w);
+                corr_acc(xacc[k], w, v, a.ximag[k] != 0);
             }
         }
         __syncthreads();
@@ -365,7 +388,7 @@ __global__ void __launch_bounds__(kRThreads) k_expect_tile(const __grid_constant
 #pragma unroll
     for (int g = 0; g < kZW; ++g) {
         if (g >= a.nzg) break;
-        Acc r = block_reduce(zacc[g], sh);
+        Acc r = block_reduce(acc_merge(zacc[g], zacc2[g]), sh);
         if (tid == 0) {
             df d = df_norm(r.s, r.e);
             neumaier(s, c, df2d(d.h, d.l) * a.zw[g]);
@@ -555,7 +578,7 @@ double expect_impl(qe_state* s, int nterms, const uint64_t* xm, const uint64_t* 
                                                         wg[g].begin() + std::min(wg[g].size(), i + kZT))});
     static thread_local ExpArgs<S> a;
     a.x = reinterpret_cast<const S*>(s->d);
-    const size_t smem = sizeof(decltype(rview(S{}))) << Tmax;
+    const size_t smem = 2 * (sizeof(decltype(rview(S{}))) << Tmax);   // two tiles
     QE_CUDA(cudaFuncSetAttribute(k_expect_tile<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     QE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_expect_tile<S>, kRThreads, smem));
@@ -662,6 +685,8 @@ double expect_impl(qe_state* s, int nterms, const uint64_t* xm, const uint64_t* 
             a.xzo[j] = zm[t] & ~inside;
             // Re(conj(w) v i^ny): ny = 0: +Re, 1: -Im, 2: -Re, 3: +Im
             const int ny = __builtin_popcountll(xm[t] & zm[t]) & 3;
+            a.xbelow[j] = (a.xloc[j] & (~a.xloc[j] + 1u)) - 1u;
+            a.xsigned[j] = zm[t] != 0;
             a.ximag[j] = ny & 1;
             a.xw[j] = 2.0 * cf[t] * ((ny == 1 || ny == 2) ? -1.0 : 1.0);
         }

@@ -248,9 +248,8 @@ class State:
         _check(load().qe_sync(self._h))
 
     def set_policy(self, policy=POLICY_AUTO, max_k=None):
-        if max_k is None:
-            max_k = 2 if self._dt == C128 else 4
-        _check(load().qe_set_policy(self._h, int(policy), int(max_k)))
+        """max_k None (0): the library's default fusion width."""
+        _check(load().qe_set_policy(self._h, int(policy), int(max_k or 0)))
 
     def set_cost_model(self, model):
         """Attach a CostModel (or None): QE_POLICY_AUTO then lets it choose."""
