@@ -47,9 +47,9 @@
 //   MMA warp:   MMA(t, Y)   |   ...      | MMA(t+1, X)    | MMA(t+1, Y) ...
 // The load warps copy the raw amplitudes of the next tile into a padded
 // staging buffer with cp.async as soon as the workers have split the current
-// one.  Hand-offs use mbarriers (digits ready, set Y free, staging read:
-// workers arrive; set X / Y done: tcgen05.commit; tile staged:
-// cp.async.mbarrier.arrive); every wait has an iteration limit and the
+// one, and record each row's largest exponent.  Hand-offs use mbarriers (digits ready, set Y free, staging read:
+// workers arrive; set X / Y done: tcgen05.commit; tile staged and
+// row exponents written); every wait has an iteration limit and the
 // workers leave their loop together when any of them times out.
 #include <cmath>
 #include <cstring>
@@ -113,10 +113,6 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b,
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src));
 }
-// Arrive on the mbarrier once this thread's earlier cp.async copies land.
-__device__ __forceinline__ void cp_async_arrive(uint64_t* mbar) {
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(mbar)) : "memory");
-}
 
 __device__ __forceinline__ void mbar_init_count(uint64_t* mbar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
@@ -124,7 +120,6 @@ __device__ __forceinline__ void mbar_init_count(uint64_t* mbar, uint32_t count) 
 __device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
 }
-__device__ __forceinline__ void workers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kWorkers) : "memory"); }
 // True on every worker thread when p holds on any of them (a barrier of the
 // workers that all reach, so a timed-out wait ends the loop on all of them).
 __device__ __forceinline__ bool workers_any(bool p) {
@@ -294,14 +289,14 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
     unsigned char* stage = sB + kDigits * kSliceB;              // raw amplitudes of one tile
     // mbarriers: A digits ready (real parts; all: workers arrive), accumulator set Y free
     // (workers arrive), MMAs into set X / set Y complete (tcgen05.commit),
-    // tile staged (the load warp's copies land), staging read (workers arrive)
+    // tile staged (load warps arrive with the row exponents), staging read (workers arrive)
     __shared__ __align__(8) uint64_t mbAre, mbA, mbYfree, mbX, mbY, mbStage, mbStageFree;
     __shared__ uint32_t tmem_base;
     __shared__ uint64_t hoff[32];
     __shared__ uint32_t cpos[32];
     __shared__ uint64_t coloff[32];
     __shared__ int sF20[kN];
-    __shared__ uint32_t semax[4][kRows];
+    __shared__ uint32_t s_em[kRows];     // largest biased exponent of each staged row
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     // W' digits into their swizzled operand layout; W row scales
@@ -331,7 +326,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
         mbar_init_count(&mbYfree, kWorkers);
         mbar_init_count(&mbX, 1);
         mbar_init_count(&mbY, 1);
-        mbar_init_count(&mbStage, 32 * kLoadWarps);
+        mbar_init_count(&mbStage, 32 * kLoadWarps);   // one arrival per staged row
         mbar_init_count(&mbStageFree, kWorkers);
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
@@ -391,7 +386,18 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
             const char* g = tile_ptr(t) + ro;
 #pragma unroll 8
             for (int c = 0; c < 32; ++c) cp_async16(d + 16u * c, g + coloff[c]);
-            cp_async_arrive(&mbStage);
+            // once the row has landed: its largest biased exponent, for the
+            // workers' splitting
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            const double2* row = reinterpret_cast<const double2*>(stage + r * kStageRow);
+            uint32_t em = 0;
+#pragma unroll 8
+            for (int c = 0; c < 32; ++c) {
+                const double2 v = row[c];
+                em = max(em, max(biased_exp(v.x), biased_exp(v.y)));
+            }
+            s_em[r] = em;
+            mbar_arrive(&mbStage);
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
     } else {
@@ -405,15 +411,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
         // (E_r - 56) << 20
         auto split_tile = [&]() -> int {
             const double2* srow = reinterpret_cast<const double2*>(stage + r * kStageRow + qq * 128);
-            uint32_t em = 0;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const double2 v = srow[c];
-                em = max(em, max(biased_exp(v.x), biased_exp(v.y)));
-            }
-            semax[qq][r] = em;
-            workers_sync();
-            em = max(max(semax[0][r], semax[1][r]), max(semax[2][r], semax[3][r]));
+            const uint32_t em = s_em[r];    // the row's largest biased exponent (load warps)
             const uint32_t base_s = (em < (uint32_t)kFlushExp) ? 0x10000u : em + 5u;
 #pragma unroll
             for (int part = 0; part < 2; ++part) {
@@ -443,33 +441,30 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
         auto epilogue = [&](int hh, char* gb, int eterm) {
             const uint32_t set = lane_base + (hh ? kSetY : 0u);
             const int m0 = 4 * qq;
+            uint32_t re[kAcc][4], im[kAcc][4];
 #pragma unroll
-            for (int u0 = 0; u0 < 4; u0 += 2) {
-                uint32_t re[kAcc][2], im[kAcc][2];
+            for (int k = 0; k < kAcc; ++k) {
+                const uint32_t ta = set + (uint32_t)(k * kNH + m0);
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                             : "=r"(re[k][0]), "=r"(re[k][1]), "=r"(re[k][2]), "=r"(re[k][3])
+                             : "r"(ta));
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                             : "=r"(im[k][0]), "=r"(im[k][1]), "=r"(im[k][2]), "=r"(im[k][3])
+                             : "r"(ta + 16u));
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = 16 * hh + m0 + u;
+                uint32_t cr[kAcc], ci[kAcc];
 #pragma unroll
                 for (int k = 0; k < kAcc; ++k) {
-                    const uint32_t ta = set + (uint32_t)(k * kNH + m0 + u0);
-                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
-                                 : "=r"(re[k][0]), "=r"(re[k][1])
-                                 : "r"(ta));
-                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
-                                 : "=r"(im[k][0]), "=r"(im[k][1])
-                                 : "r"(ta + 16u));
+                    cr[k] = re[k][u];
+                    ci[k] = im[k][u];
                 }
-                asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int c = 16 * hh + m0 + u0 + u;
-                    uint32_t cr[kAcc], ci[kAcc];
-#pragma unroll
-                    for (int k = 0; k < kAcc; ++k) {
-                        cr[k] = re[k][u];
-                        ci[k] = im[k][u];
-                    }
-                    const double yr = recombine(cr, eterm + sF20[c]);
-                    const double yi = recombine(ci, eterm + sF20[32 + c]);
-                    *reinterpret_cast<double2*>(gb + coloff[c]) = make_double2(yr, yi);
-                }
+                const double yr = recombine(cr, eterm + sF20[c]);
+                const double yi = recombine(ci, eterm + sF20[32 + c]);
+                *reinterpret_cast<double2*>(gb + coloff[c]) = make_double2(yr, yi);
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
         };
