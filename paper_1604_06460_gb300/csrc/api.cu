@@ -217,14 +217,34 @@ struct Planned {
 
 // Greedy fusion: consecutive gates whose qubits stay within max_k qubits are
 // multiplied into one block.  Open blocks have disjoint qubit sets (so they
-// commute); a gate that would overflow closes the blocks it touches.
+// commute).  A gate that would overflow closes just enough of the blocks it
+// touches (largest first) for the rest and the gate to fit; blocks closed at
+// the same moment are disjoint and are packed together into passes of at most
+// max_k qubits.
 std::vector<Planned> plan_fusion(const std::vector<PendingGate>& q, int max_k) {
     std::vector<Planned> out;
-    auto emit = [&](Block& b) {
+    auto emit_one = [&](Block& b) {
         Planned p;
         p.q = std::move(b.q);
         p.U = std::move(b.U);
         out.push_back(std::move(p));
+    };
+    // emit blocks that were open together: first-fit packing, largest first
+    auto emit = [&](std::vector<Block>& bs) {
+        std::sort(bs.begin(), bs.end(), [](const Block& x, const Block& y) { return x.q.size() > y.q.size(); });
+        std::vector<Block> packs;
+        for (auto& b : bs) {
+            bool placed = false;
+            for (auto& pk : packs)
+                if ((int)(pk.q.size() + b.q.size()) <= max_k) {
+                    merge_into(pk, b);
+                    placed = true;
+                    break;
+                }
+            if (!placed) packs.push_back(std::move(b));
+        }
+        for (auto& pk : packs) emit_one(pk);
+        bs.clear();
     };
     if (max_k <= 1) {
         for (auto& g : q) {
@@ -238,12 +258,13 @@ std::vector<Planned> plan_fusion(const std::vector<PendingGate>& q, int max_k) {
     }
     std::vector<Block> open;
     auto close_if = [&](uint64_t touch) {
-        std::vector<Block> keep;
+        std::vector<Block> keep, closed;
         for (auto& b : open) {
-            if (b.mask & touch) emit(b);
+            if (b.mask & touch) closed.push_back(std::move(b));
             else keep.push_back(std::move(b));
         }
         open.swap(keep);
+        emit(closed);
     };
     for (auto& g : q) {
         uint64_t gmask = 0;
@@ -257,38 +278,47 @@ std::vector<Planned> plan_fusion(const std::vector<PendingGate>& q, int max_k) {
             out.push_back(std::move(p));
             continue;
         }
+        // touched blocks, largest first; close from the front until the rest
+        // and the gate fit in max_k qubits
+        std::vector<int> touched;
+        for (int i = 0; i < (int)open.size(); ++i)
+            if (open[i].mask & gmask) touched.push_back(i);
+        std::sort(touched.begin(), touched.end(),
+                  [&](int x, int y) { return open[x].q.size() > open[y].q.size(); });
         uint64_t uni = gmask;
-        for (auto& b : open)
-            if (b.mask & gmask) uni |= b.mask;
+        for (int i : touched) uni |= open[i].mask;
+        uint64_t closing = 0;
+        for (size_t t = 0; t < touched.size() && __builtin_popcountll(uni) > max_k; ++t) {
+            const uint64_t m = open[touched[t]].mask;
+            closing |= m;
+            uni = gmask;
+            for (size_t u = t + 1; u < touched.size(); ++u) uni |= open[touched[u]].mask;
+        }
+        if (closing) close_if(closing);
+        // the remaining touched blocks act before the gate
         Block nb;
         nb.q.assign(g.q, g.q + g.k);
         nb.U = g.U;
         nb.mask = gmask;
         nb.gates = 1;
-        if (__builtin_popcountll(uni) <= max_k) {
-            // earlier blocks touching the gate act first
-            Block merged;
-            bool first = true;
-            std::vector<Block> keep;
-            for (auto& b : open) {
-                if (b.mask & gmask) {
-                    if (first) { merged = std::move(b); first = false; }
-                    else merge_into(merged, b);
-                } else {
-                    keep.push_back(std::move(b));
-                }
-            }
-            if (first) {
-                keep.push_back(std::move(nb));
+        Block merged;
+        bool first = true;
+        std::vector<Block> keep;
+        for (auto& b : open) {
+            if (b.mask & gmask) {
+                if (first) { merged = std::move(b); first = false; }
+                else merge_into(merged, b);
             } else {
-                merge_into(merged, nb);
-                keep.push_back(std::move(merged));
+                keep.push_back(std::move(b));
             }
-            open.swap(keep);
-        } else {
-            close_if(gmask);
-            open.push_back(std::move(nb));
         }
+        if (first) {
+            keep.push_back(std::move(nb));
+        } else {
+            merge_into(merged, nb);
+            keep.push_back(std::move(merged));
+        }
+        open.swap(keep);
     }
     close_if(~0ull);
     return out;
