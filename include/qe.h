@@ -225,6 +225,20 @@ int qe_set_cost_model(qe_state* s, qe_cost_model* model);
  * max_k, or the model's choice under QE_POLICY_AUTO), without applying them. */
 int qe_planned_fusion_width(qe_state* s, int* k);
 
+/* Host-only planning (no device work, no state): group ngates uncontrolled
+ * gates on n qubits into fused blocks of at most max_k (1..5) qubits exactly
+ * as the flush does (Sec. II, gate fusion).  Gate g acts on k[g] (1..5)
+ * qubits qubits[5 g + j], j < k[g], with the row-major 2^k x 2^k complex
+ * matrix (interleaved re, im doubles) at matrices + mat_offset[g] (doubles).
+ * Outputs, for blocks b < *nblocks (in application order): width
+ * block_k[b], qubits block_qubits[5 b + j] and matrix block_matrices +
+ * 2048 b (row-major, interleaved, width block_k[b]).  QE_ERR_ARG for invalid
+ * arguments or when more than cap blocks result (*nblocks then holds the
+ * count needed). */
+int qe_plan_fusion(int n, int ngates, const int* k, const int* qubits, const double* matrices,
+                   const int64_t* mat_offset, int max_k, int cap, int* nblocks, int* block_k,
+                   int* block_qubits, double* block_matrices);
+
 /* Per-kernel timing with CUDA events recorded on the state's stream around
  * every launch (measurement aid; the events add a few microseconds per
  * launch).  qe_profile_enable(s, 1) clears earlier records and starts

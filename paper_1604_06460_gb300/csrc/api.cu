@@ -420,6 +420,47 @@ static void check_batch(const qe_batch* b) {
 
 extern "C" {
 
+int qe_plan_fusion(int n, int ngates, const int* k, const int* qubits, const double* matrices,
+                   const int64_t* mat_offset, int max_k, int cap, int* nblocks, int* block_k,
+                   int* block_qubits, double* block_matrices) {
+    QE_API_BEGIN
+    if (n < 1 || n > 34) fail(QE_ERR_ARG, "n must be in [1, 34]");
+    if (ngates < 0 || (ngates > 0 && (!k || !qubits || !matrices || !mat_offset)))
+        fail(QE_ERR_ARG, "gate arrays are NULL");
+    if (max_k < 1 || max_k > 5) fail(QE_ERR_ARG, "max_k must be in [1, 5]");
+    if (!nblocks) fail(QE_ERR_ARG, "nblocks is NULL");
+    std::vector<PendingGate> q(ngates);
+    for (int g = 0; g < ngates; ++g) {
+        if (k[g] < 1 || k[g] > 5) fail(QE_ERR_ARG, "gate width must be in [1, 5]");
+        q[g].k = k[g];
+        uint64_t seen = 0;
+        for (int j = 0; j < k[g]; ++j) {
+            const int qq = qubits[5 * g + j];
+            if (qq < 0 || qq >= n || ((seen >> qq) & 1ull)) fail(QE_ERR_ARG, "qubit out of range or repeated");
+            seen |= 1ull << qq;
+            q[g].q[j] = qq;
+        }
+        const int D = 1 << k[g];
+        q[g].U.resize((size_t)D * D);
+        const double* m = matrices + mat_offset[g];
+        for (int i = 0; i < D * D; ++i) q[g].U[i] = cd(m[2 * i], m[2 * i + 1]);
+    }
+    const std::vector<Planned> plan = plan_fusion(q, max_k);
+    *nblocks = (int)plan.size();
+    if ((int)plan.size() > cap) fail(QE_ERR_ARG, "more blocks than cap");
+    if (!plan.empty() && (!block_k || !block_qubits || !block_matrices)) fail(QE_ERR_ARG, "output arrays are NULL");
+    for (size_t b = 0; b < plan.size(); ++b) {
+        const int kb = (int)plan[b].q.size();
+        block_k[b] = kb;
+        for (int j = 0; j < 5; ++j) block_qubits[5 * b + j] = j < kb ? plan[b].q[j] : -1;
+        for (size_t i = 0; i < plan[b].U.size(); ++i) {
+            block_matrices[2048 * b + 2 * i] = plan[b].U[i].real();
+            block_matrices[2048 * b + 2 * i + 1] = plan[b].U[i].imag();
+        }
+    }
+    QE_API_END
+}
+
 const char* qe_last_error(void) { return g_last_error.c_str(); }
 
 // Default fusion width: 5-qubit blocks where the tensor cores take them

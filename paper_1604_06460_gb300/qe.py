@@ -77,6 +77,7 @@ SIGNATURES = {
     "qe_cost_features": (_i, [_i, _i, _i, _i, _i, _i, _i, _u64, _vp]),
     "qe_set_cost_model": (_i, [_vp, _vp]),
     "qe_planned_fusion_width": (_i, [_vp, C.POINTER(_i)]),
+    "qe_plan_fusion": (_i, [_i, _i, _vp, _vp, _vp, _vp, _i, _i, C.POINTER(_i), _vp, _vp, _vp]),
     "qe_last_error": (C.c_char_p, []),
 }
 
@@ -353,6 +354,37 @@ def cost_features(op, n, dtype, k=0, lo=0, hi=0, m=0, c=0):
     _check(load().qe_cost_features(int(op), int(n), C128 if dtype == "c128" else C64, int(k),
                                    int(lo), int(hi), int(m), int(c) & ((1 << 64) - 1), _ptr(f)))
     return f
+
+
+def plan_fusion(n, gates, max_k):
+    """Host-only: the fused blocks (qubits, matrix) the flush would apply for
+    `gates` (objects with .qubits and .matrix, uncontrolled), in order."""
+    k = np.array([len(g.qubits) for g in gates], dtype=np.int32)
+    qb = np.full((max(len(gates), 1), 5), -1, dtype=np.int32)
+    mats, offs, off = [], [], 0
+    for i, g in enumerate(gates):
+        qb[i, :len(g.qubits)] = g.qubits
+        m = np.ascontiguousarray(np.asarray(g.matrix, dtype=np.complex128)).view(np.float64).ravel()
+        mats.append(m)
+        offs.append(off)
+        off += m.size
+    mat = np.concatenate(mats) if mats else np.zeros(1)
+    offs = np.array(offs or [0], dtype=np.int64)
+    cap = max(len(gates), 1)
+    nb = C.c_int(0)
+    bk = np.zeros(cap, dtype=np.int32)
+    bq = np.zeros((cap, 5), dtype=np.int32)
+    bm = np.zeros((cap, 2048), dtype=np.float64)
+    p = lambda a: a.ctypes.data_as(C.c_void_p)
+    _check(load().qe_plan_fusion(n, len(gates), p(k), p(qb), p(mat), p(offs), max_k, cap, C.byref(nb),
+                                 p(bk), p(bq), p(bm)))
+    out = []
+    for b in range(nb.value):
+        kb = int(bk[b])
+        D = 1 << kb
+        U = bm[b, :2 * D * D].view(np.complex128).reshape(D, D).copy()
+        out.append((list(bq[b, :kb]), U))
+    return out
 
 
 class CostModel:
