@@ -180,7 +180,8 @@ struct F64 {
 
 struct DF {
     using S = double2;
-    struct V { df re, im; };
+    // 16-byte aligned so that a value moves in one 128-bit shared-memory access
+    struct alignas(16) V { df re, im; };
     using M = V;
     struct A { float rs, re_, is, ie; };   // real (s,e), imaginary (s,e)
     static constexpr int bytes = 16;
