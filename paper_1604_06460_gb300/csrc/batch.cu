@@ -185,14 +185,22 @@ __device__ void tile_gates_reg(typename P::V* tile, int T, int b0, const typenam
 template <class P>
 __device__ void tile_gates(typename P::V* tile, int T, int b0, int cnt, const typename P::M* U, int gmax_arg) {
     // register budget: 16 complex64 or 8 double-float values per thread
-    const int gmax = gmax_arg;
+    // double-float groups hold at most 2 gates: wider groups are not even
+    // instantiated for it (their registers would spill)
+    constexpr bool wide = sizeof(typename P::V) < 16;
+    const int gmax = wide ? gmax_arg : (gmax_arg < 2 ? gmax_arg : 2);
     while (cnt > 0) {
         const int g = cnt >= gmax ? gmax : cnt;
-        switch (g) {
-            case 4: tile_gates_reg<P, 4>(tile, T, b0, U); break;
-            case 3: tile_gates_reg<P, 3>(tile, T, b0, U); break;
-            case 2: tile_gates_reg<P, 2>(tile, T, b0, U); break;
-            default: tile_gates_reg<P, 1>(tile, T, b0, U); break;
+        if constexpr (wide) {
+            switch (g) {
+                case 4: tile_gates_reg<P, 4>(tile, T, b0, U); break;
+                case 3: tile_gates_reg<P, 3>(tile, T, b0, U); break;
+                case 2: tile_gates_reg<P, 2>(tile, T, b0, U); break;
+                default: tile_gates_reg<P, 1>(tile, T, b0, U); break;
+            }
+        } else {
+            if (g == 2) tile_gates_reg<P, 2>(tile, T, b0, U);
+            else tile_gates_reg<P, 1>(tile, T, b0, U);
         }
         b0 += g;
         cnt -= g;
