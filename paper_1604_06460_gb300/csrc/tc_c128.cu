@@ -45,9 +45,12 @@
 // the next tile:
 //   workers: epilogue(t, X) | split(t+1) | epilogue(t, Y) | ...
 //   MMA warp:   MMA(t, Y)   |   ...      | MMA(t+1, X)    | MMA(t+1, Y) ...
+// An epilogue releases its accumulator set as soon as the values are in
+// registers, before recombining them.
 // The load warps copy the raw amplitudes of the next tile into a padded
 // staging buffer with cp.async as soon as the workers have split the current
-// one, and record each row's largest exponent.  Hand-offs use mbarriers (digits ready, set Y free, staging read:
+// one, record each row's largest exponent, and prefetch the tile after it
+// into L2 (bulk prefetches of its contiguous runs).  Hand-offs use mbarriers (digits ready, set Y free, staging read:
 // workers arrive; set X / Y done: tcgen05.commit; tile staged and
 // row exponents written); every wait has an iteration limit and the
 // workers leave their loop together when any of them times out.
@@ -139,6 +142,12 @@ __device__ __forceinline__ long long mad_wide(int a, int b, long long c) {
     long long d;
     asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
     return d;
+}
+
+// Bulk prefetch of `bytes` (a multiple of 16) at a 16-byte aligned global
+// address into L2.
+__device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ uint32_t biased_exp(double v) { return ((uint32_t)__double2hiint(v) >> 20) & 0x7FFu; }
@@ -386,6 +395,14 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
             const char* g = tile_ptr(t) + ro;
 #pragma unroll 8
             for (int c = 0; c < 32; ++c) cp_async16(d + 16u * c, g + coloff[c]);
+            // the tile after this one into L2 meanwhile: its 2^kh contiguous
+            // runs of 2^L amplitudes (>= 2 KB), one bulk prefetch each
+            const uint64_t tn = t + gridDim.x;
+            if (tn < a.ntiles) {
+                const char* gn = tile_ptr(tn);
+                for (int h = r; h < (1 << a.kh); h += 32 * kLoadWarps)
+                    l2_prefetch(gn + 16ull * hoff[h], 16u << a.L);
+            }
             // once the row has landed: its largest biased exponent, for the
             // workers' splitting
             asm volatile("cp.async.wait_all;" ::: "memory");
@@ -453,6 +470,11 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
                              : "r"(ta + 16u));
             }
             asm volatile("tcgen05.wait::ld.sync.aligned;");
+            // the accumulators are in registers now: set Y may be refilled
+            // while this thread recombines (set X is released with the next
+            // tile's digits)
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            if (hh) mbar_arrive(&mbYfree);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int c = 16 * hh + m0 + u;
@@ -466,7 +488,6 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
                 const double yi = recombine(ci, eterm + sF20[32 + c]);
                 *reinterpret_cast<double2*>(gb + coloff[c]) = make_double2(yr, yi);
             }
-            asm volatile("tcgen05.fence::before_thread_sync;");
         };
         uint32_t px = 0, py = 0, ps = 0;
         uint64_t t = blockIdx.x;
@@ -507,7 +528,6 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
                 break;
             }
             epilogue(1, gb, eterm);
-            mbar_arrive(&mbYfree);
             eterm = eterm_next;
         }
     }
