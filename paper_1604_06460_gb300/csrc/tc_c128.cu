@@ -40,20 +40,20 @@
 // Schedule: sixteen worker warps (four threads per group row) split and
 // recombine, one warp issues the MMAs, four warps stream tiles in.  The 64
 // outputs of a row are computed as two halves of 32 (16 complex columns
-// each) into two tensor-memory accumulator sets X and Y, so
-// the MMAs of one half overlap the epilogue of the other and the splitting of
-// the next tile:
+// each) into two tensor-memory accumulator sets X and Y, so the MMAs of one
+// half overlap the epilogue of the other and the splitting of the next tile:
 //   workers: epilogue(t, X) | split(t+1) | epilogue(t, Y) | ...
 //   MMA warp:   MMA(t, Y)   |   ...      | MMA(t+1, X)    | MMA(t+1, Y) ...
 // An epilogue releases its accumulator set as soon as the values are in
-// registers, before recombining them.
-// The load warps copy the raw amplitudes of the next tile into a padded
-// staging buffer with cp.async as soon as the workers have split the current
-// one, record each row's largest exponent, and prefetch the tile after it
-// into L2 (bulk prefetches of its contiguous runs).  Hand-offs use mbarriers (digits ready, set Y free, staging read:
-// workers arrive; set X / Y done: tcgen05.commit; tile staged and
-// row exponents written); every wait has an iteration limit and the
-// workers leave their loop together when any of them times out.
+// registers, before recombining them.  The load warps copy the raw
+// amplitudes of the next tile into a padded staging buffer with cp.async as
+// soon as the workers have split the current one, record each row's largest
+// exponent, and prefetch the tile after it into L2 (one bulk prefetch per
+// contiguous run).  Hand-offs use mbarriers (digits ready, set Y free,
+// staging read: workers arrive; set X / Y done: tcgen05.commit; tile staged
+// with its row exponents: load warps arrive); every wait has an iteration
+// limit, and the workers leave their loop together when any of them times
+// out.
 #include <cmath>
 #include <cstring>
 

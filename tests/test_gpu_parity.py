@@ -475,6 +475,23 @@ def test_tensor_core_blocks_c128(qe, qubits):
     close(got, ref)
 
 
+@pytest.mark.parametrize("n,qubits", [(12, [0, 4, 7, 9, 11]), (12, [11, 10, 9, 8, 7]), (13, [12, 0, 6, 3, 9]),
+                                      (13, [12, 11, 1])])
+def test_tensor_core_c128_smallest_states(qe, n, qubits):
+    # n = 12: one tile holds the whole state (a single CTA); n = 13: two tiles;
+    # the highest qubits as gate qubits
+    U = rand_unitary(1 << len(qubits), np.random.default_rng(n * 31 + len(qubits)))
+    psi = I.random_state(n, 5)
+    with make(qe, n, "c128", psi=psi, max_k=5) as st:
+        st.profile(True)
+        st.apply_gate(qubits, U)
+        got = st.get()
+        prof = st.profile_read()
+        st.profile(False)
+    assert prof.get("gate_tc_k5_c128", (0,))[0] == 1
+    close(got, oracle.apply_gate(psi, qubits, U))
+
+
 def test_tensor_core_c128_special_values(qe):
     # a basis state (all but one amplitude zero), amplitudes that are powers of
     # two (the splitting's binade edges), +-1 entries, and rows below the flush
