@@ -37,23 +37,27 @@
 // 2^-48 of the group norm, with no FP64 arithmetic but the final conversion.
 // Rows whose largest magnitude is below 2^-920 are flushed to zero.
 //
-// Schedule: sixteen worker warps (four threads per group row) split and
-// recombine, one warp issues the MMAs, four warps stream tiles in.  The 64
-// outputs of a row are computed as two halves of 32 (16 complex columns
-// each) into two tensor-memory accumulator sets X and Y, so the MMAs of one
-// half overlap the epilogue of the other and the splitting of the next tile:
-//   workers: epilogue(t, X) | split(t+1) | epilogue(t, Y) | ...
-//   MMA warp:   MMA(t, Y)   |   ...      | MMA(t+1, X)    | MMA(t+1, Y) ...
-// An epilogue releases its accumulator set as soon as the values are in
-// registers, before recombining them.  The load warps copy the raw
+// Schedule (warp-specialised, one CTA per SM, persistent over tiles): eight
+// warps split (two threads per group row), eight warps recombine (two per
+// tensor-memory lane quarter), one warp issues the MMAs and four warps
+// stream tiles in.  The 64 outputs of a row are computed as two halves of 32
+// (16 complex columns each) into two tensor-memory accumulator sets X and Y.
+// Per tile the MMAs run in the order X(real K), Y(real K), X(imaginary K),
+// Y(imaginary K), so the digit slices are released in two parts: the
+// splitters write the next tile's real-part digits as soon as both sets have
+// consumed the current real parts, and its imaginary-part digits once the
+// tile's last MMA is done.  The splitting of tile t + 1 (integer ALU work)
+// thus overlaps the recombination of tile t (whose int64 -> double
+// conversions run on the FP64 pipe), and a set is released to the MMAs as
+// soon as its accumulators are in registers.  The load warps copy the raw
 // amplitudes of the next tile into a padded staging buffer with cp.async as
-// soon as the workers have split the current one, record each row's largest
+// soon as the splitters have read the current one, record each row's largest
 // exponent, and prefetch the tile after it into L2 (one bulk prefetch per
-// contiguous run).  Hand-offs use mbarriers (digits ready, set Y free,
-// staging read: workers arrive; set X / Y done: tcgen05.commit; tile staged
-// with its row exponents: load warps arrive); every wait has an iteration
-// limit, and the workers leave their loop together when any of them times
-// out.
+// contiguous run).  Every hand-off is an mbarrier (count-based arrivals by
+// threads, tcgen05.commit for MMA completion); every wait has an iteration
+// limit, after which the waiting thread raises a shared abort flag that ends
+// the waits of all other threads, and the MMA warp waits for its own MMAs
+// before tensor memory is freed.
 #include <cmath>
 #include <cstring>
 
@@ -68,10 +72,12 @@ namespace {
 using tc::mbar_wait;
 using tc::smem_u32;
 
-constexpr int kWorkers = 512;                // 16 warps: splitting and epilogue
-constexpr int kLoadWarps = 4;
-constexpr int kOzThreads = kWorkers + 32 + 32 * kLoadWarps;   // + 1 warp issuing the MMAs, 4 loading tiles
-constexpr int kMmaWarp = kWorkers / 32, kLoadWarp0 = kWorkers / 32 + 1;
+constexpr int kEpiWarps = 8;                 // warps [0, 8): recombination, two per TMEM lane quarter
+constexpr int kSplitWarps = 8;               // warps [8, 16): splitting, two threads per group row
+constexpr int kLoadWarps = 2;                // one group row of each staged half per thread
+constexpr int kSplitWarp0 = kEpiWarps, kMmaWarp = kEpiWarps + kSplitWarps, kLoadWarp0 = kMmaWarp + 1;
+constexpr int kOzThreads = 32 * (kLoadWarp0 + kLoadWarps);   // 608: at most 5 warps per SM sub-partition
+constexpr int kSplitThreads = 32 * kSplitWarps, kEpiThreads = 32 * kEpiWarps;
 constexpr int kRows = 128;                    // groups per tile (MMA M)
 constexpr int kK = 64;                        // real K
 constexpr int kN = 64;                        // real N (two halves of 32)
@@ -83,6 +89,8 @@ constexpr uint32_t kSetY = 256;               // column of the second set
 constexpr uint32_t kSliceA = kRows * 128;     // bytes of one digit slice of In (fp16, 128 B per row)
 constexpr uint32_t kSliceB = kN * 128;        // bytes of one digit slice of W
 constexpr uint32_t kStageRow = 32 * 16 + 16;  // staged row of 32 complex128, padded by 16 bytes
+constexpr int kHalfRows = kRows / 2;          // the staging buffer holds the two halves of a tile's rows
+constexpr uint32_t kHalfStage = kHalfRows * kStageRow;
 constexpr uint32_t kStackB = kDigits * kNH * 128; // bytes of one half's stack of the six W' digit slices
 constexpr int kFlushExp = 100;                // biased exponent below which a row is flushed
 
@@ -117,25 +125,36 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src));
 }
 
+// Arrive on the mbarrier once every cp.async issued so far by this thread
+// has landed (the arrival is counted in the barrier's expected count).
+__device__ __forceinline__ void cp_async_arrive(uint64_t* mbar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
 __device__ __forceinline__ void mbar_init_count(uint64_t* mbar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
 }
-// True on every worker thread when p holds on any of them (a barrier of the
-// workers that all reach, so a timed-out wait ends the loop on all of them).
-__device__ __forceinline__ bool workers_any(bool p) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred a, b;\n\t"
-        "setp.ne.u32 a, %1, 0;\n\t"
-        "bar.red.or.pred b, 2, %2, a;\n\t"
-        "selp.u32 %0, 1, 0, b;\n\t}\n"
-        : "=r"(r)
-        : "r"((uint32_t)p), "n"(kWorkers)
-        : "memory");
-    return r != 0;
+// Wait for phase `phase` of an mbarrier.  False when the shared abort flag
+// is raised (checked every 32 polls) or after `limit` polls, in which case
+// this thread raises it.
+__device__ __forceinline__ bool wait_or_abort(uint32_t mbar, uint32_t phase, long long limit, uint32_t* abort_flag) {
+    for (long long i = 0; i < limit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+        if (done) return true;
+        if ((i & 31) == 31 && *reinterpret_cast<volatile uint32_t*>(abort_flag)) return false;
+    }
+    *reinterpret_cast<volatile uint32_t*>(abort_flag) = 1u;
+    return false;
 }
 
 __device__ __forceinline__ long long mad_wide(int a, int b, long long c) {
@@ -202,9 +221,8 @@ __device__ __forceinline__ void digit_pairs(const Zw& A, const Zw& B, uint32_t w
     w[5] = hfma2(mag(A.zl, B.zl, 0u), sf, c1);
 }
 
-// Output value from the seven accumulators (raw FP32 bits); eadj = (E_r +
-// F_n - 56) << 20 shifts the exponent.
-__device__ __forceinline__ double recombine(const uint32_t c[kAcc], int eadj) {
+// The integer Y of one output from its seven accumulators (raw FP32 bits).
+__device__ __forceinline__ long long combine_y(const uint32_t c[kAcc]) {
     const float M = 12582912.0f;   // 1.5 * 2^23; bits 0x4B400000
     const uint32_t u2 = __float_as_uint(__fadd_rn(__uint_as_float(c[0]), M));
     const uint32_t u3 = __float_as_uint(__fadd_rn(__uint_as_float(c[1]), M));
@@ -216,11 +234,34 @@ __device__ __forceinline__ double recombine(const uint32_t c[kAcc], int eadj) {
     long long Y = mad_wide(c6, 256, (long long)c78);
     Y = mad_wide(c5, 1 << 16, Y);
     Y = mad_wide(c4, 1 << 24, Y);
-    Y += (long long)H << 32;
+    return Y + ((long long)H << 32);
+}
+
+// Y as a double, its exponent shifted by eadj = (E_r + F_n - 56) << 20.
+__device__ __forceinline__ double finish_y(long long Y, int eadj) {
     const double y = __ll2double_rn(Y);
     const int hi = __double2hiint(y);
     return __hiloint2double(hi == 0 ? 0 : hi + eadj, __double2loint(y));
 }
+
+// mbarriers of the kernel
+enum Bar {
+    kReReady,     // splitters: real-part digits of the tile written (256 arrivals)
+    kImReady,     // splitters: imaginary-part digits written (256)
+    kReFree,      // commit: the MMAs over the real-part digits are done
+    kXFull,       // commit: set X holds the tile's first half
+    kYFull,       // commit: set Y holds the second half; all digits consumed
+    kXFree,       // recombiners: set X read into registers (256)
+    kYFree,       // recombiners: set Y read (256)
+    kStage0,      // load warps: rows [0, 64) of the tile staged (64 cp.async arrivals)
+    kStage1,      // rows [64, 128) staged
+    kStageFree0,  // splitters: staged half 0 read (256)
+    kStageFree1,  // staged half 1 read
+    kEt0,         // splitters: row scales of the tile, ring slot 0 / 1 (128)
+    kEt1,
+    kDrain,       // commit: every MMA issued has completed
+    kBars
+};
 
 // The MMA-issuing thread.  The accumulators of one half lie side by side,
 // C_d at column 32 (d - 2), and each half's W' digit slices are stacked along
@@ -228,12 +269,12 @@ __device__ __forceinline__ double recombine(const uint32_t c[kAcc], int eadj) {
 // j0..j1 writes C_{i + j0} .. C_{i + j1} at once: the digit products form a
 // convolution.  Per K-step and half: (1,1) and (2,1..6) start the sums, then
 // (1,2..6), (3,1..5), (4,1..4), (5,1..3), (6,1..2) add to them (26 pairs in 7
-// MMAs).  Per tile: the first half's K-steps over the real parts start as
-// soon as those digits are split, its imaginary-part K-steps when the rest
-// is; the second half follows once set Y is free; each half is committed to
-// its own mbarrier.
-__device__ __noinline__ void issue_mmas(const OzArgs& a, uint32_t tmem, uint32_t a0, uint32_t b0, uint64_t* mbAre,
-                                        uint64_t* mbA, uint64_t* mbYfree, uint64_t* mbX, uint64_t* mbY) {
+// MMAs).  Per tile: both halves' K-steps over the real parts (each half once
+// its set is free), a commit that releases the real-part digits, then the
+// imaginary-part K-steps of X (committed: X full) and of Y (committed: Y
+// full and every digit consumed).  False when a wait ran out.
+__device__ __noinline__ bool issue_mmas(const OzArgs& a, uint32_t tmem, uint32_t a0, uint32_t b0, uint64_t* bars,
+                                        uint32_t* abort_flag) {
     // (i, j0, j1) in issue order
     constexpr int kI[7] = {1, 2, 1, 3, 4, 5, 6};
     constexpr int kJ0[7] = {1, 1, 2, 1, 1, 1, 1};
@@ -256,56 +297,44 @@ __device__ __noinline__ void issue_mmas(const OzArgs& a, uint32_t tmem, uint32_t
             }
         }
     };
-    uint32_t pre = 0, pa = 0, pyf = 0;
+    auto wait = [&](Bar b, uint32_t& ph) {
+        if (!wait_or_abort(smem_u32(&bars[b]), ph, a.spin_limit, abort_flag)) return false;
+        ph ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        return true;
+    };
+    uint32_t pre = 0, pim = 0, pxf = 0, pyf = 0;
     bool first = true;
     for (uint64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-        // half X: K-steps 0, 1 (real parts) as soon as they are split
-        if (!mbar_wait(smem_u32(mbAre), pre, a.spin_limit)) {
-            atomicExch(a.status, 1u);
-            return;
-        }
-        pre ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (!wait(kReReady, pre)) return false;
+        if (!first && !wait(kXFree, pxf)) return false;
         issue(0, 0, 2);
-        if (!mbar_wait(smem_u32(mbA), pa, a.spin_limit)) {
-            atomicExch(a.status, 1u);
-            return;
-        }
-        pa ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (!first && !wait(kYFree, pyf)) return false;
+        issue(1, 0, 2);
+        tc::mma_commit(&bars[kReFree]);
+        if (!wait(kImReady, pim)) return false;
         issue(0, 2, 4);
-        tc::mma_commit(mbX);
-        // half Y once its accumulators are free
-        if (!first) {
-            if (!mbar_wait(smem_u32(mbYfree), pyf, a.spin_limit)) {
-                atomicExch(a.status, 1u);
-                return;
-            }
-            pyf ^= 1u;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        issue(1, 0, 4);
-        tc::mma_commit(mbY);
+        tc::mma_commit(&bars[kXFull]);
+        issue(1, 2, 4);
+        tc::mma_commit(&bars[kYFull]);
         first = false;
     }
+    return true;
 }
 
-__global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_constant__ OzArgs a) {
+__global__ void __maxnreg__(96) k_gate_tc5_c128(const __grid_constant__ OzArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char* sA = base;                                   // 6 digit slices of In
     unsigned char* sB = sA + kDigits * kSliceA;                 // per half: the 6 W' digit slices stacked
     unsigned char* stage = sB + kDigits * kSliceB;              // raw amplitudes of one tile
-    // mbarriers: A digits ready (real parts; all: workers arrive), accumulator set Y free
-    // (workers arrive), MMAs into set X / set Y complete (tcgen05.commit),
-    // tile staged (load warps arrive with the row exponents), staging read (workers arrive)
-    __shared__ __align__(8) uint64_t mbAre, mbA, mbYfree, mbX, mbY, mbStage, mbStageFree;
-    __shared__ uint32_t tmem_base;
+    __shared__ __align__(8) uint64_t bars[kBars];
+    __shared__ uint32_t tmem_base, abort_flag;
     __shared__ uint64_t hoff[32];
     __shared__ uint32_t cpos[32];
     __shared__ uint64_t coloff[32];
     __shared__ int sF20[kN];
-    __shared__ uint32_t s_em[kRows];     // largest biased exponent of each staged row
+    __shared__ int s_eterm[2][kRows];          // (E_r - 56) << 20 of the rows of two tiles in flight
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     // W' digits into their swizzled operand layout; W row scales
@@ -330,13 +359,11 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
         cpos[tid] = o;
     }
     if (tid == 0) {
-        mbar_init_count(&mbAre, kWorkers);
-        mbar_init_count(&mbA, kWorkers);
-        mbar_init_count(&mbYfree, kWorkers);
-        mbar_init_count(&mbX, 1);
-        mbar_init_count(&mbY, 1);
-        mbar_init_count(&mbStage, 32 * kLoadWarps);   // one arrival per staged row
-        mbar_init_count(&mbStageFree, kWorkers);
+        const uint32_t counts[kBars] = {kSplitThreads, kSplitThreads, 1,      1, 1, kEpiThreads, kEpiThreads,
+                                        32 * kLoadWarps, 32 * kLoadWarps, kSplitThreads, kSplitThreads,
+                                        kRows,         kRows,         1};
+        for (int b = 0; b < kBars; ++b) mbar_init_count(&bars[b], counts[b]);
+        abort_flag = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == kMmaWarp) {
@@ -370,94 +397,144 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
     };
     char* const xb = reinterpret_cast<char*>(a.x);
     auto tile_ptr = [&](uint64_t t) { return xb + 16ull * insert_zero_bits(t << a.L, a.hq, a.kh); };
+    // wait (all lanes of a warp) for a phase of barrier b; on a timeout or an
+    // abort raise the status word.  The outcome is the same on every lane,
+    // so the warp stays converged for its .sync.aligned instructions.
+    auto wait = [&](Bar b, uint32_t& ph) {
+        const bool ok = wait_or_abort(smem_u32(&bars[b]), ph, a.spin_limit, &abort_flag);
+        if (__any_sync(0xFFFFFFFFu, !ok)) {
+            if (!ok) atomicExch(a.status, 1u);
+            return false;
+        }
+        ph ^= 1u;
+        return true;
+    };
     if (warp == kMmaWarp) {
         // ---------------------------------------------------- MMA issuer
-        if (lane == 0) issue_mmas(a, tmem, smem_u32(sA), smem_u32(sB), &mbAre, &mbA, &mbYfree, &mbX, &mbY);
+        if (lane == 0) {
+            if (!issue_mmas(a, tmem, smem_u32(sA), smem_u32(sB), bars, &abort_flag)) atomicExch(a.status, 1u);
+            // every MMA issued has completed before tensor memory is freed
+            tc::mma_commit(&bars[kDrain]);
+            if (!tc::mbar_wait(smem_u32(&bars[kDrain]), 0u, a.spin_limit)) atomicExch(a.status, 1u);
+        }
         __syncwarp();
     } else if (warp >= kLoadWarp0) {
         // ------------------------------------------------------- tile loads
-        // thread <-> group row: 32 16-byte copies into the padded staging
-        // buffer per tile, completion signalled on mbStage
-        const int r = tid - kLoadWarp0 * 32;
-        const uint64_t ro = row_off(r);
-        const uint32_t d = smem_u32(stage) + (uint32_t)r * kStageRow;
-        uint32_t pf = 0;
-        bool first = true;
-        for (uint64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-            if (!first) {
-                if (!mbar_wait(smem_u32(&mbStageFree), pf, a.spin_limit)) {
-                    atomicExch(a.status, 1u);
+        // thread <-> group row i of each staged half: per half, once the
+        // splitters have read it, 32 16-byte copies into the padded staging
+        // buffer and an arrival on the half's stage barrier when they land
+        const int i = tid - kLoadWarp0 * 32;
+        const uint64_t ro[2] = {row_off(i), row_off(kHalfRows + i)};
+        const uint32_t d = smem_u32(stage) + (uint32_t)i * kStageRow;
+        uint32_t pf[2] = {0u, 0u};
+        bool first = true, ok = true;
+        for (uint64_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+            const char* g = tile_ptr(t);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (!first && !wait(h ? kStageFree1 : kStageFree0, pf[h])) {
+                    ok = false;
                     break;
                 }
-                pf ^= 1u;
+                const char* gr = g + ro[h];
+                const uint32_t dh = d + (uint32_t)h * kHalfStage;
+#pragma unroll 8
+                for (int c = 0; c < 32; ++c) cp_async16(dh + 16u * c, gr + coloff[c]);
+                cp_async_arrive(&bars[h ? kStage1 : kStage0]);
             }
             first = false;
-            const char* g = tile_ptr(t) + ro;
-#pragma unroll 8
-            for (int c = 0; c < 32; ++c) cp_async16(d + 16u * c, g + coloff[c]);
             // the tile after this one into L2 meanwhile: its 2^kh contiguous
             // runs of 2^L amplitudes (>= 2 KB), one bulk prefetch each
             const uint64_t tn = t + gridDim.x;
-            if (tn < a.ntiles) {
+            if (ok && tn < a.ntiles) {
                 const char* gn = tile_ptr(tn);
-                for (int h = r; h < (1 << a.kh); h += 32 * kLoadWarps)
-                    l2_prefetch(gn + 16ull * hoff[h], 16u << a.L);
+                for (int h = i; h < (1 << a.kh); h += 32 * kLoadWarps) l2_prefetch(gn + 16ull * hoff[h], 16u << a.L);
             }
-            // once the row has landed: its largest biased exponent, for the
-            // workers' splitting
-            asm volatile("cp.async.wait_all;" ::: "memory");
-            const double2* row = reinterpret_cast<const double2*>(stage + r * kStageRow);
-            uint32_t em = 0;
-#pragma unroll 8
-            for (int c = 0; c < 32; ++c) {
-                const double2 v = row[c];
-                em = max(em, max(biased_exp(v.x), biased_exp(v.y)));
-            }
-            s_em[r] = em;
-            mbar_arrive(&mbStage);
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
-    } else {
-        // ------------------------------------------ splitting and epilogue
-        const int r = ((warp & 3) << 5) | lane;   // group row = TMEM lane
-        const int qq = warp >> 2;                 // complex columns [8 qq, 8 qq + 8)
-        const uint64_t rowoff = row_off(r);
-        auto tile_base = [&](uint64_t t) { return tile_ptr(t) + rowoff; };
-        // digits of this thread's 16 values into the six operand slices
-        // (chunk qq: real parts, chunk 4 + qq: imaginary parts); returns
-        // (E_r - 56) << 20
-        auto split_tile = [&]() -> int {
-            const double2* srow = reinterpret_cast<const double2*>(stage + r * kStageRow + qq * 128);
-            const uint32_t em = s_em[r];    // the row's largest biased exponent (load warps)
-            const uint32_t base_s = (em < (uint32_t)kFlushExp) ? 0x10000u : em + 5u;
-#pragma unroll
-            for (int part = 0; part < 2; ++part) {
-                uint32_t w[kDigits][4];      // packed fp16 pairs: slice i, values 2p, 2p + 1
-#pragma unroll
-                for (int p2 = 0; p2 < 4; ++p2) {
-                    const double2 va = srow[2 * p2], vb = srow[2 * p2 + 1];
-                    uint32_t d[kDigits];
-                    digit_pairs(split_z(part ? va.y : va.x, base_s), split_z(part ? vb.y : vb.x, base_s), d);
-#pragma unroll
-                    for (int i = 0; i < kDigits; ++i) w[i][p2] = d[i];
+    } else if (warp >= kSplitWarp0) {
+        // -------------------------------------------------------- splitting
+        // thread <-> (row 64 h + ri of each half h, complex columns
+        // [8 qq, 8 qq + 8)); the four threads of a row are lanes l, l ^ 8,
+        // l ^ 16, l ^ 24 of one warp.  Per half: the 8 amplitudes into
+        // registers (the staging half is then released), the row's largest
+        // exponent by two shuffles, the real-part digits (operand chunk qq),
+        // then the imaginary-part digits (chunk 4 + qq).
+        const int sw = warp - kSplitWarp0;
+        const int ri = 8 * sw + (lane & 7), qq = lane >> 3;
+        const unsigned char* const srow = stage + ri * kStageRow + qq * 128;
+        uint32_t prf = 0, pyf = 0;
+        bool first = true, ok = true;
+        int it = 0;
+        for (uint64_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++it) {
+            const uint32_t ph = (uint32_t)it & 1u;    // each stage barrier completes once per tile
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                uint32_t phh = ph;
+                if (!wait(h ? kStage1 : kStage0, phh)) {
+                    ok = false;
+                    break;
                 }
-                const uint32_t off = sw128_chunk(r, part * 4 + qq);
+                const int r = kHalfRows * h + ri;
+                double2 v[8];
+                const double2* src = reinterpret_cast<const double2*>(srow + (uint32_t)h * kHalfStage);
 #pragma unroll
-                for (int i = 0; i < kDigits; ++i)
-                    *reinterpret_cast<uint4*>(sA + i * kSliceA + off) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
-                // the real parts (K 0..31) go to the tensor cores first
-                asm volatile("fence.proxy.async.shared::cta;");
-                mbar_arrive(part ? &mbA : &mbAre);
+                for (int k = 0; k < 8; ++k) v[k] = src[k];
+                mbar_arrive(&bars[h ? kStageFree1 : kStageFree0]);
+                uint32_t em = 0;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) em = max(em, max(biased_exp(v[k].x), biased_exp(v[k].y)));
+                em = max(em, __shfl_xor_sync(0xFFFFFFFFu, em, 8));
+                em = max(em, __shfl_xor_sync(0xFFFFFFFFu, em, 16));
+                const uint32_t base_s = (em < (uint32_t)kFlushExp) ? 0x10000u : em + 5u;
+#pragma unroll
+                for (int part = 0; part < 2; ++part) {
+                    uint32_t w[kDigits][4];      // packed fp16 pairs: slice i, values 2p, 2p + 1
+#pragma unroll
+                    for (int p2 = 0; p2 < 4; ++p2) {
+                        const double2 va = v[2 * p2], vb = v[2 * p2 + 1];
+                        uint32_t dg[kDigits];
+                        digit_pairs(split_z(part ? va.y : va.x, base_s), split_z(part ? vb.y : vb.x, base_s), dg);
+#pragma unroll
+                        for (int k = 0; k < kDigits; ++k) w[k][p2] = dg[k];
+                    }
+                    // the previous tile's MMAs over this part are done
+                    if (h == 0 && !first && !(part ? wait(kYFull, pyf) : wait(kReFree, prf))) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t off = sw128_chunk(r, part * 4 + qq);
+#pragma unroll
+                    for (int k = 0; k < kDigits; ++k)
+                        *reinterpret_cast<uint4*>(sA + k * kSliceA + off) = make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]);
+                    if (part == 0 && qq == 0) {
+                        // the row scale, for the recombination of this tile
+                        // (the slot's previous tile was read before set X
+                        // was released for the previous tile's MMAs)
+                        s_eterm[it & 1][r] = ((int)em - 1021 - 56) * (1 << 20);
+                        mbar_arrive(&bars[(it & 1) ? kEt1 : kEt0]);
+                    }
+                    if (h == 1) {
+                        asm volatile("fence.proxy.async.shared::cta;");
+                        mbar_arrive(&bars[part ? kImReady : kReReady]);
+                    }
+                }
+                if (!ok) break;
             }
-            return ((int)em - 1021 - 56) * (1 << 20);
-        };
-        // outputs of accumulator set hh: this thread's 4 complex columns
-        // 16 hh + 4 qq + [0, 4); set column m < 16 is the real part of complex
-        // column 16 hh + m, m >= 16 the imaginary part of 16 hh + m - 16
+            first = false;
+        }
+    } else {
+        // ---------------------------------------------------- recombination
+        // thread <-> (row r = TMEM lane, complex columns [8 eh, 8 eh + 8) of
+        // each half); set column m < 16 is the real part of complex column
+        // 16 hh + m, m >= 16 the imaginary part of 16 hh + m - 16
+        const int eh = warp >> 2;
+        const int r = ((warp & 3) << 5) | lane;
+        const uint64_t rowoff = row_off(r);
         const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-        auto epilogue = [&](int hh, char* gb, int eterm) {
-            const uint32_t set = lane_base + (hh ? kSetY : 0u);
-            const int m0 = 4 * qq;
+        // the accumulators of 4 complex columns m0 .. m0 + 3 of set hh as
+        // the integers Y (re, im interleaved)
+        auto load_y = [&](uint32_t set, int m0, long long y[8], Bar release) {
             uint32_t re[kAcc][4], im[kAcc][4];
 #pragma unroll
             for (int k = 0; k < kAcc; ++k) {
@@ -470,65 +547,55 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gate_tc5_c128(const __grid_co
                              : "r"(ta + 16u));
             }
             asm volatile("tcgen05.wait::ld.sync.aligned;");
-            // the accumulators are in registers now: set Y may be refilled
-            // while this thread recombines (set X is released with the next
-            // tile's digits)
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            if (hh) mbar_arrive(&mbYfree);
+            if (release != kBars) {
+                // the set's accumulators are all in registers: it may be refilled
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                mbar_arrive(&bars[release]);
+            }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int c = 16 * hh + m0 + u;
                 uint32_t cr[kAcc], ci[kAcc];
 #pragma unroll
                 for (int k = 0; k < kAcc; ++k) {
                     cr[k] = re[k][u];
                     ci[k] = im[k][u];
                 }
-                const double yr = recombine(cr, eterm + sF20[c]);
-                const double yi = recombine(ci, eterm + sF20[32 + c]);
-                *reinterpret_cast<double2*>(gb + coloff[c]) = make_double2(yr, yi);
+                y[2 * u] = combine_y(cr);
+                y[2 * u + 1] = combine_y(ci);
             }
         };
-        uint32_t px = 0, py = 0, ps = 0;
-        uint64_t t = blockIdx.x;
-        int eterm = 0;
-        // staged tile -> digits; false when a wait ran out (on every worker)
-        auto split_next = [&](int& et) {
-            if (workers_any(!mbar_wait(smem_u32(&mbStage), ps, a.spin_limit))) return false;
-            ps ^= 1u;
-            et = split_tile();
-            mbar_arrive(&mbStageFree);
-            return true;
+        auto store = [&](char* gb, int c0, const long long y[8], int eterm) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = c0 + u;
+                *reinterpret_cast<double2*>(gb + coloff[c]) =
+                    make_double2(finish_y(y[2 * u], eterm + sF20[c]), finish_y(y[2 * u + 1], eterm + sF20[32 + c]));
+            }
         };
-        if (t < a.ntiles && !split_next(eterm)) {
-            atomicExch(a.status, 1u);
-            t = a.ntiles;
-        }
-        for (; t < a.ntiles; t += gridDim.x) {
-            const uint64_t tn = t + gridDim.x;
-            char* gb = tile_base(t);
-            // outputs of the first half (set X)
-            if (workers_any(!mbar_wait(smem_u32(&mbX), px, a.spin_limit))) {
-                atomicExch(a.status, 1u);
-                break;
+        uint32_t px = 0, py = 0;
+        int it = 0;
+        for (uint64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
+            char* gb = tile_ptr(t) + rowoff;
+            const int slot = it & 1;
+            uint32_t pet = (uint32_t)(it >> 1) & 1u;     // each slot completes every other tile
+            if (!wait(slot ? kEt1 : kEt0, pet)) break;
+            const int eterm = s_eterm[slot][r];
+            bool ok = true;
+#pragma unroll 1
+            for (int hh = 0; hh < 2; ++hh) {
+                if (!wait(hh ? kYFull : kXFull, hh ? py : px)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t set = lane_base + (hh ? kSetY : 0u);
+                long long ya[8], yb[8];
+                load_y(set, 8 * eh, ya, kBars);
+                load_y(set, 8 * eh + 4, yb, hh ? kYFree : kXFree);
+                store(gb, 16 * hh + 8 * eh, ya, eterm);
+                store(gb, 16 * hh + 8 * eh + 4, yb, eterm);
             }
-            px ^= 1u;
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            epilogue(0, gb, eterm);
-            // second-half MMAs done: the digit slices are free
-            if (workers_any(!mbar_wait(smem_u32(&mbY), py, a.spin_limit))) {
-                atomicExch(a.status, 1u);
-                break;
-            }
-            py ^= 1u;
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            int eterm_next = 0;
-            if (tn < a.ntiles && !split_next(eterm_next)) {
-                atomicExch(a.status, 1u);
-                break;
-            }
-            epilogue(1, gb, eterm);
-            eterm = eterm_next;
+            if (!ok) break;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
