@@ -38,10 +38,10 @@
 // Rows whose largest magnitude is below 2^-920 are flushed to zero.
 //
 // Schedule (warp-specialised, one CTA per SM, persistent over tiles): eight
-// warps split (two threads per group row), eight warps recombine (two per
-// tensor-memory lane quarter), one warp issues the MMAs and four warps
-// stream tiles in.  The 64 outputs of a row are computed as two halves of 32
-// (16 complex columns each) into two tensor-memory accumulator sets X and Y.
+// warps split (four threads per group row), eight warps recombine (two per
+// tensor-memory lane quarter), one warp issues the MMAs and two warps stream
+// tiles in.  The 64 outputs of a row are computed as two halves of 32 (16
+// complex columns each) into two tensor-memory accumulator sets X and Y.
 // Per tile the MMAs run in the order X(real K), Y(real K), X(imaginary K),
 // Y(imaginary K), so the digit slices are released in two parts: the
 // splitters write the next tile's real-part digits as soon as both sets have
@@ -49,15 +49,17 @@
 // tile's last MMA is done.  The splitting of tile t + 1 (integer ALU work)
 // thus overlaps the recombination of tile t (whose int64 -> double
 // conversions run on the FP64 pipe), and a set is released to the MMAs as
-// soon as its accumulators are in registers.  The load warps copy the raw
-// amplitudes of the next tile into a padded staging buffer with cp.async as
-// soon as the splitters have read the current one, record each row's largest
-// exponent, and prefetch the tile after it into L2 (one bulk prefetch per
-// contiguous run).  Every hand-off is an mbarrier (count-based arrivals by
-// threads, tcgen05.commit for MMA completion); every wait has an iteration
-// limit, after which the waiting thread raises a shared abort flag that ends
-// the waits of all other threads, and the MMA warp waits for its own MMAs
-// before tensor memory is freed.
+// soon as its accumulators are in registers.  The staging buffer holds the
+// raw amplitudes of a tile as two halves of 64 rows, each column-major; the
+// load warps refill a half with cp.async as soon as the splitters have read
+// it into registers (completion is signalled on the half's mbarrier), and
+// prefetch the next tile into L2 (one bulk prefetch per contiguous run).  The
+// splitters derive each row's largest exponent from the values they hold.
+// Every hand-off is an mbarrier (count-based arrivals by threads,
+// tcgen05.commit for MMA completion); waits suspend the thread until the
+// phase completes, have an iteration limit, and on a timeout raise a shared
+// abort flag that ends the waits of all other threads; the MMA warp waits for
+// its own MMAs before tensor memory is freed.
 #include <cmath>
 #include <cstring>
 
@@ -88,9 +90,8 @@ constexpr uint32_t kTmemCols = 512;           // two accumulator sets of 7 x 32 
 constexpr uint32_t kSetY = 256;               // column of the second set
 constexpr uint32_t kSliceA = kRows * 128;     // bytes of one digit slice of In (fp16, 128 B per row)
 constexpr uint32_t kSliceB = kN * 128;        // bytes of one digit slice of W
-constexpr uint32_t kStageRow = 32 * 16 + 16;  // staged row of 32 complex128, padded by 16 bytes
-constexpr int kHalfRows = kRows / 2;          // the staging buffer holds the two halves of a tile's rows
-constexpr uint32_t kHalfStage = kHalfRows * kStageRow;
+constexpr int kHalfRows = kRows / 2;          // the staging buffer holds the two halves of a tile's rows,
+constexpr uint32_t kHalfStage = kHalfRows * 32 * 16;   // each column-major: amplitude (row, column c) at 16 (64 c + row)
 constexpr uint32_t kStackB = kDigits * kNH * 128; // bytes of one half's stack of the six W' digit slices
 constexpr int kFlushExp = 100;                // biased exponent below which a row is flushed
 
@@ -137,21 +138,23 @@ __device__ __forceinline__ void mbar_init_count(uint64_t* mbar, uint32_t count) 
 __device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
 }
-// Wait for phase `phase` of an mbarrier.  False when the shared abort flag
-// is raised (checked every 32 polls) or after `limit` polls, in which case
-// this thread raises it.
+// Wait for phase `phase` of an mbarrier, each poll suspending the thread for
+// up to kSuspendNs (it resumes when the phase completes), so waiting warps
+// take no issue slots.  False when the shared abort flag is raised (checked
+// every 8 polls) or after `limit` polls, in which case this thread raises it.
+constexpr int kSuspendNs = 1000;
 __device__ __forceinline__ bool wait_or_abort(uint32_t mbar, uint32_t phase, long long limit, uint32_t* abort_flag) {
     for (long long i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.b32 %0, 1, 0, p;\n\t}\n"
             : "=r"(done)
-            : "r"(mbar), "r"(phase)
+            : "r"(mbar), "r"(phase), "n"(kSuspendNs)
             : "memory");
         if (done) return true;
-        if ((i & 31) == 31 && *reinterpret_cast<volatile uint32_t*>(abort_flag)) return false;
+        if ((i & 7) == 7 && *reinterpret_cast<volatile uint32_t*>(abort_flag)) return false;
     }
     *reinterpret_cast<volatile uint32_t*>(abort_flag) = 1u;
     return false;
@@ -169,29 +172,26 @@ __device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ uint32_t biased_exp(double v) { return ((uint32_t)__double2hiint(v) >> 20) & 0x7FFu; }
 
 // The balanced-offset integer Z = X + 0x8080808080 of v (as two words) for a
 // row whose shift base is base_s = (largest biased exponent of the row) + 5:
-// q = M53 >> (base_s - e), X = (q + 1) >> 1; and v's sign bit.
+// q = M53 >> (base_s - e), X = (q + 1) >> 1, with the shift done as clamped
+// 32-bit shifts (a shift of 64 or more, which includes zero and subnormal v
+// with e = 0, gives q = 0); and the high word of v (its sign).
 struct Zw {
-    uint32_t zl, zh, sign;
+    uint32_t zl, zh, hi;
 };
 __device__ __forceinline__ Zw split_z(double v, uint32_t base_s) {
     const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
-    const uint32_t e = (hi >> 20) & 0x7FFu;
-    const uint32_t s = (e == 0u) ? 64u : base_s - e;              // >= 5
+    const uint32_t s = base_s - ((hi << 1) >> 21);                // >= 5
     const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;
-    uint32_t ql, qh;
-    if (s < 32u) {
-        ql = __funnelshift_r(lo, mh, s);
-        qh = mh >> s;
-    } else {
-        ql = (s < 64u) ? (mh >> (s - 32u)) : 0u;
-        qh = 0u;
-    }
+    uint32_t t, qh, ql;
+    asm("shf.r.clamp.b32 %0, %1, %2, %3;" : "=r"(t) : "r"(lo), "r"(mh), "r"(s));   // low word of M53 >> min(s, 32)
+    asm("shr.b32 %0, %1, %2;" : "=r"(qh) : "r"(mh), "r"(s));                         // 0 for s >= 32
+    const uint32_t s2 = (uint32_t)max((int)s - 32, 0);
+    asm("shr.b32 %0, %1, %2;" : "=r"(ql) : "r"(t), "r"(s2));                         // s >= 32: mh >> (s - 32)
     const uint64_t Z = ((((uint64_t)qh << 32) | ql) + 0x10101010101ull) >> 1;
-    return Zw{(uint32_t)Z, (uint32_t)(Z >> 32), hi & 0x80000000u};
+    return Zw{(uint32_t)Z, (uint32_t)(Z >> 32), hi};
 }
 
 __device__ __forceinline__ uint32_t hfma2(uint32_t a, uint32_t b, uint32_t c) {
@@ -206,7 +206,7 @@ __device__ __forceinline__ uint32_t hfma2(uint32_t a, uint32_t b, uint32_t c) {
 // the leading digit) exactly.  Digit 0 is byte 1 of zh, digit 1 byte 0 of zh,
 // digits 2..5 bytes 3..0 of zl.
 __device__ __forceinline__ void digit_pairs(const Zw& A, const Zw& B, uint32_t w[kDigits]) {
-    const uint32_t sg = (A.sign >> 16) | B.sign;                  // sign bits 15 and 31
+    const uint32_t sg = __byte_perm(A.hi, B.hi, 0x7030u) & 0x80008000u;   // the signs at bits 15 and 31
     const uint32_t sf = 0x3C003C00u | sg;                         // (+-1, +-1)
     const uint32_t c0 = 0x64006400u | (sg ^ 0x80008000u);         // -sign * 1024
     const uint32_t c1 = 0x64806480u | (sg ^ 0x80008000u);         // -sign * 1152
@@ -421,11 +421,12 @@ __global__ void __maxnreg__(96) k_gate_tc5_c128(const __grid_constant__ OzArgs a
     } else if (warp >= kLoadWarp0) {
         // ------------------------------------------------------- tile loads
         // thread <-> group row i of each staged half: per half, once the
-        // splitters have read it, 32 16-byte copies into the padded staging
-        // buffer and an arrival on the half's stage barrier when they land
+        // splitters have read it, 32 16-byte copies into the column-major
+        // staging buffer (a warp's copies of one column fill 512 contiguous
+        // bytes) and an arrival on the half's stage barrier when they land
         const int i = tid - kLoadWarp0 * 32;
         const uint64_t ro[2] = {row_off(i), row_off(kHalfRows + i)};
-        const uint32_t d = smem_u32(stage) + (uint32_t)i * kStageRow;
+        const uint32_t d = smem_u32(stage) + 16u * (uint32_t)i;
         uint32_t pf[2] = {0u, 0u};
         bool first = true, ok = true;
         for (uint64_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
@@ -439,7 +440,7 @@ __global__ void __maxnreg__(96) k_gate_tc5_c128(const __grid_constant__ OzArgs a
                 const char* gr = g + ro[h];
                 const uint32_t dh = d + (uint32_t)h * kHalfStage;
 #pragma unroll 8
-                for (int c = 0; c < 32; ++c) cp_async16(dh + 16u * c, gr + coloff[c]);
+                for (int c = 0; c < 32; ++c) cp_async16(dh + 16u * kHalfRows * c, gr + coloff[c]);
                 cp_async_arrive(&bars[h ? kStage1 : kStage0]);
             }
             first = false;
@@ -462,7 +463,7 @@ __global__ void __maxnreg__(96) k_gate_tc5_c128(const __grid_constant__ OzArgs a
         // then the imaginary-part digits (chunk 4 + qq).
         const int sw = warp - kSplitWarp0;
         const int ri = 8 * sw + (lane & 7), qq = lane >> 3;
-        const unsigned char* const srow = stage + ri * kStageRow + qq * 128;
+        const unsigned char* const srow = stage + 16u * (kHalfRows * 8 * qq + ri);   // (row ri, column 8 qq)
         uint32_t prf = 0, pyf = 0;
         bool first = true, ok = true;
         int it = 0;
@@ -479,13 +480,15 @@ __global__ void __maxnreg__(96) k_gate_tc5_c128(const __grid_constant__ OzArgs a
                 double2 v[8];
                 const double2* src = reinterpret_cast<const double2*>(srow + (uint32_t)h * kHalfStage);
 #pragma unroll
-                for (int k = 0; k < 8; ++k) v[k] = src[k];
+                for (int k = 0; k < 8; ++k) v[k] = src[kHalfRows * k];
                 mbar_arrive(&bars[h ? kStageFree1 : kStageFree0]);
-                uint32_t em = 0;
+                uint32_t em = 0;    // largest (high word << 1): the biased exponent in the top 11 bits
 #pragma unroll
-                for (int k = 0; k < 8; ++k) em = max(em, max(biased_exp(v[k].x), biased_exp(v[k].y)));
+                for (int k = 0; k < 8; ++k)
+                    em = max(em, max((uint32_t)__double2hiint(v[k].x) << 1, (uint32_t)__double2hiint(v[k].y) << 1));
                 em = max(em, __shfl_xor_sync(0xFFFFFFFFu, em, 8));
                 em = max(em, __shfl_xor_sync(0xFFFFFFFFu, em, 16));
+                em >>= 21;
                 const uint32_t base_s = (em < (uint32_t)kFlushExp) ? 0x10000u : em + 5u;
 #pragma unroll
                 for (int part = 0; part < 2; ++part) {
@@ -684,8 +687,8 @@ void launch_gate_tc5_c128(qe_state* s, const int* qubits, const cd* U) {
     a.status = status;
     a.B = reinterpret_cast<const uint16_t*>(scr + 256);
     a.F = reinterpret_cast<const int*>(scr + 256 + sizeof(hw.B));
-    a.spin_limit = 1ll << 26;
-    const size_t smem = 1024 + (size_t)kDigits * (kSliceA + kSliceB) + (size_t)kRows * kStageRow;
+    a.spin_limit = 1ll << 21;   // polls of up to kSuspendNs each
+    const size_t smem = 1024 + (size_t)kDigits * (kSliceA + kSliceB) + 2 * (size_t)kHalfStage;
     QE_CUDA(cudaFuncSetAttribute(k_gate_tc5_c128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const uint64_t grid = std::min<uint64_t>(a.ntiles, (uint64_t)num_sms());
     {
