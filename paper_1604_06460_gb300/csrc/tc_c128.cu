@@ -194,31 +194,34 @@ __device__ __forceinline__ Zw split_z(double v, uint32_t base_s) {
     return Zw{(uint32_t)Z, (uint32_t)(Z >> 32), hi};
 }
 
-__device__ __forceinline__ uint32_t hfma2(uint32_t a, uint32_t b, uint32_t c) {
+// add.rn.f16x2
+__device__ __forceinline__ uint32_t hadd2(uint32_t a, uint32_t b) {
     uint32_t d;
-    asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
     return d;
 }
 
 // The six signed digits of two values a, b as packed fp16 pairs (a in the
-// low half): byte k of Z becomes the fp16 number 1024 + byte (bits 0x64bb),
-// and one f16x2 fused multiply-add gives sign * (byte - 128) (sign * byte for
-// the leading digit) exactly.  Digit 0 is byte 1 of zh, digit 1 byte 0 of zh,
-// digits 2..5 bytes 3..0 of zl.
+// low half).  The bytes of the two Z are first interleaved (a0 b0 a1 b1 ...);
+// one byte permute against the constant with bytes 0x64 | sign << 7 then
+// makes each pair of bytes the fp16 numbers sign * (1024 + byte), and one
+// f16x2 addition of -sign * 1152 (-sign * 1024 for the leading digit) gives
+// sign * (byte - 128) (sign * byte) exactly.  Digit 0 is byte 1 of zh, digit 1
+// byte 0 of zh, digits 2..5 bytes 3..0 of zl.
 __device__ __forceinline__ void digit_pairs(const Zw& A, const Zw& B, uint32_t w[kDigits]) {
     const uint32_t sg = __byte_perm(A.hi, B.hi, 0x7030u) & 0x80008000u;   // the signs at bits 15 and 31
-    const uint32_t sf = 0x3C003C00u | sg;                         // (+-1, +-1)
+    const uint32_t hs = 0x64006400u | sg;                         // bytes 1, 3: 0x64 | sign
     const uint32_t c0 = 0x64006400u | (sg ^ 0x80008000u);         // -sign * 1024
     const uint32_t c1 = 0x64806480u | (sg ^ 0x80008000u);         // -sign * 1152
-    auto mag = [](uint32_t xa, uint32_t xb, uint32_t k) {
-        return (__byte_perm(xa, xb, k | ((4u + k) << 8)) & 0x00FF00FFu) | 0x64006400u;
-    };
-    w[0] = hfma2(mag(A.zh, B.zh, 1u), sf, c0);
-    w[1] = hfma2(mag(A.zh, B.zh, 0u), sf, c1);
-    w[2] = hfma2(mag(A.zl, B.zl, 3u), sf, c1);
-    w[3] = hfma2(mag(A.zl, B.zl, 2u), sf, c1);
-    w[4] = hfma2(mag(A.zl, B.zl, 1u), sf, c1);
-    w[5] = hfma2(mag(A.zl, B.zl, 0u), sf, c1);
+    const uint32_t ph = __byte_perm(A.zh, B.zh, 0x5140u);         // a0 b0 a1 b1 of zh
+    const uint32_t p01 = __byte_perm(A.zl, B.zl, 0x5140u);        // a0 b0 a1 b1 of zl
+    const uint32_t p23 = __byte_perm(A.zl, B.zl, 0x7362u);        // a2 b2 a3 b3 of zl
+    w[0] = hadd2(__byte_perm(ph, hs, 0x7352u), c0);
+    w[1] = hadd2(__byte_perm(ph, hs, 0x7150u), c1);
+    w[2] = hadd2(__byte_perm(p23, hs, 0x7352u), c1);
+    w[3] = hadd2(__byte_perm(p23, hs, 0x7150u), c1);
+    w[4] = hadd2(__byte_perm(p01, hs, 0x7352u), c1);
+    w[5] = hadd2(__byte_perm(p01, hs, 0x7150u), c1);
 }
 
 // The integer Y of one output from its seven accumulators (raw FP32 bits).
