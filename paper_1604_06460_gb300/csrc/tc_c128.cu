@@ -229,14 +229,15 @@ __device__ __forceinline__ long long combine_y(const uint32_t c[kAcc]) {
     const float M = 12582912.0f;   // 1.5 * 2^23; bits 0x4B400000
     const uint32_t u2 = __float_as_uint(__fadd_rn(__uint_as_float(c[0]), M));
     const uint32_t u3 = __float_as_uint(__fadd_rn(__uint_as_float(c[1]), M));
-    const int c4 = (int)(__float_as_uint(__fadd_rn(__uint_as_float(c[2]), M)) - 0x4B400000u);
-    const int c5 = (int)(__float_as_uint(__fadd_rn(__uint_as_float(c[3]), M)) - 0x4B400000u);
+    const uint32_t u4 = __float_as_uint(__fadd_rn(__uint_as_float(c[2]), M));
+    const uint32_t u5 = __float_as_uint(__fadd_rn(__uint_as_float(c[3]), M));
     const int c6 = __float2int_rn(__uint_as_float(c[4]));
     const int c78 = __float2int_rn(__fmaf_rn(__uint_as_float(c[6]), 0.00390625f, __uint_as_float(c[5])));
-    const int H = (int)(u2 * 256u + u3 - 257u * 0x4B400000u);     // C_2 * 256 + C_3, |H| < 2^29
-    long long Y = mad_wide(c6, 256, (long long)c78);
-    Y = mad_wide(c5, 1 << 16, Y);
-    Y = mad_wide(c4, 1 << 24, Y);
+    // u4 2^24 + u5 2^16 carry the offsets 0x4B400000 (2^24 + 2^16) = 0x4B8B40 2^32,
+    // taken off H: H = C_2 256 + C_3 - 0x4B8B40 (mod 2^32), and Y is exact mod 2^64
+    const int H = (int)(u2 * 256u + u3 - (257u * 0x4B400000u + 0x4B8B40u));
+    long long Y = mad_wide((int)u5, 1 << 16, (long long)(c6 * 256 + c78));   // |C_6 256 + c78| < 2^31
+    Y = mad_wide((int)u4, 1 << 24, Y);
     return Y + ((long long)H << 32);
 }
 
