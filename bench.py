@@ -46,7 +46,61 @@ def parse():
     ap.add_argument("--only", default="", choices=["", "batch", "tensor_cores", "config4", "qft"],
                     help="run one secondary configuration alone (sizes from --n) and print its JSON")
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64"], help="state type for --only qft")
+    ap.add_argument("--kernel-case", default="", choices=["", *KERNEL_CASES],
+                    help="run a few launches of one hot kernel on a small state (the ncu capture cases)")
     return ap.parse_args()
+
+
+# small single-kernel workloads for ncu captures: (dtype, n, what)
+KERNEL_CASES = {
+    "tc128": "complex128 5-qubit block on qubits (3,7,11,15,19) of a 24-qubit state, 3 passes",
+    "tc64": "complex64 5-qubit block on qubits (3,7,11,15,19) of a 26-qubit state, 3 passes",
+    "direct2": "complex128 2-qubit block on qubits (5,17) of a 26-qubit state (fusion width 2), 3 passes",
+    "expect": "TFIM energy of a 26-qubit complex128 state, 2 evaluations",
+    "fft": "emulated 26-qubit QFT of a complex128 state, 2 transforms",
+}
+
+
+def run_kernel_case(qe, I, which):
+    """A few launches of one hot kernel on a small state (a few hundred MB)."""
+    import torch
+    rng = np.random.default_rng(0)
+
+    def unitary(d):
+        z = rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))
+        q, r = np.linalg.qr(z)
+        return q * (np.diag(r) / abs(np.diag(r)))[None, :]
+
+    if which in ("tc128", "tc64"):
+        with qe.State(24 if which == "tc128" else 26, "c128" if which == "tc128" else "c64") as st:
+            st.set_policy(qe.POLICY_AUTO, 5)
+            st.init_random(3)
+            U = unitary(32)
+            for _ in range(3):
+                st.apply_gate([3, 7, 11, 15, 19], U)
+                st.flush()
+    elif which == "direct2":
+        with qe.State(26, "c128") as st:
+            st.set_policy(qe.POLICY_AUTO, 2)
+            st.init_random(3)
+            U = unitary(4)
+            for _ in range(3):
+                st.apply_gate([5, 17], U)
+                st.flush()
+    elif which == "expect":
+        with qe.State(26, "c128") as st:
+            st.init_random(2)
+            xm, zm, cf = I.tfim_terms(26)
+            for _ in range(2):
+                st.expectation(xm, zm, cf)
+    else:
+        with qe.State(26, "c128") as st:
+            st.set_policy(qe.POLICY_EMULATE, 1)
+            st.init_random(2)
+            for _ in range(2):
+                st.apply_qft(0, 26)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_case": which, "workload": KERNEL_CASES[which]}), flush=True)
 
 
 def workload_desc(n, depth, max_k):
@@ -229,6 +283,15 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     import torch
+    if args.kernel_case:
+        torch.cuda.set_device(0)
+        from paper_1604_06460_gb300 import build as B
+        from paper_1604_06460_gb300 import inputs as I
+        from paper_1604_06460_gb300 import qe
+        B.build()
+        qe.load()
+        run_kernel_case(qe, I, args.kernel_case)
+        return 0
     if args.only:
         torch.cuda.set_device(0)
         from paper_1604_06460_gb300 import build as B
