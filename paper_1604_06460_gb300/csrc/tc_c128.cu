@@ -61,6 +61,7 @@
 // abort flag that ends the waits of all other threads; the MMA warp waits for
 // its own MMAs before tensor memory is freed.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "qe_arith.cuh"
@@ -105,6 +106,7 @@ struct OzArgs {
     long long spin_limit;
     const uint16_t* B;      // [6][64][64] fp16 digits of W': slice j, row n', column k
     const int* F;           // [64] row scale exponents of W (original row order)
+    int stall_test;         // failure-path test: the first staged half is never announced
 };
 
 // Byte offset of the 16-byte chunk `ch` (8 fp16 along K) of row r in a
@@ -445,7 +447,7 @@ __global__ void __maxnreg__(96) k_gate_tc5_c128(const __grid_constant__ OzArgs a
                 const uint32_t dh = d + (uint32_t)h * kHalfStage;
 #pragma unroll 8
                 for (int c = 0; c < 32; ++c) cp_async16(dh + 16u * kHalfRows * c, gr + coloff[c]);
-                cp_async_arrive(&bars[h ? kStage1 : kStage0]);
+                if (!(a.stall_test && first && h == 0)) cp_async_arrive(&bars[h ? kStage1 : kStage0]);
             }
             first = false;
             // the tile after this one into L2 meanwhile: its 2^kh contiguous
@@ -692,6 +694,13 @@ void launch_gate_tc5_c128(qe_state* s, const int* qubits, const cd* U) {
     a.B = reinterpret_cast<const uint16_t*>(scr + 256);
     a.F = reinterpret_cast<const int*>(scr + 256 + sizeof(hw.B));
     a.spin_limit = 1ll << 21;   // polls of up to kSuspendNs each
+    // Failure-path test (QE_TEST_STALL_TC128=1): the load warps withhold the
+    // arrival for the first staged half, so the splitters' wait runs out after
+    // a short limit, every role leaves through the shared abort flag, and the
+    // host reports QE_ERR_TIMEOUT with the context intact.
+    const char* stall = std::getenv("QE_TEST_STALL_TC128");
+    a.stall_test = (stall != nullptr && stall[0] == '1') ? 1 : 0;
+    if (a.stall_test) a.spin_limit = 1ll << 12;
     const size_t smem = 1024 + (size_t)kDigits * (kSliceA + kSliceB) + 2 * (size_t)kHalfStage;
     QE_CUDA(cudaFuncSetAttribute(k_gate_tc5_c128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const uint64_t grid = std::min<uint64_t>(a.ntiles, (uint64_t)num_sms());

@@ -452,7 +452,7 @@ def test_tensor_core_fused_circuit_c64(qe):
 
 
 # ------------------------------------------ tensor cores (complex128, k = 4, 5)
-# Exact integer-digit products on the BF16 tensor pipe: inputs and matrix
+# Exact integer-digit products on the FP16 tensor pipe: inputs and matrix
 # entries are rounded to 2^-48 of their row scale, so the FP64 bar holds.
 @pytest.mark.parametrize("qubits", [[0, 1, 2, 3, 4], [10, 11, 12, 13, 14], [4, 0, 15, 7, 12],
                                     [2, 9, 5, 14], [15, 14, 13, 12], [6, 3, 11, 1, 8],
@@ -473,6 +473,28 @@ def test_tensor_core_blocks_c128(qe, qubits):
     assert launches == 1
     assert prof.get("gate_tc_k5_c128", (0,))[0] == 1
     close(got, ref)
+
+
+# A bounded wait that runs out: the load warps withhold one stage arrival
+# (a flag nothing else sets), the splitters give up after a short limit, every
+# role leaves through the abort flag and tensor memory is freed; the host
+# reports QE_ERR_TIMEOUT and the same context then runs the block correctly.
+def test_tensor_core_c128_wait_timeout_reports_and_recovers(qe, monkeypatch):
+    from paper_1604_06460_gb300.qe import QEError
+    n, qubits = 14, [0, 3, 6, 9, 12]
+    U = rand_unitary(32, np.random.default_rng(77))
+    psi = I.random_state(n, 21)
+    with make(qe, n, "c128", psi=psi, max_k=5) as st:
+        monkeypatch.setenv("QE_TEST_STALL_TC128", "1")
+        with pytest.raises(QEError) as err:
+            st.apply_gate(qubits, U)
+            st.flush()
+        assert err.value.status == -4 and "QE_ERR_TIMEOUT" in str(err.value)
+        monkeypatch.delenv("QE_TEST_STALL_TC128")
+        st.set(psi)
+        st.apply_gate(qubits, U)
+        got = st.get()
+    close(got, oracle.apply_gate(psi, qubits, U))
 
 
 @pytest.mark.parametrize("n,qubits", [(12, [0, 4, 7, 9, 11]), (12, [11, 10, 9, 8, 7]), (13, [12, 0, 6, 3, 9]),
