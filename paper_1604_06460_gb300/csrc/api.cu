@@ -2,6 +2,7 @@
 // gate queue, gate fusion, structure detection and the choice between
 // emulating and simulating a subroutine (Sec. III).
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -147,65 +148,6 @@ void apply_block(qe_state* s, int k, const int* qubits, const std::vector<cd>& U
 
 // ----------------------------------------------------------------- fusion
 namespace {
-struct Block {
-    std::vector<int> q;      // matrix bit j <-> q[j]
-    std::vector<cd> U;       // 2^|q| x 2^|q|
-    uint64_t mask = 0;
-    int gates = 0;
-};
-
-// U_block <- G (on qubits gq, embedded) * U_block, where gq is a subset of b.q
-void left_multiply(Block& b, int gk, const int* gq, const std::vector<cd>& G) {
-    const int k = (int)b.q.size(), D = 1 << k, Dg = 1 << gk;
-    int pos[5];
-    for (int j = 0; j < gk; ++j)
-        pos[j] = (int)(std::find(b.q.begin(), b.q.end(), gq[j]) - b.q.begin());
-    int gmask = 0;
-    for (int j = 0; j < gk; ++j) gmask |= 1 << pos[j];
-    std::vector<cd> out(D * D);
-    std::vector<int> dep(Dg);
-    for (int c = 0; c < Dg; ++c) {
-        int o = 0;
-        for (int j = 0; j < gk; ++j)
-            if ((c >> j) & 1) o |= 1 << pos[j];
-        dep[c] = o;
-    }
-    for (int col = 0; col < D; ++col)
-        for (int r = 0; r < D; ++r) {
-            int gr = 0;
-            for (int j = 0; j < gk; ++j) gr |= ((r >> pos[j]) & 1) << j;
-            const int base = r & ~gmask;
-            cd acc = 0.0;
-            for (int c = 0; c < Dg; ++c) acc += G[gr * Dg + c] * b.U[(base | dep[c]) * D + col];
-            out[r * D + col] = acc;
-        }
-    b.U.swap(out);
-}
-
-// Grow block b to also cover qubits extra (identity on them).
-void extend(Block& b, const std::vector<int>& extra) {
-    for (int qn : extra) {
-        const int k = (int)b.q.size(), D = 1 << k;
-        std::vector<cd> out(4 * D * D, 0.0);
-        // new bit k is qn: U' = I_2 (x) U (block diagonal over the new bit)
-        for (int hb = 0; hb < 2; ++hb)
-            for (int r = 0; r < D; ++r)
-                for (int c = 0; c < D; ++c) out[(r | (hb << k)) * (2 * D) + (c | (hb << k))] = b.U[r * D + c];
-        b.U.swap(out);
-        b.q.push_back(qn);
-        b.mask |= 1ull << qn;
-    }
-}
-
-// Merge block o into b (disjoint qubit sets; the two commute).
-void merge_into(Block& b, const Block& o) {
-    std::vector<int> extra;
-    for (int qn : o.q)
-        if (!((b.mask >> qn) & 1ull)) extra.push_back(qn);
-    extend(b, extra);
-    left_multiply(b, (int)o.q.size(), o.q.data(), o.U);
-    b.gates += o.gates;
-}
 }  // namespace
 
 // A fused block ready to run (controls only for gates that came with them).
@@ -215,114 +157,214 @@ struct Planned {
     uint64_t cmask = 0;
 };
 
-// Greedy fusion: consecutive gates whose qubits stay within max_k qubits are
-// multiplied into one block.  Open blocks have disjoint qubit sets (so they
-// commute).  A gate that would overflow closes just enough of the blocks it
-// touches (largest first) for the rest and the gate to fit; blocks closed at
-// the same moment are disjoint and are packed together into passes of at most
-// max_k qubits.
-std::vector<Planned> plan_fusion(const std::vector<PendingGate>& q, int max_k) {
-    std::vector<Planned> out;
-    auto emit_one = [&](Block& b) {
-        Planned p;
-        p.q = std::move(b.q);
-        p.U = std::move(b.U);
-        out.push_back(std::move(p));
-    };
-    // emit blocks that were open together: first-fit packing, largest first
-    auto emit = [&](std::vector<Block>& bs) {
-        std::sort(bs.begin(), bs.end(), [](const Block& x, const Block& y) { return x.q.size() > y.q.size(); });
-        std::vector<Block> packs;
-        for (auto& b : bs) {
-            bool placed = false;
-            for (auto& pk : packs)
-                if ((int)(pk.q.size() + b.q.size()) <= max_k) {
-                    merge_into(pk, b);
-                    placed = true;
-                    break;
-                }
-            if (!placed) packs.push_back(std::move(b));
+// U <- G U, where G acts on the matrix bits pos[0..gk) (row operations on
+// the groups of rows that differ only in those bits), in place.
+void apply_in_place(std::vector<cd>& U, int D, int gk, const int* pos, const std::vector<cd>& G) {
+    const int Dg = 1 << gk;
+    int gmask = 0, dep[32];
+    for (int j = 0; j < gk; ++j) gmask |= 1 << pos[j];
+    for (int c = 0; c < Dg; ++c) {
+        int o = 0;
+        for (int j = 0; j < gk; ++j)
+            if ((c >> j) & 1) o |= 1 << pos[j];
+        dep[c] = o;
+    }
+    cd x[32];
+    for (int r0 = 0; r0 < D; ++r0) {
+        if (r0 & gmask) continue;
+        for (int col = 0; col < D; ++col) {
+            for (int c = 0; c < Dg; ++c) x[c] = U[(size_t)(r0 | dep[c]) * D + col];
+            for (int r = 0; r < Dg; ++r) {
+                cd acc = 0.0;
+                for (int c = 0; c < Dg; ++c) acc += G[(size_t)r * Dg + c] * x[c];
+                U[(size_t)(r0 | dep[r]) * D + col] = acc;
+            }
         }
-        for (auto& pk : packs) emit_one(pk);
-        bs.clear();
+    }
+}
+
+// Frontier fusion: the gates form per-qubit queues; a gate can join a block
+// on qubit set S when all its qubits are in S and it is at the front of each
+// of their queues (so every gate before it on those qubits is already
+// applied or in the block).  Each pass takes the set S (at most max_k qubits)
+// that absorbs the most gates: candidate sets are grown from every gate at a
+// queue front, adding at each step the qubit, or the remaining qubits of a
+// front gate, that lets the block absorb the most gates.  Controlled gates
+// and gates wider than max_k stay passes of their own, emitted once they are
+// at the front of all their qubits (targets and controls).  Qubits a block
+// absorbed no gate on are dropped from it.
+void plan_fusion_frontier(const std::vector<PendingGate>& q, int max_k, int nq,
+                          const std::function<void(Planned&&)>& emit, bool matrices) {
+    const int G = (int)q.size();
+    std::vector<uint64_t> gm(G);      // all qubits of gate i (targets and controls)
+    std::vector<char> special(G);
+    std::vector<std::vector<int>> queue(nq);
+    for (int i = 0; i < G; ++i) {
+        uint64_t m = q[i].cmask;
+        for (int j = 0; j < q[i].k; ++j) m |= 1ull << q[i].q[j];
+        gm[i] = m;
+        special[i] = (q[i].cmask != 0 || q[i].k > max_k) ? 1 : 0;
+        for (int b = 0; b < nq; ++b)
+            if ((m >> b) & 1ull) queue[b].push_back(i);
+    }
+    std::vector<int> ptr(nq, 0);
+    auto front = [&](int b, const std::vector<int>& p) { return p[b] < (int)queue[b].size() ? queue[b][p[b]] : -1; };
+    // gates absorbable into a block on S from positions p (p is advanced)
+    auto absorb = [&](uint64_t S, std::vector<int>& p, std::vector<int>* taken) {
+        int count = 0;
+        bool progress = true;
+        while (progress) {
+            progress = false;
+            for (uint64_t r = S; r; r &= r - 1) {
+                const int b = __builtin_ctzll(r);
+                for (;;) {
+                    const int gi = front(b, p);
+                    if (gi < 0 || special[gi] || (gm[gi] & ~S)) break;
+                    bool at_front = true;
+                    for (uint64_t t = gm[gi]; t; t &= t - 1)
+                        if (front(__builtin_ctzll(t), p) != gi) { at_front = false; break; }
+                    if (!at_front) break;
+                    for (uint64_t t = gm[gi]; t; t &= t - 1) ++p[__builtin_ctzll(t)];
+                    if (taken) taken->push_back(gi);
+                    ++count;
+                    progress = true;
+                }
+            }
+        }
+        return count;
     };
+    // Absorption is confluent (taking a gate never blocks another), so the
+    // gates of S | add are those of S plus what absorbing S | add from S's
+    // end positions adds.
+    std::vector<int> pS(nq), scratch(nq);
+    // grow a candidate set from S up to max_k qubits; returns its gate count
+    auto grow = [&](uint64_t& S) {
+        pS = ptr;
+        int cS = absorb(S, pS, nullptr);
+        while (__builtin_popcountll(S) < max_k) {
+            int best = -1, best_add = 0;
+            uint64_t best_m = 0;
+            auto consider = [&](uint64_t add) {
+                if (!add || __builtin_popcountll(S | add) > max_k) return;
+                scratch = pS;
+                const int sc = cS + absorb(S | add, scratch, nullptr), na = __builtin_popcountll(add);
+                if (sc > best || (sc == best && na < best_add)) { best = sc; best_add = na; best_m = add; }
+            };
+            for (int b = 0; b < nq; ++b) {
+                if (((S >> b) & 1ull) || ptr[b] >= (int)queue[b].size()) continue;
+                consider(1ull << b);
+                const int gi = queue[b][ptr[b]];
+                if (!special[gi]) consider(gm[gi] & ~S);
+            }
+            if (best < 0) break;
+            S |= best_m;
+            cS += absorb(S, pS, nullptr);
+        }
+        return cS;
+    };
+    int remaining = G;
+    std::vector<int> taken;
+    while (remaining > 0) {
+        // standalone gates that are ready go first
+        bool emitted = false;
+        for (int b = 0; b < nq && !emitted; ++b) {
+            const int gi = front(b, ptr);
+            if (gi < 0 || !special[gi]) continue;
+            bool ready = true;
+            for (uint64_t t = gm[gi]; t; t &= t - 1)
+                if (front(__builtin_ctzll(t), ptr) != gi) { ready = false; break; }
+            if (!ready) continue;
+            Planned p;
+            p.q.assign(q[gi].q, q[gi].q + q[gi].k);
+            if (matrices) p.U = q[gi].U;
+            p.cmask = q[gi].cmask;
+            for (uint64_t t = gm[gi]; t; t &= t - 1) ++ptr[__builtin_ctzll(t)];
+            --remaining;
+            emitted = true;
+            emit(std::move(p));
+        }
+        if (emitted) continue;
+        // the best block over the sets grown from each front gate
+        uint64_t bestS = 0;
+        int bestc = -1;
+        std::vector<uint64_t> seen;
+        for (int b = 0; b < nq; ++b) {
+            const int gi = front(b, ptr);
+            if (gi < 0 || special[gi]) continue;
+            uint64_t S = gm[gi];
+            if (std::find(seen.begin(), seen.end(), S) != seen.end()) continue;
+            seen.push_back(S);
+            const int c = grow(S);
+            if (c > bestc || (c == bestc && __builtin_popcountll(S) < __builtin_popcountll(bestS))) {
+                bestc = c;
+                bestS = S;
+            }
+        }
+        if (bestc <= 0) fail(QE_ERR_STATE, "fusion planner made no progress");
+        taken.clear();
+        absorb(bestS, ptr, &taken);
+        uint64_t used = 0;
+        for (int gi : taken) used |= gm[gi];
+        Planned p;
+        for (uint64_t t = used; t; t &= t - 1) p.q.push_back(__builtin_ctzll(t));
+        if (matrices) {
+            const int D = 1 << p.q.size();
+            p.U.assign((size_t)D * D, 0.0);
+            for (int r = 0; r < D; ++r) p.U[(size_t)r * D + r] = 1.0;
+            for (int gi : taken) {
+                int pos[5];
+                for (int j = 0; j < q[gi].k; ++j)
+                    pos[j] = (int)(std::find(p.q.begin(), p.q.end(), q[gi].q[j]) - p.q.begin());
+                apply_in_place(p.U, D, q[gi].k, pos, q[gi].U);
+            }
+        }
+        remaining -= (int)taken.size();
+        emit(std::move(p));
+    }
+}
+
+// The fused passes for the queued gates, handed to `emit` in order as they
+// are planned (so the caller can launch each while the next is planned).
+// max_k <= 1: no fusion, every gate is its own pass.  Without `matrices` only
+// the qubit sets are produced.
+void plan_fusion(const std::vector<PendingGate>& q, int max_k, int nq, const std::function<void(Planned&&)>& emit,
+                 bool matrices = true) {
     if (max_k <= 1) {
         for (auto& g : q) {
             Planned p;
             p.q.assign(g.q, g.q + g.k);
-            p.U = g.U;
+            if (matrices) p.U = g.U;
             p.cmask = g.cmask;
-            out.push_back(std::move(p));
+            emit(std::move(p));
         }
-        return out;
+        return;
     }
-    std::vector<Block> open;
-    auto close_if = [&](uint64_t touch) {
-        std::vector<Block> keep, closed;
-        for (auto& b : open) {
-            if (b.mask & touch) closed.push_back(std::move(b));
-            else keep.push_back(std::move(b));
-        }
-        open.swap(keep);
-        emit(closed);
-    };
-    for (auto& g : q) {
-        uint64_t gmask = 0;
-        for (int j = 0; j < g.k; ++j) gmask |= 1ull << g.q[j];
-        if (g.cmask != 0 || g.k > max_k) {
-            close_if(gmask | g.cmask);
-            Planned p;
-            p.q.assign(g.q, g.q + g.k);
-            p.U = g.U;
-            p.cmask = g.cmask;
-            out.push_back(std::move(p));
-            continue;
-        }
-        // touched blocks, largest first; close from the front until the rest
-        // and the gate fit in max_k qubits
-        std::vector<int> touched;
-        for (int i = 0; i < (int)open.size(); ++i)
-            if (open[i].mask & gmask) touched.push_back(i);
-        std::sort(touched.begin(), touched.end(),
-                  [&](int x, int y) { return open[x].q.size() > open[y].q.size(); });
-        uint64_t uni = gmask;
-        for (int i : touched) uni |= open[i].mask;
-        uint64_t closing = 0;
-        for (size_t t = 0; t < touched.size() && __builtin_popcountll(uni) > max_k; ++t) {
-            const uint64_t m = open[touched[t]].mask;
-            closing |= m;
-            uni = gmask;
-            for (size_t u = t + 1; u < touched.size(); ++u) uni |= open[touched[u]].mask;
-        }
-        if (closing) close_if(closing);
-        // the remaining touched blocks act before the gate
-        Block nb;
-        nb.q.assign(g.q, g.q + g.k);
-        nb.U = g.U;
-        nb.mask = gmask;
-        nb.gates = 1;
-        Block merged;
-        bool first = true;
-        std::vector<Block> keep;
-        for (auto& b : open) {
-            if (b.mask & gmask) {
-                if (first) { merged = std::move(b); first = false; }
-                else merge_into(merged, b);
-            } else {
-                keep.push_back(std::move(b));
-            }
-        }
-        if (first) {
-            keep.push_back(std::move(nb));
-        } else {
-            merge_into(merged, nb);
-            keep.push_back(std::move(merged));
-        }
-        open.swap(keep);
-    }
-    close_if(~0ull);
+    plan_fusion_frontier(q, max_k, nq, emit, matrices);
+}
+
+std::vector<Planned> plan_fusion_list(const std::vector<PendingGate>& q, int max_k, int nq, bool matrices) {
+    std::vector<Planned> out;
+    plan_fusion(q, max_k, nq, [&](Planned&& p) { out.push_back(std::move(p)); }, matrices);
     return out;
 }
+
+uint32_t* status_word_host(qe_state* s) {
+    if (!s->status_host) {
+        QE_CUDA(cudaMallocHost(&s->status_host, sizeof(uint32_t)));
+        *s->status_host = 0u;
+    }
+    return s->status_host;
+}
+
+void complete_pending(qe_state* s) {
+    if (!s->status_pending) return;
+    s->status_pending = false;
+    QE_CUDA(cudaStreamSynchronize(s->stream));
+    const uint32_t st = *s->status_host;
+    *s->status_host = 0u;
+    if (st) fail(QE_ERR_TIMEOUT, "tensor-core gate: an mbarrier wait exceeded its limit");
+}
+
 
 void flush(qe_state* s) {
     if (s->queue.empty()) return;
@@ -330,7 +372,17 @@ void flush(qe_state* s) {
     q.swap(s->queue);
     const int k = choose_fusion_width(s, q);
     s->stats.gates += q.size();
-    for (auto& b : plan_fusion(q, k)) apply_block(s, (int)b.q.size(), b.q.data(), b.U, b.cmask);
+    try {
+        plan_fusion(q, k, s->n,
+                    [&](Planned&& b) { apply_block(s, (int)b.q.size(), b.q.data(), b.U, b.cmask); });
+    } catch (...) {
+        try {
+            complete_pending(s);
+        } catch (...) {
+        }
+        throw;
+    }
+    complete_pending(s);
 }
 
 // Fusion width: the state's max_k, or, under QE_POLICY_AUTO with a learned
@@ -341,7 +393,7 @@ int choose_fusion_width(qe_state* s, const std::vector<PendingGate>& q) {
     std::vector<float> X;
     std::vector<int> owner;
     for (int k = 1; k <= s->max_k; ++k) {
-        for (auto& b : plan_fusion(q, k)) {
+        for (auto& b : plan_fusion_list(q, k, s->n, false)) {
             int lo = s->n, hi = 0;
             for (int v : b.q) { lo = std::min(lo, v); hi = std::max(hi, v); }
             for (int j = 0; j < s->n; ++j)
@@ -445,7 +497,7 @@ int qe_plan_fusion(int n, int ngates, const int* k, const int* qubits, const dou
         const double* m = matrices + mat_offset[g];
         for (int i = 0; i < D * D; ++i) q[g].U[i] = cd(m[2 * i], m[2 * i + 1]);
     }
-    const std::vector<Planned> plan = plan_fusion(q, max_k);
+    const std::vector<Planned> plan = plan_fusion_list(q, max_k, n, true);
     *nblocks = (int)plan.size();
     if ((int)plan.size() > cap) fail(QE_ERR_ARG, "more blocks than cap");
     if (!plan.empty() && (!block_k || !block_qubits || !block_matrices)) fail(QE_ERR_ARG, "output arrays are NULL");
@@ -522,6 +574,7 @@ int qe_free_state(qe_state* s) {
     cudaStreamSynchronize(s->stream);
     if (s->owned && s->d) cudaFree(s->d);
     if (s->scratch) cudaFree(s->scratch);
+    if (s->status_host) cudaFreeHost(s->status_host);
     profile_clear(s);
     for (auto e : s->event_pool) cudaEventDestroy(e);
     s->magic = 0;

@@ -63,6 +63,10 @@ struct qe_state {
     // pinned host mirror of small results
     double* host_result = nullptr;
     qe::Stats stats;
+    // status word of the last tensor-core launch (pinned host copy), checked
+    // before the next such launch and at the end of every flush
+    uint32_t* status_host = nullptr;
+    bool status_pending = false;
     // optional per-launch event timing
     bool profile = false;
     std::vector<qe::ProfRec> prof;
@@ -96,6 +100,11 @@ void launch_scale(qe_state* s, double factor);
 
 // dense k-qubit gate (1 <= k <= 5) through shared-memory tiles
 void launch_gate_dense(qe_state* s, int k, const int* qubits, const cd* U);
+// The tensor-core launchers copy their device status word into the state's
+// pinned host word after the kernel and mark it pending; complete_pending()
+// waits for the stream and raises QE_ERR_TIMEOUT if a launch reported one.
+uint32_t* status_word_host(qe_state* s);
+void complete_pending(qe_state* s);
 // 5-qubit block on a complex64 state with tcgen05 tensor cores (n >= 12)
 void launch_gate_tc5(qe_state* s, const int* qubits, const cd* U);
 void launch_gate_tc5_c128(qe_state* s, const int* qubits, const cd* U);

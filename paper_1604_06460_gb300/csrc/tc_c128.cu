@@ -686,6 +686,7 @@ void launch_gate_tc5_c128(qe_state* s, const int* qubits, const cd* U) {
                 hw.B[((size_t)j * kN + np) * kK + k] = fp16_bits(dg[j][k]);
             }
     }
+    complete_pending(s);   // the previous tensor-core launch, before the scratch is reused
     char* scr = (char*)ensure_scratch(s, 256 + sizeof(HostW));
     uint32_t* status = (uint32_t*)scr;
     QE_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), s->stream));
@@ -709,10 +710,10 @@ void launch_gate_tc5_c128(qe_state* s, const int* qubits, const cd* U) {
         k_gate_tc5_c128<<<(unsigned)grid, kOzThreads, smem, s->stream>>>(a);
         QE_CUDA(cudaGetLastError());
     }
-    uint32_t host_status = 0;
-    QE_CUDA(cudaMemcpyAsync(&host_status, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s->stream));
-    QE_CUDA(cudaStreamSynchronize(s->stream));
-    if (host_status) fail(QE_ERR_TIMEOUT, "tensor-core gate: an mbarrier wait exceeded its limit");
+    // checked before the next tensor-core launch or at the end of the flush,
+    // so that the host plans the next block while this one runs
+    QE_CUDA(cudaMemcpyAsync(status_word_host(s), status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s->stream));
+    s->status_pending = true;
 }
 
 }  // namespace qe
