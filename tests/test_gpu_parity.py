@@ -175,6 +175,45 @@ def test_controlled_dense(qe, controls, targets):
 
 
 # ------------------------------------------------------------ circuits
+# The fusion planner keeps controlled gates as passes of their own and lets
+# blocks on other qubits move past them: a fused random circuit with
+# controlled-U and multi-controlled-X gates interleaved must match the
+# oracle applied gate by gate.
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_fused_circuit_with_controlled_gates(qe, dtype):
+    n = 14
+    rng = np.random.default_rng(31)
+    gates = []
+    for _ in range(6):
+        for q in range(n):
+            gates.append(I.single(q, I.haar_u2(rng)))
+        perm = rng.permutation(n)
+        for j in range(0, n - 1, 2):
+            gates.append(I.cnot(int(perm[j]), int(perm[j + 1])))
+        qs = [int(v) for v in rng.permutation(n)[:4]]
+        gates.append(I.Gate((qs[0],), rand_unitary(2, rng), (qs[1], qs[2]), "cu"))
+        gates.append(I.mcx([qs[3], qs[0]], qs[1]))
+    psi = I.random_state(n, 17)
+    ref = psi.copy()
+    for g in gates:
+        if g.controls:
+            ref = oracle.apply_controlled(ref, list(g.controls), list(g.qubits), g.matrix)
+        else:
+            ref = oracle.apply_gate(ref, list(g.qubits), g.matrix)
+    with make(qe, n, dtype, psi=psi, max_k=5) as st:
+        st.reset_stats()
+        for g in gates:
+            st.apply(g)
+        got = st.get().astype(np.complex128)
+        passes = st.stats()["passes"]
+    assert passes < len(gates) / 4
+    if dtype == "c128":
+        close(got, ref)
+    else:
+        assert np.max(np.abs(got - ref)) < 2e-5
+        assert oracle.fidelity(ref, got) > 1 - 1e-8
+
+
 @pytest.mark.parametrize("max_k,tile", [(1, False), (2, False), (3, False), (4, False), (5, False),
                                         (2, True)])
 def test_random_circuit_fused_vs_oracle(qe, max_k, tile):
