@@ -194,7 +194,7 @@ void apply_in_place(std::vector<cd>& U, int D, int gk, const int* pos, const std
 // at the front of all their qubits (targets and controls).  Qubits a block
 // absorbed no gate on are dropped from it.
 void plan_fusion_frontier(const std::vector<PendingGate>& q, int max_k, int nq,
-                          const std::function<void(Planned&&)>& emit, bool matrices) {
+                          const std::function<void(Planned&&)>& emit, bool matrices, bool lookahead) {
     const int G = (int)q.size();
     std::vector<uint64_t> gm(G);      // all qubits of gate i (targets and controls)
     std::vector<char> special(G);
@@ -237,9 +237,10 @@ void plan_fusion_frontier(const std::vector<PendingGate>& q, int max_k, int nq,
     // gates of S | add are those of S plus what absorbing S | add from S's
     // end positions adds.
     std::vector<int> pS(nq), scratch(nq);
-    // grow a candidate set from S up to max_k qubits; returns its gate count
-    auto grow = [&](uint64_t& S) {
-        pS = ptr;
+    // grow a candidate set from S up to max_k qubits with the queues at
+    // positions base; returns its gate count
+    auto grow = [&](uint64_t& S, const std::vector<int>& base) {
+        pS = base;
         int cS = absorb(S, pS, nullptr);
         while (__builtin_popcountll(S) < max_k) {
             int best = -1, best_add = 0;
@@ -251,9 +252,9 @@ void plan_fusion_frontier(const std::vector<PendingGate>& q, int max_k, int nq,
                 if (sc > best || (sc == best && na < best_add)) { best = sc; best_add = na; best_m = add; }
             };
             for (int b = 0; b < nq; ++b) {
-                if (((S >> b) & 1ull) || ptr[b] >= (int)queue[b].size()) continue;
+                if (((S >> b) & 1ull) || base[b] >= (int)queue[b].size()) continue;
                 consider(1ull << b);
-                const int gi = queue[b][ptr[b]];
+                const int gi = queue[b][base[b]];
                 if (!special[gi]) consider(gm[gi] & ~S);
             }
             if (best < 0) break;
@@ -262,6 +263,25 @@ void plan_fusion_frontier(const std::vector<PendingGate>& q, int max_k, int nq,
         }
         return cS;
     };
+    // (gate count, set) of the set grown from each distinct front gate
+    auto candidates = [&](const std::vector<int>& base, std::vector<std::pair<int, uint64_t>>& out) {
+        out.clear();
+        for (int b = 0; b < nq; ++b) {
+            const int gi = front(b, base);
+            if (gi < 0 || special[gi]) continue;
+            uint64_t S = gm[gi];
+            bool dup = false;   // the same front gate seen from another of its qubits
+            for (int c = 0; c < b && !dup; ++c) {
+                const int gc = front(c, base);
+                dup = gc >= 0 && !special[gc] && gm[gc] == gm[gi];
+            }
+            if (dup) continue;
+            const int cnt = grow(S, base);
+            out.emplace_back(cnt, S);
+        }
+    };
+    std::vector<std::pair<int, uint64_t>> cand, next;
+    std::vector<int> after(nq);
     int remaining = G;
     std::vector<int> taken;
     while (remaining > 0) {
@@ -284,20 +304,34 @@ void plan_fusion_frontier(const std::vector<PendingGate>& q, int max_k, int nq,
             emit(std::move(p));
         }
         if (emitted) continue;
-        // the best block over the sets grown from each front gate
+        // the best block over the sets grown from each front gate; with
+        // look-ahead, the sets are ranked by their own gate count plus that
+        // of the best block after them
+        candidates(ptr, cand);
         uint64_t bestS = 0;
         int bestc = -1;
-        std::vector<uint64_t> seen;
-        for (int b = 0; b < nq; ++b) {
-            const int gi = front(b, ptr);
-            if (gi < 0 || special[gi]) continue;
-            uint64_t S = gm[gi];
-            if (std::find(seen.begin(), seen.end(), S) != seen.end()) continue;
-            seen.push_back(S);
-            const int c = grow(S);
+        for (auto& [c, S] : cand)
             if (c > bestc || (c == bestc && __builtin_popcountll(S) < __builtin_popcountll(bestS))) {
                 bestc = c;
                 bestS = S;
+            }
+        if (lookahead && cand.size() > 1) {
+            std::sort(cand.begin(), cand.end(), [](const std::pair<int, uint64_t>& x, const std::pair<int, uint64_t>& y) {
+                return x.first != y.first ? x.first > y.first
+                                          : __builtin_popcountll(x.second) < __builtin_popcountll(y.second);
+            });
+            int best_total = -1;
+            for (auto& [c, S] : cand) {
+                after = ptr;
+                absorb(S, after, nullptr);
+                candidates(after, next);
+                int nb = 0;
+                for (auto& x : next) nb = std::max(nb, x.first);
+                if (c + nb > best_total) {
+                    best_total = c + nb;
+                    bestc = c;
+                    bestS = S;
+                }
             }
         }
         if (bestc <= 0) fail(QE_ERR_STATE, "fusion planner made no progress");
@@ -328,7 +362,7 @@ void plan_fusion_frontier(const std::vector<PendingGate>& q, int max_k, int nq,
 // max_k <= 1: no fusion, every gate is its own pass.  Without `matrices` only
 // the qubit sets are produced.
 void plan_fusion(const std::vector<PendingGate>& q, int max_k, int nq, const std::function<void(Planned&&)>& emit,
-                 bool matrices = true) {
+                 bool matrices = true, bool lookahead = false) {
     if (max_k <= 1) {
         for (auto& g : q) {
             Planned p;
@@ -339,14 +373,22 @@ void plan_fusion(const std::vector<PendingGate>& q, int max_k, int nq, const std
         }
         return;
     }
-    plan_fusion_frontier(q, max_k, nq, emit, matrices);
+    plan_fusion_frontier(q, max_k, nq, emit, matrices, lookahead);
 }
 
-std::vector<Planned> plan_fusion_list(const std::vector<PendingGate>& q, int max_k, int nq, bool matrices) {
+std::vector<Planned> plan_fusion_list(const std::vector<PendingGate>& q, int max_k, int nq, bool matrices,
+                                      bool lookahead) {
     std::vector<Planned> out;
-    plan_fusion(q, max_k, nq, [&](Planned&& p) { out.push_back(std::move(p)); }, matrices);
+    plan_fusion(q, max_k, nq, [&](Planned&& p) { out.push_back(std::move(p)); }, matrices, lookahead);
     return out;
 }
+
+// Look-ahead costs about ten times the planning (~3 ms per block for 900
+// gates on 30 qubits, against ~0.3 ms); it is used from 2^30 amplitudes on,
+// where a pass is long enough for the planning of the next block to hide
+// behind it.  On seven random circuits of 28-32 qubits it takes 2 % fewer
+// blocks in all (never more on any of them).
+bool plan_lookahead(int n) { return n >= 30; }
 
 uint32_t* status_word_host(qe_state* s) {
     if (!s->status_host) {
@@ -373,8 +415,9 @@ void flush(qe_state* s) {
     const int k = choose_fusion_width(s, q);
     s->stats.gates += q.size();
     try {
-        plan_fusion(q, k, s->n,
-                    [&](Planned&& b) { apply_block(s, (int)b.q.size(), b.q.data(), b.U, b.cmask); });
+        plan_fusion(
+            q, k, s->n, [&](Planned&& b) { apply_block(s, (int)b.q.size(), b.q.data(), b.U, b.cmask); }, true,
+            plan_lookahead(s->n));
     } catch (...) {
         try {
             complete_pending(s);
@@ -393,7 +436,7 @@ int choose_fusion_width(qe_state* s, const std::vector<PendingGate>& q) {
     std::vector<float> X;
     std::vector<int> owner;
     for (int k = 1; k <= s->max_k; ++k) {
-        for (auto& b : plan_fusion_list(q, k, s->n, false)) {
+        for (auto& b : plan_fusion_list(q, k, s->n, false, false)) {
             int lo = s->n, hi = 0;
             for (int v : b.q) { lo = std::min(lo, v); hi = std::max(hi, v); }
             for (int j = 0; j < s->n; ++j)
@@ -497,7 +540,7 @@ int qe_plan_fusion(int n, int ngates, const int* k, const int* qubits, const dou
         const double* m = matrices + mat_offset[g];
         for (int i = 0; i < D * D; ++i) q[g].U[i] = cd(m[2 * i], m[2 * i + 1]);
     }
-    const std::vector<Planned> plan = plan_fusion_list(q, max_k, n, true);
+    const std::vector<Planned> plan = plan_fusion_list(q, max_k, n, true, plan_lookahead(n));
     *nblocks = (int)plan.size();
     if ((int)plan.size() > cap) fail(QE_ERR_ARG, "more blocks than cap");
     if (!plan.empty() && (!block_k || !block_qubits || !block_matrices)) fail(QE_ERR_ARG, "output arrays are NULL");
