@@ -59,6 +59,29 @@ def test_blocks_are_unitary_and_ordered_on_shared_qubits(lib):
         assert np.max(np.abs(apply_all(psi, blocks) - want)) < 1e-12
 
 
+@pytest.mark.parametrize("max_k", [2, 3, 4, 5])
+def test_mixed_width_gates(lib, max_k):
+    # gates of 1..5 qubits; those wider than max_k stay passes of their own
+    # and the blocks around them keep the order on their shared qubits
+    n = 8
+    rng = np.random.default_rng(40 + max_k)
+    gates = []
+    for _ in range(60):
+        w = int(rng.integers(1, 6))
+        qs = [int(v) for v in rng.permutation(n)[:w]]
+        z = rng.standard_normal((1 << w, 1 << w)) + 1j * rng.standard_normal((1 << w, 1 << w))
+        U, _ = np.linalg.qr(z)
+        gates.append(I.Gate(tuple(qs), U))
+    blocks = qe.plan_fusion(n, gates, max_k)
+    for q, U in blocks:
+        assert len(q) <= max(max_k, max(len(g.qubits) for g in gates))
+        assert np.allclose(U.conj().T @ U, np.eye(len(U)), atol=1e-12)
+    assert len(blocks) <= len(gates)
+    psi = I.random_state(n, 5)
+    want = apply_all(psi, [(g.qubits, g.matrix) for g in gates])
+    assert np.max(np.abs(apply_all(psi, blocks) - want)) < 1e-12
+
+
 def test_frontier_blocks_on_the_benchmark_circuits(lib):
     # each pass takes the qubit set that absorbs the most front gates (from
     # 30 qubits on ranked with a one-block look-ahead): on the depth-20,
