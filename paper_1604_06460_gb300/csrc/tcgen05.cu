@@ -29,6 +29,7 @@
 // raises a shared abort flag on a timeout; the status word reports it and
 // tensor memory is freed after the MMAs have drained.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 
 #include "qe_arith.cuh"
@@ -61,6 +62,7 @@ struct TcArgs {
     uint32_t* status;
     long long spin_limit;
     const float* W;           // [2][kN * kK]: hi, lo parts of W, row n, column k
+    int stall_test;           // failure-path test: the first tile's operand is never announced
 };
 
 // Round an FP32 value to TF32 (10 explicit mantissa bits, nearest, ties
@@ -294,7 +296,7 @@ __global__ void __maxnreg__(72) k_gate_tc5(const __grid_constant__ TcArgs a) {
                 *reinterpret_cast<float4*>(sA_lo + sw128_offset(lr, 32 + 4 * q, kRows)) = il;
             }
             asm volatile("fence.proxy.async.shared::cta;");
-            mbar_arrive(&mbAFull[b]);
+            if (!(a.stall_test && i == 0)) mbar_arrive(&mbAFull[b]);
 #pragma unroll
             for (int k = 0; k < 8; ++k) cur[k] = nxt[k];
         }
@@ -389,6 +391,12 @@ void launch_gate_tc5(qe_state* s, const int* qubits, const cd* U) {
     a.status = status;
     a.W = (const float*)(scr + 256);
     a.spin_limit = 1ll << 21;   // polls of up to kSuspendNs each
+    // Failure-path test (QE_TEST_STALL_TC64=1): the splitters withhold the
+    // first tile's operand arrival, so the MMA thread's wait runs out after a
+    // short limit and every role leaves through the shared abort flag.
+    const char* stall = std::getenv("QE_TEST_STALL_TC64");
+    a.stall_test = (stall != nullptr && stall[0] == '1') ? 1 : 0;
+    if (a.stall_test) a.spin_limit = 1ll << 12;
     const size_t smem = 1024 + (size_t)2 * kN * kK * 4 + (size_t)2 * 2 * kRows * kK * 4;
     QE_CUDA(cudaFuncSetAttribute(k_gate_tc5, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     QE_CUDA(cudaFuncSetAttribute(k_gate_tc5, cudaFuncAttributePreferredSharedMemoryCarveout, 100));

@@ -490,6 +490,29 @@ def test_tensor_core_fused_circuit_c64(qe):
     assert oracle.fidelity(ref, got) > 1 - 1e-8
 
 
+# The complex64 kernel's bounded waits: the splitters withhold the first
+# operand arrival, the MMA thread's wait runs out, every role leaves through
+# the abort flag; QE_ERR_TIMEOUT, then the same context computes correctly.
+def test_tensor_core_c64_wait_timeout_reports_and_recovers(qe, monkeypatch):
+    from paper_1604_06460_gb300.qe import QEError
+    n, qubits = 14, [1, 4, 6, 9, 13]
+    U = rand_unitary(32, np.random.default_rng(78))
+    psi = I.random_state(n, 22)
+    with make(qe, n, "c64", psi=psi, max_k=5) as st:
+        monkeypatch.setenv("QE_TEST_STALL_TC64", "1")
+        with pytest.raises(QEError) as err:
+            st.apply_gate(qubits, U)
+            st.flush()
+        assert err.value.status == -4 and "QE_ERR_TIMEOUT" in str(err.value)
+        monkeypatch.delenv("QE_TEST_STALL_TC64")
+        st.set(psi)
+        st.apply_gate(qubits, U)
+        got = st.get().astype(np.complex128)
+    ref = oracle.apply_gate(psi, qubits, U)
+    assert np.max(np.abs(got - ref)) < 2e-5
+    assert oracle.fidelity(ref, got) > 1 - 1e-8
+
+
 # ------------------------------------------ tensor cores (complex128, k = 4, 5)
 # Exact integer-digit products on the FP16 tensor pipe: inputs and matrix
 # entries are rounded to 2^-48 of their row scale, so the FP64 bar holds.
