@@ -169,15 +169,46 @@ void apply_in_place(std::vector<cd>& U, int D, int gk, const int* pos, const std
             if ((c >> j) & 1) o |= 1 << pos[j];
         dep[c] = o;
     }
-    cd x[32];
+    // explicit real arithmetic (no library complex multiply); the rows of a
+    // group are contiguous runs of D entries
+    double* u = reinterpret_cast<double*>(U.data());
+    const double* g = reinterpret_cast<const double*>(G.data());
+    if (gk == 1) {
+        const double g00r = g[0], g00i = g[1], g01r = g[2], g01i = g[3];
+        const double g10r = g[4], g10i = g[5], g11r = g[6], g11i = g[7];
+        for (int r0 = 0; r0 < D; ++r0) {
+            if (r0 & gmask) continue;
+            double* a = u + 2 * (size_t)r0 * D;
+            double* b = u + 2 * (size_t)(r0 | dep[1]) * D;
+            for (int col = 0; col < D; ++col) {
+                const double ar = a[2 * col], ai = a[2 * col + 1], br = b[2 * col], bi = b[2 * col + 1];
+                a[2 * col] = g00r * ar - g00i * ai + g01r * br - g01i * bi;
+                a[2 * col + 1] = g00r * ai + g00i * ar + g01r * bi + g01i * br;
+                b[2 * col] = g10r * ar - g10i * ai + g11r * br - g11i * bi;
+                b[2 * col + 1] = g10r * ai + g10i * ar + g11r * bi + g11i * br;
+            }
+        }
+        return;
+    }
+    double xr[32], xi[32];
     for (int r0 = 0; r0 < D; ++r0) {
         if (r0 & gmask) continue;
         for (int col = 0; col < D; ++col) {
-            for (int c = 0; c < Dg; ++c) x[c] = U[(size_t)(r0 | dep[c]) * D + col];
+            for (int c = 0; c < Dg; ++c) {
+                const double* e = u + 2 * ((size_t)(r0 | dep[c]) * D + col);
+                xr[c] = e[0];
+                xi[c] = e[1];
+            }
             for (int r = 0; r < Dg; ++r) {
-                cd acc = 0.0;
-                for (int c = 0; c < Dg; ++c) acc += G[(size_t)r * Dg + c] * x[c];
-                U[(size_t)(r0 | dep[r]) * D + col] = acc;
+                double sr = 0.0, si = 0.0;
+                const double* gr = g + 2 * (size_t)r * Dg;
+                for (int c = 0; c < Dg; ++c) {
+                    sr += gr[2 * c] * xr[c] - gr[2 * c + 1] * xi[c];
+                    si += gr[2 * c] * xi[c] + gr[2 * c + 1] * xr[c];
+                }
+                double* e = u + 2 * ((size_t)(r0 | dep[r]) * D + col);
+                e[0] = sr;
+                e[1] = si;
             }
         }
     }
