@@ -140,7 +140,10 @@ int qe_probs(qe_state* s, int m, const int* qubits, double* out);
 /* sum_i |alpha_i|^2 in compensated FP64. */
 int qe_norm2(qe_state* s, double* out);
 
-/* Apply queued gates / wait for all work on the state's stream. */
+/* Apply queued gates / wait for all work on the state's stream.  qe_flush
+ * launches the fused passes as they are planned and, before returning, waits
+ * for the last tensor-core pass: QE_ERR_TIMEOUT if one of them reported a
+ * bounded wait that ran out (the remaining queued gates are then dropped). */
 int qe_flush(qe_state* s);
 int qe_sync(qe_state* s);
 
@@ -227,7 +230,10 @@ int qe_planned_fusion_width(qe_state* s, int* k);
 
 /* Host-only planning (no device work, no state): group ngates uncontrolled
  * gates on n qubits into fused blocks of at most max_k (1..5) qubits exactly
- * as the flush does (Sec. II, gate fusion).  Gate g acts on k[g] (1..5)
+ * as the flush does (Sec. II, gate fusion): each block is the qubit set that
+ * absorbs the most gates at the fronts of the per-qubit gate queues; a gate
+ * wider than max_k stays a block of its own, and max_k = 1 applies every gate
+ * as its own block.  Gate g acts on k[g] (1..5)
  * qubits qubits[5 g + j], j < k[g], with the row-major 2^k x 2^k complex
  * matrix (interleaved re, im doubles) at matrices + mat_offset[g] (doubles).
  * Outputs, for blocks b < *nblocks (in application order): width
