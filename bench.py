@@ -23,6 +23,7 @@ import os
 import re
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -48,6 +49,8 @@ def parse():
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64"], help="state type for --only qft")
     ap.add_argument("--kernel-case", default="", choices=["", *KERNEL_CASES],
                     help="run a few launches of one hot kernel on a small state (the ncu capture cases)")
+    ap.add_argument("--clocks-csv", default=None,
+                    help="keep the nvidia-smi clock samples of the timed region in this file")
     return ap.parse_args()
 
 
@@ -164,16 +167,23 @@ def run_reference(args):
 
 # ----------------------------------------------------------------- helpers
 class Clocks:
-    """nvidia-smi samples every 200 ms while the timed region runs."""
+    """nvidia-smi samples every 200 ms while the timed region runs, written to
+    `path` (a temporary file, removed after summary(), when `path` is None)."""
 
-    def __init__(self, index):
+    def __init__(self, index, path=None):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.keep = path is not None
+        if path is None:
+            fd, path = tempfile.mkstemp(prefix="clocks_bench_", suffix=".csv")
+            os.close(fd)
+        self.path = path
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            d = os.path.dirname(self.path)
+            if d:
+                os.makedirs(d, exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
@@ -189,14 +199,18 @@ class Clocks:
         if self.proc:
             self.proc.terminate()
             self.proc.wait()
+        if getattr(self, "f", None):
             self.f.close()
 
     def summary(self):
-        if not self.proc:
-            return None
+        try:
+            lines = open(self.path).read().splitlines() if self.proc else []
+        finally:
+            if not self.keep and os.path.exists(self.path):
+                os.remove(self.path)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in lines:
             p = [x.strip() for x in line.split(",")]
             if len(p) < 8:
                 continue
@@ -357,7 +371,7 @@ def main():
     st.profile(True)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    with Clocks(torch.cuda.current_device()) as clk:
+    with Clocks(torch.cuda.current_device(), args.clocks_csv) as clk:
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(args.steps):
