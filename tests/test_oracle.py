@@ -312,6 +312,22 @@ def test_tfim_closed_forms():
     assert abs(oracle.expectation(plus, xm, zm, cf) - 0.7 * n) < 1e-13
 
 
+@pytest.mark.parametrize("n,seed", [(2, 4), (7, 5)])
+def test_one_layer_ansatz_tfim_energy_closed_form(n, seed):
+    # RY(theta) then RZ(phi) on |0> gives <Z> = cos theta, <X> = sin theta
+    # cos phi; the CZ ladder commutes with every Z_i Z_{i+1} and turns X_i
+    # into Z_{i-1} X_i Z_{i+1}, whose mean factorises over the product state.
+    psi = oracle.zero_state(n)
+    for g in I.ansatz_circuit(n, 1, seed):
+        psi = oracle.apply_gate(psi, g.qubits, g.matrix)
+    th, ph = I.ansatz_angles(n, 1, seed)[0].T
+    zz = sum(np.cos(th[i]) * np.cos(th[i + 1]) for i in range(n - 1))
+    x = sum(np.sin(th[i]) * np.cos(ph[i]) * np.prod([np.cos(th[j]) for j in (i - 1, i + 1) if 0 <= j < n])
+            for i in range(n))
+    xm, zm, cf = I.tfim_terms(n)
+    assert abs(oracle.expectation(psi, xm, zm, cf) - (zz + 0.7 * x)) < 1e-13
+
+
 def test_expectation_dense_brute_force():
     n = 6
     rng = np.random.default_rng(12)
