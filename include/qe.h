@@ -178,11 +178,20 @@ int qe_reset_stats(qe_state* s);
  * Ising chain; the expectation computed directly, Sec. III-D).  qe_batch_create
  * copies the inputs, allocates the device states of circuits too large for
  * one CTA's shared memory, builds the work queue and captures the graph.
- * qe_batch_run replays it and writes count energies to host memory.
- * qe_batch_tune times the candidate tile schedules (tile bits, tiles per work
- * item, threads per CTA: 128 or 256) reps times each and keeps the fastest; the chosen
- * plan is returned through the optional pointers.  qe_batch_info reports
- * the algorithmic HBM bytes of one run and the number of work items. */
+ * qe_batch_run replays it, synchronises the stream and writes count energies
+ * to host memory (energies may be NULL to discard them); it returns
+ * QE_ERR_TIMEOUT if a work item's bounded wait for the items it depends on
+ * ran out.  qe_batch_tune times the candidate tile schedules (tile bits,
+ * tiles per work item, threads per CTA: 128, 256 or 512) reps times each and
+ * keeps the fastest; the chosen plan is returned through the optional
+ * pointers.  qe_batch_set_plan sets one: 4 <= tile_bits <= 12 (13 for
+ * QE_C64) with 2 tile_bits - 1 >= the largest n, tiles_per_item >= 1.
+ * qe_batch_info reports the algorithmic HBM bytes of one run and the number
+ * of work items.  QE_ERR_ARG: count or layers < 1, NULL nqubits or angles, a
+ * qubit count out of range, a non-finite angle or field, an unknown dtype, a
+ * plan outside the ranges above, reps < 1.  The stream is borrowed (NULL =
+ * legacy default stream); the batch owns its device memory, which
+ * qe_batch_free releases. */
 typedef struct qe_batch qe_batch;
 int qe_batch_create(int count, const int* nqubits, int layers, const double* angles,
                     double hx, int dtype, void* stream, qe_batch** out);
@@ -223,6 +232,9 @@ int qe_cost_model_predict(qe_cost_model* m, const float* X, int n, float* y);
 int qe_cost_model_free(qe_cost_model* m);
 int qe_cost_features(int op, int n, int dtype, int k, int lo, int hi, int m, uint64_t c,
                      float* features);
+/* Attach a model to a state (NULL detaches it) after flushing the queued
+ * gates.  The state borrows the model: keep it alive, and do not pass it to
+ * qe_cost_model_free, while a state holds it. */
 int qe_set_cost_model(qe_state* s, qe_cost_model* model);
 /* Fusion width the planner would use for the gates queued now (the state's
  * max_k, or the model's choice under QE_POLICY_AUTO), without applying them. */
