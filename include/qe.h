@@ -74,7 +74,8 @@ int qe_free_state(qe_state* s);
 /* Report n, dtype and the device address of amplitude 0. */
 int qe_state_info(const qe_state* s, int* n, int* dtype, void** dev_ptr);
 
-/* Reset to the basis state |index> (Sec. II): alpha_index = 1, all others 0. */
+/* Reset to the basis state |index> (Sec. II): alpha_index = 1, all others 0.
+ * QE_ERR_ARG if index >= 2^n. */
 int qe_init_basis(qe_state* s, uint64_t index);
 
 /* Fill with i.i.d. standard complex Gaussian amplitudes and normalise by the
@@ -86,7 +87,8 @@ int qe_init_random(qe_state* s, uint64_t seed);
 
 /* Copy count amplitudes between host memory (in the state's dtype,
  * interleaved) and the state, starting at amplitude offset.  Pending gates
- * are applied before a read and before an overwrite. */
+ * are applied before a read and before an overwrite.  QE_ERR_ARG if
+ * offset + count > 2^n, or host is NULL with count > 0. */
 int qe_set_amplitudes(qe_state* s, const void* host, uint64_t offset, uint64_t count);
 int qe_get_amplitudes(qe_state* s, void* host, uint64_t offset, uint64_t count);
 
@@ -105,7 +107,8 @@ int qe_apply_gate(qe_state* s, int k, const int* qubits, const double* matrix);
 /* Apply U (2^k x 2^k, 0 <= k <= 2) on targets[] only where every one of the
  * nc controls[] is 1 (multi-controlled gates such as the Toffoli / MCX used
  * by reversible arithmetic, Sec. III).  k = 0 multiplies the controlled
- * amplitudes by the scalar matrix[0]. */
+ * amplitudes by the scalar matrix[0].  QE_ERR_ARG for k > 2, a repeated
+ * qubit, or a qubit that is both control and target. */
 int qe_apply_controlled(qe_state* s, int nc, const int* controls, int k,
                         const int* targets, const double* matrix);
 
@@ -115,7 +118,8 @@ int qe_apply_controlled(qe_state* s, int nc, const int* controls, int k,
  *     alpha_l -> 2^{-m/2} sum_k alpha_k exp(+2 pi i k l / 2^m),
  * natural output order; inverse != 0 uses the opposite sign.  Emulated as an
  * in-place FFT, or simulated as m Hadamards, m(m-1)/2 CR gates and the
- * qubit reversal, as the policy decides. */
+ * qubit reversal, as the policy decides.  QE_ERR_ARG unless m >= 1, lo >= 0
+ * and lo + m <= n. */
 int qe_apply_qft(qe_state* s, int lo, int m, int inverse);
 
 /* Add the classical constant c to the m-qubit register qubits[] (bit j of
@@ -128,7 +132,9 @@ int qe_apply_add_const(qe_state* s, int m, const int* qubits, uint64_t c);
 /* <psi| sum_t coeff[t] P_t |psi> for Pauli strings P_t given by bit masks
  * over the qubits: (x,z) = (0,0) I, (1,0) X, (0,1) Z, (1,1) Y (Sec. III-D:
  * the expectation computed in one step instead of by repeated sampling).
- * Accumulated in FP64 with compensation; *out receives the real value. */
+ * Accumulated in FP64 with compensation; *out receives the real value
+ * (0 for nterms = 0).  QE_ERR_ARG for nterms < 0, a mask naming a qubit >= n
+ * or a non-finite coefficient. */
 int qe_expectation(qe_state* s, int nterms, const uint64_t* xmask,
                    const uint64_t* zmask, const double* coeff, double* out);
 
