@@ -450,7 +450,13 @@ def test_invalid_arguments_leave_state_untouched(qe):
     with make(qe, n, psi=psi) as st:
         for bad in [lambda: st.apply_gate([0, 0], np.eye(4)), lambda: st.apply_gate([6], np.eye(2)),
                     lambda: st.apply_qft(3, 4), lambda: st.add_const([7], 1),
-                    lambda: st.probs([0, 0]), lambda: st.apply_gate([1], np.full((2, 2), np.nan))]:
+                    lambda: st.probs([0, 0]), lambda: st.apply_gate([1], np.full((2, 2), np.nan)),
+                    lambda: st.apply_qft(-1, 2), lambda: st.init_basis(1 << n),
+                    lambda: st.set(np.zeros(10), offset=60), lambda: st.get(offset=60, count=10),
+                    lambda: st.apply_controlled([1], [1], I.mat_x()),
+                    lambda: st.apply_controlled([0], [1, 2, 3], np.eye(8)),
+                    lambda: st.expectation([1 << n], [0], [1.0]),
+                    lambda: st.expectation([0], [1], [np.inf])]:
             with pytest.raises(qe.QEError) as ei:
                 bad()
             assert ei.value.status == -1
