@@ -12,8 +12,11 @@
  * Conventions used by every call
  *   - qubit q is bit q of the amplitude index (little-endian); amplitudes are
  *     interleaved (re, im) in one contiguous allocation of 2^n elements;
- *   - QE_C128 stores complex128 (16 B/amplitude, computed to FP64 accuracy),
- *     QE_C64 stores complex64 (8 B/amplitude, computed in FP32);
+ *   - QE_C128 stores complex128 (16 B/amplitude); by default it is computed
+ *     in the FP64 mode (qe_set_arith: 53-bit FP64 arithmetic, dense blocks
+ *     as exact products of 56-bit splittings on the tensor cores), or in the
+ *     faster double-float mode on request.  QE_C64 stores complex64
+ *     (8 B/amplitude) and is computed in FP32;
  *   - a k-qubit matrix is 2^k x 2^k complex, row-major, interleaved doubles
  *     (2 * 4^k values), host memory, whose row/column bit j <-> qubits[j];
  *   - all device work is enqueued on the state's CUDA stream; calls that
@@ -158,6 +161,35 @@ int qe_sync(qe_state* s);
  * (5 where the tensor cores take 3-5-qubit blocks, i.e. n >= 12, else 2 for
  * complex128 and 4 for complex64).  QE_ERR_ARG for other values. */
 int qe_set_policy(qe_state* s, int policy, int max_k);
+
+/* Arithmetic of a complex128 state.  The paper's CPU kernels compute in
+ * double complex (Sec. IV-A); GB300 runs FP64 at about 1/64 of its FP32
+ * rate, so the library offers two modes:
+ *   QE_ARITH_FP64 (default): every operation at least as accurate as FP64
+ *     arithmetic.  Dense 3-5-qubit blocks (n >= 12) run on the tensor cores
+ *     as exact products of integer digits: every input is rounded to 2^-56 of
+ *     its 32-amplitude group's scale and every matrix entry to 2^-56 of its
+ *     row's, the digit products are summed exactly and each output is
+ *     rounded once to a double, so an output is within 2^-50 of the product
+ *     of the two scales -- inside the worst-case rounding error of an FP64
+ *     dot product of the same 64 real terms.  1-2-qubit, diagonal,
+ *     controlled and smaller-state gates, the FFT, expectation values and
+ *     probabilities run in native FP64 (53-bit significands).
+ *   QE_ARITH_DF64: the fast mode.  Values are split into pairs of floats
+ *     (double-float, 47 significant bits; magnitudes below 2^-80 keep only
+ *     the leading float, below 2^-126 become zero, and magnitudes of 2^127
+ *     or more are not representable), dense 3-5-qubit blocks use 48-bit
+ *     splittings on the tensor cores (inputs rounded to 2^-48 of their group's
+ *     scale), and reductions sum float-float partials of about 44 bits.  For
+ *     unitary gates on normalised states the results stay within 1e-12 of
+ *     FP64 arithmetic over thousands of gates; other inputs get no such bound.
+ * Both modes give bit-identical permutations.  Switching flushes the queued
+ * gates and synchronises the stream; the fusion width follows the mode's
+ * default unless one was set with qe_set_policy.  QE_ERR_ARG for another
+ * value. */
+typedef enum { QE_ARITH_FP64 = 0, QE_ARITH_DF64 = 1 } qe_arith;
+int qe_set_arith(qe_state* s, int arith);
+int qe_get_arith(const qe_state* s, int* arith);
 
 /* Counters since the last reset: kernel launches, full-state passes, and the
  * algorithmic bytes those passes move (reads + writes, see Sec. III-B's

@@ -30,9 +30,10 @@ def build(force: bool = False) -> Path:
     _LIB_DIR.mkdir(exist_ok=True)
     if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
         tmp = _LIB_DIR / f"liboracle.{os.getpid()}.so"
-        subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-             "-o", str(tmp), str(_SRC), "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(tmp), str(_SRC)]
+        # OpenMP for the gate loops when the compiler has it; otherwise one thread
+        if subprocess.run(base + ["-fopenmp", "-lm"], capture_output=True).returncode != 0:
+            subprocess.check_call(base + ["-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -46,6 +47,8 @@ def _load():
         i, u64, d = C.c_int, C.c_uint64, C.c_double
         sig = {
             "or_philox4x32_10": (None, [dp, dp, dp]),
+            "or_set_threads": (None, [i]),
+            "or_max_threads": (i, []),
             "or_norm2": (d, [dp, i]),
             "or_init_zero": (None, [dp, i]),
             "or_init_gaussian": (None, [dp, i, u64]),
@@ -88,6 +91,16 @@ def _ptr(a):
     return a.ctypes.data_as(C.c_void_p)
 
 
+def set_threads(t):
+    """Host threads for the gate loops (OpenMP; no effect without it)."""
+    _load().or_set_threads(int(t))
+
+
+def max_threads():
+    """Threads the gate loops use (1 when the oracle was built without OpenMP)."""
+    return int(_load().or_max_threads())
+
+
 def philox4x32_10(ctr, key):
     c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32))
     k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
@@ -119,9 +132,14 @@ def norm2(psi):
     return _load().or_norm2(_ptr(a), n)
 
 
-def apply_gate(psi, qubits, matrix):
+def apply_gate(psi, qubits, matrix, inplace=False):
+    """The gate applied to a copy of psi (to psi itself, a C-contiguous
+    complex128 array, with inplace=True)."""
     a, n = _state(psi)
-    a = a.copy()
+    if not inplace:
+        a = a.copy()
+    elif a is not psi:
+        raise ValueError("inplace needs a C-contiguous complex128 array")
     q = _ints(qubits)
     U = np.ascontiguousarray(np.asarray(matrix, dtype=np.complex128))
     if U.shape != (1 << q.size, 1 << q.size):
@@ -130,9 +148,12 @@ def apply_gate(psi, qubits, matrix):
     return a
 
 
-def apply_controlled(psi, controls, targets, matrix):
+def apply_controlled(psi, controls, targets, matrix, inplace=False):
     a, n = _state(psi)
-    a = a.copy()
+    if not inplace:
+        a = a.copy()
+    elif a is not psi:
+        raise ValueError("inplace needs a C-contiguous complex128 array")
     c = _ints(controls)
     t = _ints(targets)
     U = np.ascontiguousarray(np.asarray(matrix, dtype=np.complex128))
@@ -140,9 +161,12 @@ def apply_controlled(psi, controls, targets, matrix):
     return a
 
 
-def apply_mcx(psi, controls, target):
+def apply_mcx(psi, controls, target, inplace=False):
     a, n = _state(psi)
-    a = a.copy()
+    if not inplace:
+        a = a.copy()
+    elif a is not psi:
+        raise ValueError("inplace needs a C-contiguous complex128 array")
     c = _ints(controls)
     _load().or_apply_mcx(_ptr(a), n, c.size, _ptr(c), int(target))
     return a

@@ -17,6 +17,9 @@
  *     column index carries bit j <-> qubits[j].
  *   - Every function is the definition written out, loop by loop; sums of
  *     many terms use Neumaier's compensated summation.
+ *   - Gate application may run its independent amplitude groups on several
+ *     host threads (OpenMP, when the compiler provides it); each group is
+ *     still computed by the same loop, so the arithmetic is unchanged.
  */
 #define _USE_MATH_DEFINES
 #include <complex.h>
@@ -24,8 +27,27 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef double complex cplx;
+
+/* Host threads used by the gate loops (1 without OpenMP). */
+void or_set_threads(int t) {
+#ifdef _OPENMP
+    omp_set_num_threads(t > 0 ? t : 1);
+#else
+    (void)t;
+#endif
+}
+int or_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -141,17 +163,21 @@ void or_gaussian_slice(cplx* out, uint64_t seed, uint64_t i0, uint64_t cnt) {
 void or_apply_gate(cplx* psi, int n, int k, const int* qubits, const cplx* U) {
     uint64_t dim = (uint64_t)1 << n, K = (uint64_t)1 << k;
     uint64_t gate_mask = deposit(K - 1, k, qubits);
-    cplx* v = (cplx*)malloc(K * sizeof(cplx));
-    for (uint64_t x = 0; x < dim; ++x) {
-        if (x & gate_mask) continue;          /* x is the base of a group */
-        for (uint64_t c = 0; c < K; ++c) v[c] = psi[x | deposit(c, k, qubits)];
-        for (uint64_t r = 0; r < K; ++r) {
-            cplx acc = 0.0;
-            for (uint64_t c = 0; c < K; ++c) acc += U[r * K + c] * v[c];
-            psi[x | deposit(r, k, qubits)] = acc;
+#pragma omp parallel
+    {
+        cplx* v = (cplx*)malloc(K * sizeof(cplx));   /* this thread's copy of one group */
+#pragma omp for schedule(static)
+        for (uint64_t x = 0; x < dim; ++x) {
+            if (x & gate_mask) continue;          /* x is the base of a group */
+            for (uint64_t c = 0; c < K; ++c) v[c] = psi[x | deposit(c, k, qubits)];
+            for (uint64_t r = 0; r < K; ++r) {
+                cplx acc = 0.0;
+                for (uint64_t c = 0; c < K; ++c) acc += U[r * K + c] * v[c];
+                psi[x | deposit(r, k, qubits)] = acc;
+            }
         }
+        free(v);
     }
-    free(v);
 }
 
 /* A gate U on targets[] applied only where every control qubit is 1
@@ -162,17 +188,21 @@ void or_apply_controlled(cplx* psi, int n, int nc, const int* controls, int k,
     uint64_t cmask = 0;
     for (int j = 0; j < nc; ++j) cmask |= (uint64_t)1 << controls[j];
     uint64_t tmask = deposit(K - 1, k, targets);
-    cplx* v = (cplx*)malloc(K * sizeof(cplx));
-    for (uint64_t x = 0; x < dim; ++x) {
-        if ((x & tmask) || (x & cmask) != cmask) continue;
-        for (uint64_t c = 0; c < K; ++c) v[c] = psi[x | deposit(c, k, targets)];
-        for (uint64_t r = 0; r < K; ++r) {
-            cplx acc = 0.0;
-            for (uint64_t c = 0; c < K; ++c) acc += U[r * K + c] * v[c];
-            psi[x | deposit(r, k, targets)] = acc;
+#pragma omp parallel
+    {
+        cplx* v = (cplx*)malloc(K * sizeof(cplx));
+#pragma omp for schedule(static)
+        for (uint64_t x = 0; x < dim; ++x) {
+            if ((x & tmask) || (x & cmask) != cmask) continue;
+            for (uint64_t c = 0; c < K; ++c) v[c] = psi[x | deposit(c, k, targets)];
+            for (uint64_t r = 0; r < K; ++r) {
+                cplx acc = 0.0;
+                for (uint64_t c = 0; c < K; ++c) acc += U[r * K + c] * v[c];
+                psi[x | deposit(r, k, targets)] = acc;
+            }
         }
+        free(v);
     }
-    free(v);
 }
 
 /* Multi-controlled NOT: where every control is 1, exchange the amplitudes
@@ -181,6 +211,7 @@ void or_apply_mcx(cplx* psi, int n, int nc, const int* controls, int target) {
     uint64_t dim = (uint64_t)1 << n;
     uint64_t cmask = 0, t = (uint64_t)1 << target;
     for (int j = 0; j < nc; ++j) cmask |= (uint64_t)1 << controls[j];
+#pragma omp parallel for schedule(static)
     for (uint64_t x = 0; x < dim; ++x) {
         if ((x & t) || (x & cmask) != cmask) continue;
         cplx tmp = psi[x];

@@ -590,10 +590,10 @@ int qe_plan_fusion(int n, int ngates, const int* k, const int* qubits, const dou
 const char* qe_last_error(void) { return g_last_error.c_str(); }
 
 // Default fusion width: 5-qubit blocks where the tensor cores take them
-// (n >= 12, no native-FP64 baseline), else 2 (complex128) / 4 (complex64).
+// (n >= 12, not the native-FP64 baseline), else 2 (complex128) / 4 (complex64).
 static int default_fusion_width(const qe_state* s) {
     const bool tc_blocks = s->tensor_cores && !s->force_tile && s->n >= 12 &&
-                           !(s->dtype == QE_C128 && s->c128_native);
+                           !(s->dtype == QE_C128 && !s->c128_tc);
     return tc_blocks ? 5 : (s->dtype == QE_C128 ? 2 : 4);
 }
 
@@ -608,8 +608,11 @@ int qe_alloc_state(int n, int dtype, void* dev_ptr, size_t bytes, void* stream, 
     s->n = n;
     s->dtype = dtype;
     s->stream = (cudaStream_t)stream;
+    // QE_C128_ARITH: "df64" selects the double-float mode, "f64" the FP64
+    // mode without tensor cores (the native-FP64 baseline); unset: FP64 mode
     const char* ar = std::getenv("QE_C128_ARITH");
-    s->c128_native = (ar && std::strcmp(ar, "f64") == 0) ? 1 : 0;
+    s->arith = (ar && std::strcmp(ar, "df64") == 0) ? QE_ARITH_DF64 : QE_ARITH_FP64;
+    s->c128_tc = (ar && std::strcmp(ar, "f64") == 0) ? 0 : 1;
     const char* tl = std::getenv("QE_DENSE_TILE");
     s->force_tile = (tl && std::strcmp(tl, "1") == 0) ? 1 : 0;
     const char* tc = std::getenv("QE_TENSOR_CORES");
@@ -833,6 +836,26 @@ int qe_set_policy(qe_state* s, int policy, int max_k) {
     flush(s);
     s->policy = policy;
     s->max_k = max_k == 0 ? default_fusion_width(s) : max_k;
+    QE_API_END
+}
+
+int qe_set_arith(qe_state* s, int arith) {
+    QE_API_BEGIN
+    check_state(s);
+    if (arith != QE_ARITH_FP64 && arith != QE_ARITH_DF64) fail(QE_ERR_ARG, "unknown arithmetic mode");
+    flush(s);
+    QE_CUDA(cudaStreamSynchronize(s->stream));
+    const bool keep_k = s->max_k != default_fusion_width(s);
+    s->arith = arith;
+    if (!keep_k) s->max_k = default_fusion_width(s);
+    QE_API_END
+}
+
+int qe_get_arith(const qe_state* s, int* arith) {
+    QE_API_BEGIN
+    check_state(s);
+    if (!arith) fail(QE_ERR_ARG, "arith is NULL");
+    *arith = s->arith;
     QE_API_END
 }
 

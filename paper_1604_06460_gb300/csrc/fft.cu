@@ -447,7 +447,7 @@ void bitrev_impl(qe_state* s, int lo, int m) {
 
 void launch_qft_fft(qe_state* s, int lo, int m, int inverse) {
     if (s->dtype == QE_C64) fft_impl<F32>(s, lo, m, inverse, 0);
-    else if (s->c128_native) fft_impl<F64>(s, lo, m, inverse, 1);
+    else if (s->arith == QE_ARITH_FP64) fft_impl<F64>(s, lo, m, inverse, 1);
     else fft_impl<DF>(s, lo, m, inverse, 2);
 }
 

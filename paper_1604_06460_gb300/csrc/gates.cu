@@ -387,17 +387,17 @@ void diag_impl(qe_state* s, int k, const int* qubits, const cd* d) {
 #define QE_DISPATCH(s, FN, ...)                                  \
     do {                                                         \
         if ((s)->dtype == QE_C64) FN<F32>(__VA_ARGS__);          \
-        else if ((s)->c128_native) FN<F64>(__VA_ARGS__);         \
+        else if ((s)->arith == QE_ARITH_FP64) FN<F64>(__VA_ARGS__); \
         else FN<DF>(__VA_ARGS__);                                \
     } while (0)
 
 void launch_gate_dense(qe_state* s, int k, const int* qubits, const cd* U) {
     const bool tc64 = s->dtype == QE_C64;
-    const bool tc128 = s->dtype == QE_C128 && !s->c128_native;
-    // complex64 blocks of 4-5 qubits and complex128 blocks of 3-5 qubits run
-    // on the tensor cores (complex128 3-qubit blocks are ALU-bound in
-    // double-float arithmetic)
-    const int kmin = tc64 ? 4 : 3;
+    const bool tc128 = s->dtype == QE_C128 && s->c128_tc;
+    // complex64 blocks of 4-5 qubits and complex128 blocks of 3-5 qubits
+    // run on the tensor cores (3-qubit blocks are ALU-bound in double-float
+    // and in native FP64 arithmetic)
+    const int kmin = tc64 ? 4 : c128_tc_kmin(s);
     if ((tc64 || tc128) && s->tensor_cores && !s->force_tile && s->n >= 12 && k >= kmin) {
         auto run = [&](const int* q5, const cd* U5) {
             if (tc64) launch_gate_tc5(s, q5, U5);

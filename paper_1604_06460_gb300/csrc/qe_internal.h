@@ -52,9 +52,10 @@ struct qe_state {
     cudaStream_t stream = nullptr;
     int policy = QE_POLICY_AUTO;
     int max_k = 4;
-    int c128_native = 0;          // 1: native FP64 arithmetic for complex128
+    int arith = QE_ARITH_FP64;    // complex128 arithmetic (qe_set_arith)
+    int c128_tc = 1;              // 0: complex128 blocks never on the tensor cores (native FP64 baseline)
     int force_tile = 0;           // 1: dense gates always through shared-memory tiles
-    int tensor_cores = 1;         // complex64 blocks of 4-5 qubits on tcgen05 (n >= 12)
+    int tensor_cores = 1;         // 4-5 (complex64) / 1-5 or 3-5 (complex128) qubit blocks on tcgen05 (n >= 12)
     qe_cost_model* model = nullptr;   // learned cost model (borrowed), used by QE_POLICY_AUTO
     std::vector<qe::PendingGate> queue;
     // device scratch for reductions, grown on demand
@@ -90,6 +91,13 @@ class Launch {
 };
 void profile_clear(qe_state* s);
 inline int amp_bytes(const qe_state* s) { return s->dtype == QE_C128 ? 16 : 8; }
+// complex128 computed in native FP64 (the FP64 mode) rather than double-float
+inline bool c128_f64(const qe_state* s) { return s->dtype == QE_C128 && s->arith == QE_ARITH_FP64; }
+// dense complex128 blocks of at least this many qubits run on the tensor cores
+// (7-digit splitting in the FP64 mode, 6-digit in the double-float mode);
+// 1-2-qubit blocks stay elementwise (native FP64 or double-float): widened to
+// five qubits they would share one scale with 8-16 unrelated groups
+inline int c128_tc_kmin(const qe_state*) { return 3; }
 int num_sms();
 void* ensure_scratch(qe_state* s, size_t bytes);
 

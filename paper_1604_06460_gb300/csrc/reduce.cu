@@ -9,7 +9,9 @@
 // writes one FP64 pair (sum, Neumaier compensation) per block; a final
 // single-block kernel adds the block partials in FP64 with Neumaier's
 // compensation in a fixed order, so results are deterministic.
-// The native-FP64 policy accumulates in FP64 directly.
+// In the FP64 mode (complex128) the products and per-thread sums are native
+// FP64 (53-bit significands) instead, with the same FP64 compensated
+// combination of the block partials.
 #include <algorithm>
 #include <type_traits>
 #include <vector>
@@ -134,6 +136,31 @@ __device__ __forceinline__ void async_copy(void* dst, const void* src) {
 __device__ __forceinline__ float2 rview(float2 v) { return v; }
 __device__ __forceinline__ DF::V rview(double2 v) { return DF::load(v); }
 
+// Native FP64 reductions (the FP64 mode of complex128 states): one FP64
+// accumulator per quantity, products by fused multiply-add.
+struct AccD {
+    double s;
+};
+__device__ __forceinline__ double abs2d(const double2& v) { return __fma_rn(v.x, v.x, __dmul_rn(v.y, v.y)); }
+__device__ __forceinline__ double2 vneg(const double2& v) { return make_double2(-v.x, -v.y); }
+// acc += Re (im = false) or Im (im = true) of conj(w) v
+__device__ __forceinline__ void corr_acc(AccD& a, const double2& w, const double2& v, bool im) {
+    if (!im) a.s = __fma_rn(w.x, v.x, __fma_rn(w.y, v.y, a.s));
+    else a.s = __fma_rn(w.x, v.y, __fma_rn(-w.y, v.x, a.s));
+}
+__device__ __forceinline__ double block_reduce_d(double a, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[w] = a;
+    __syncthreads();
+    if (w == 0) {
+        a = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    }
+    return a;   // valid in thread 0
+}
+
 // ---------------------------------------------------------------- probs
 // Block b handles bin r = b / chunks and the chunk b % chunks of the
 // 2^(n-m) amplitudes whose bits at the qubits spell r.
@@ -250,9 +277,15 @@ struct ExpArgs {
 template <class S>
 constexpr int kPer = (sizeof(S) >= 16 ? (1 << 11) : (1 << 12)) / kRThreads;
 
-template <class S>
+__device__ __forceinline__ void acc_zero(Acc& a) { a = Acc{0.f, 0.f}; }
+__device__ __forceinline__ void acc_zero(AccD& a) { a.s = 0.0; }
+
+// NAT: native FP64 (complex128 in the FP64 mode); otherwise double-float
+// views (complex128) or FP32 (complex64) with compensated float sums.
+template <class S, bool NAT>
 __global__ void __launch_bounds__(kRThreads) k_expect_tile(const __grid_constant__ ExpArgs<S> a) {
-    using V = decltype(rview(S{}));
+    using V = std::conditional_t<NAT, S, decltype(rview(S{}))>;
+    using A = std::conditional_t<NAT, AccD, Acc>;
     constexpr int PER = kPer<S>;
     static_assert(sizeof(V) == sizeof(S), "tiles are converted in place");
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -260,6 +293,7 @@ __global__ void __launch_bounds__(kRThreads) k_expect_tile(const __grid_constant
     // while the current one is evaluated, then are converted in place
     V* const tiles = reinterpret_cast<V*>(smem_raw);
     __shared__ Acc sh[32];
+    __shared__ double shd[32];
     __shared__ uint64_t offA[64], offB[64];
     __shared__ uint32_t s_zl[kZT];       // zl with the tile's outside parity in bit 31
     __shared__ int s_zout[kZW];          // per group: odd outside-only masks of this tile
@@ -275,11 +309,14 @@ __global__ void __launch_bounds__(kRThreads) k_expect_tile(const __grid_constant
         offB[tid] = ob;
     }
     __syncthreads();
-    Acc zacc[kZW], zacc2[kZW], xacc[kXT];
+    A zacc[kZW], zacc2[kZW], xacc[kXT];
 #pragma unroll
-    for (int g = 0; g < kZW; ++g) zacc[g] = zacc2[g] = Acc{0.f, 0.f};
+    for (int g = 0; g < kZW; ++g) {
+        acc_zero(zacc[g]);
+        acc_zero(zacc2[g]);
+    }
 #pragma unroll
-    for (int t = 0; t < kXT; ++t) xacc[t] = Acc{0.f, 0.f};
+    for (int t = 0; t < kXT; ++t) acc_zero(xacc[t]);
     const uint32_t Tn = 1u << a.T, lowmask = (1u << a.L) - 1u;
     auto load = [&](uint64_t t, V* buf) {   // this thread's elements, raw
         const uint64_t b = insert_zero_bits(t << a.L, a.hq, a.kh);
@@ -295,7 +332,7 @@ __global__ void __launch_bounds__(kRThreads) k_expect_tile(const __grid_constant
         const uint64_t base = insert_zero_bits(t << a.L, a.hq, a.kh);
         V* const tile = tiles + (size_t)cur * Tn;
         asm volatile("cp.async.wait_group 0;" ::: "memory");
-        if (sizeof(S) == 16)   // complex128: split into double-float in place
+        if constexpr (sizeof(S) == 16 && !NAT)   // complex128: split into double-float in place
             for (uint32_t l = tid; l < Tn; l += blockDim.x) tile[l] = rview(*reinterpret_cast<const S*>(tile + l));
         __syncthreads();
         if (t + gridDim.x < a.ntiles) load(t + gridDim.x, tiles + (size_t)(cur ^ 1) * Tn);
@@ -333,11 +370,16 @@ __global__ void __launch_bounds__(kRThreads) k_expect_tile(const __grid_constant
 #pragma unroll 1
             for (int j0 = 0; j0 < PER; j0 += C) {
                 float ph[C], pl[C];
+                double pd[C];
 #pragma unroll
                 for (int j = 0; j < C; ++j) {
                     const uint32_t l = tid + (uint32_t)(j0 + j) * kRThreads;
-                    if (l < Tn) abs2(tile[l], ph[j], pl[j]);
-                    else ph[j] = pl[j] = 0.f;
+                    if constexpr (NAT) {
+                        pd[j] = (l < Tn) ? abs2d(tile[l]) : 0.0;
+                    } else {
+                        if (l < Tn) abs2(tile[l], ph[j], pl[j]);
+                        else ph[j] = pl[j] = 0.f;
+                    }
                 }
                 int begin = 0;
 #pragma unroll
@@ -356,9 +398,14 @@ __global__ void __launch_bounds__(kRThreads) k_expect_tile(const __grid_constant
                     begin = a.zg_end[g];
 #pragma unroll
                     for (int j = 0; j < C; ++j) {
-                        const float f = (float)(ng - 2 * odd[j]);
-                        const float p = fmul(ph[j], f);
-                        acc_add((j & 1) ? zacc2[g] : zacc[g], p, __fmaf_rn(pl[j], f, __fmaf_rn(ph[j], f, -p)));
+                        if constexpr (NAT) {
+                            A& z = (j & 1) ? zacc2[g] : zacc[g];
+                            z.s = __fma_rn(pd[j], (double)(ng - 2 * odd[j]), z.s);
+                        } else {
+                            const float f = (float)(ng - 2 * odd[j]);
+                            const float p = fmul(ph[j], f);
+                            acc_add((j & 1) ? zacc2[g] : zacc[g], p, __fmaf_rn(pl[j], f, __fmaf_rn(ph[j], f, -p)));
+                        }
                     }
                 }
             }
@@ -388,19 +435,29 @@ __global__ void __launch_bounds__(kRThreads) k_expect_tile(const __grid_constant
 #pragma unroll
     for (int g = 0; g < kZW; ++g) {
         if (g >= a.nzg) break;
-        Acc r = block_reduce(acc_merge(zacc[g], zacc2[g]), sh);
-        if (tid == 0) {
-            df d = df_norm(r.s, r.e);
-            neumaier(s, c, df2d(d.h, d.l) * a.zw[g]);
+        if constexpr (NAT) {
+            const double r = block_reduce_d(zacc[g].s + zacc2[g].s, shd);
+            if (tid == 0) neumaier(s, c, r * a.zw[g]);
+        } else {
+            Acc r = block_reduce(acc_merge(zacc[g], zacc2[g]), sh);
+            if (tid == 0) {
+                df d = df_norm(r.s, r.e);
+                neumaier(s, c, df2d(d.h, d.l) * a.zw[g]);
+            }
         }
     }
 #pragma unroll
     for (int k = 0; k < kXT; ++k) {
         if (k >= a.nxt) break;
-        Acc r = block_reduce(xacc[k], sh);
-        if (tid == 0) {
-            df d = df_norm(r.s, r.e);
-            neumaier(s, c, df2d(d.h, d.l) * a.xw[k]);
+        if constexpr (NAT) {
+            const double r = block_reduce_d(xacc[k].s, shd);
+            if (tid == 0) neumaier(s, c, r * a.xw[k]);
+        } else {
+            Acc r = block_reduce(xacc[k], sh);
+            if (tid == 0) {
+                df d = df_norm(r.s, r.e);
+                neumaier(s, c, df2d(d.h, d.l) * a.xw[k]);
+            }
         }
     }
     if (tid == 0) a.partial[blockIdx.x] = make_double2(s, c);
@@ -414,10 +471,19 @@ __global__ void __launch_bounds__(kRThreads) k_probs_partial_f64(const __grid_co
     for (int j = 0; j < a.m; ++j) dep |= ((bin >> j) & 1ull) << a.q[j];
     const uint64_t t0 = ch * a.chunk_len;
     const uint64_t t1 = min(a.per_bin, t0 + a.chunk_len);
+    // two FP64 accumulators a thread (products by fused multiply-add); the
+    // block's warp sums are combined with Neumaier's compensation
     double s = 0.0, c = 0.0;
-    for (uint64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+    uint64_t t = t0 + threadIdx.x;
+    for (; t + blockDim.x < t1; t += 2 * (uint64_t)blockDim.x) {
         const double2 v = a.x[insert_zero_bits(t, a.q_sorted, a.m) | dep];
-        neumaier(s, c, v.x * v.x + v.y * v.y);
+        const double2 u = a.x[insert_zero_bits(t + blockDim.x, a.q_sorted, a.m) | dep];
+        s = __fma_rn(v.x, v.x, __fma_rn(v.y, v.y, s));
+        c = __fma_rn(u.x, u.x, __fma_rn(u.y, u.y, c));
+    }
+    if (t < t1) {
+        const double2 v = a.x[insert_zero_bits(t, a.q_sorted, a.m) | dep];
+        s = __fma_rn(v.x, v.x, __fma_rn(v.y, v.y, s));
     }
     s += c;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
@@ -458,7 +524,7 @@ void probs_impl(qe_state* s, int m, const int* qubits, double* host_out) {
     if (nblocks > 0x7FFFFFFFull) fail(QE_ERR_UNSUPPORTED, "too many probability blocks");
     {
         Launch L(s, "probs_partial", (double)dim(s) * amp_bytes(s));
-        if (std::is_same<S, double2>::value && s->c128_native)
+        if (std::is_same<S, double2>::value && c128_f64(s))
             k_probs_partial_f64<<<(unsigned)nblocks, kRThreads, 0, s->stream>>>(
                 *reinterpret_cast<ProbArgs<double2>*>(&a));
         else
@@ -488,40 +554,58 @@ struct WideArgs {
     double2* partial;
 };
 
-template <class S>
+template <class S, bool NAT>
 __global__ void __launch_bounds__(kRThreads) k_expect_wide(const __grid_constant__ WideArgs<S> a) {
+    using A = std::conditional_t<NAT, AccD, Acc>;
     __shared__ Acc sh[32];
-    Acc acc[kXT];
+    __shared__ double shd[32];
+    A acc[kXT];
 #pragma unroll
-    for (int t = 0; t < kXT; ++t) acc[t] = Acc{0.f, 0.f};
+    for (int t = 0; t < kXT; ++t) acc_zero(acc[t]);
     for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < a.count;
          x += (uint64_t)gridDim.x * blockDim.x) {
-        const auto v = rview(a.x[x]);
+        const S raw = a.x[x];
 #pragma unroll
         for (int t = 0; t < kXT; ++t) {
             if (t >= a.nt) break;
             const uint64_t xm = a.xm[t];
             if (x & (xm & (~xm + 1ull))) continue;
-            float h, l;
-            corr(rview(a.x[x ^ xm]), v, a.ny[t], h, l);
-            if (__popcll(x & a.zm[t]) & 1) { h = -h; l = -l; }
-            acc_add(acc[t], 2.f * h, 2.f * l);
+            const bool neg = (__popcll(x & a.zm[t]) & 1) != 0;
+            if constexpr (NAT) {
+                // Re(conj(w) v i^ny), as in corr()
+                const S w = a.x[x ^ xm];
+                const int ny = a.ny[t];
+                double h = ((ny & 1) == 0) ? __fma_rn(w.x, raw.x, __dmul_rn(w.y, raw.y))
+                                           : __fma_rn(w.x, raw.y, -__dmul_rn(w.y, raw.x));
+                if ((ny == 1 || ny == 2) != neg) h = -h;
+                acc[t].s = __fma_rn(2.0, h, acc[t].s);
+            } else {
+                float h, l;
+                corr(rview(a.x[x ^ xm]), rview(raw), a.ny[t], h, l);
+                if (neg) { h = -h; l = -l; }
+                acc_add(acc[t], 2.f * h, 2.f * l);
+            }
         }
     }
     double s = 0.0, c = 0.0;
 #pragma unroll
     for (int t = 0; t < kXT; ++t) {
         if (t >= a.nt) break;
-        Acc r = block_reduce(acc[t], sh);
-        if (threadIdx.x == 0) {
-            df d = df_norm(r.s, r.e);
-            neumaier(s, c, df2d(d.h, d.l) * a.w[t]);
+        if constexpr (NAT) {
+            const double r = block_reduce_d(acc[t].s, shd);
+            if (threadIdx.x == 0) neumaier(s, c, r * a.w[t]);
+        } else {
+            Acc r = block_reduce(acc[t], sh);
+            if (threadIdx.x == 0) {
+                df d = df_norm(r.s, r.e);
+                neumaier(s, c, df2d(d.h, d.l) * a.w[t]);
+            }
         }
     }
     if (threadIdx.x == 0) a.partial[blockIdx.x] = make_double2(s, c);
 }
 
-template <class S>
+template <class S, bool NAT>
 double expect_impl(qe_state* s, int nterms, const uint64_t* xm, const uint64_t* zm, const double* cf) {
     const int n = s->n;
     const int Tmax = std::min(n, sizeof(S) >= 16 ? 11 : 12);
@@ -582,9 +666,9 @@ double expect_impl(qe_state* s, int nterms, const uint64_t* xm, const uint64_t* 
     static thread_local ExpArgs<S> a;
     a.x = reinterpret_cast<const S*>(s->d);
     const size_t smem = 2 * (sizeof(decltype(rview(S{}))) << Tmax);   // two tiles
-    QE_CUDA(cudaFuncSetAttribute(k_expect_tile<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    QE_CUDA(cudaFuncSetAttribute(k_expect_tile<S, NAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
-    QE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_expect_tile<S>, kRThreads, smem));
+    QE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_expect_tile<S, NAT>, kRThreads, smem));
     // count launches first to size the scratch
     struct Plan { int layout; std::vector<std::pair<int, std::vector<int>>> z; std::vector<int> x; };
     std::vector<Plan> plans;
@@ -641,7 +725,7 @@ double expect_impl(qe_state* s, int nterms, const uint64_t* xm, const uint64_t* 
         QE_CUDA(cudaMemsetAsync(b.partial, 0, max_grid * sizeof(double2), s->stream));
         const unsigned g = (unsigned)std::min<uint64_t>((dim(s) + kRThreads - 1) / kRThreads, max_grid);
         Launch Lw(s, "expect_wide", (double)dim(s) * amp_bytes(s));
-        k_expect_wide<S><<<g, kRThreads, 0, s->stream>>>(b);
+        k_expect_wide<S, NAT><<<g, kRThreads, 0, s->stream>>>(b);
         QE_CUDA(cudaGetLastError());
     }
     for (size_t i = 0; i < plans.size(); ++i) {
@@ -697,7 +781,7 @@ double expect_impl(qe_state* s, int nterms, const uint64_t* xm, const uint64_t* 
         // unused partial slots of this launch read as zero
         QE_CUDA(cudaMemsetAsync(a.partial, 0, max_grid * sizeof(double2), s->stream));
         Launch Lz(s, "expect_tile", (double)dim(s) * amp_bytes(s));
-        k_expect_tile<S><<<grids[i], kRThreads, smem, s->stream>>>(a);
+        k_expect_tile<S, NAT><<<grids[i], kRThreads, smem, s->stream>>>(a);
         QE_CUDA(cudaGetLastError());
     }
     {
@@ -728,8 +812,11 @@ void reduce_probs(qe_state* s, int m, const int* qubits, double* out) {
 double reduce_expectation(qe_state* s, int nterms, const uint64_t* xm, const uint64_t* zm,
                           const double* cf) {
     if (nterms == 0) return 0.0;
-    if (s->dtype == QE_C128) return expect_impl<double2>(s, nterms, xm, zm, cf);
-    return expect_impl<float2>(s, nterms, xm, zm, cf);
+    if (s->dtype == QE_C128) {
+        if (c128_f64(s)) return expect_impl<double2, true>(s, nterms, xm, zm, cf);
+        return expect_impl<double2, false>(s, nterms, xm, zm, cf);
+    }
+    return expect_impl<float2, false>(s, nterms, xm, zm, cf);
 }
 
 }  // namespace qe

@@ -10,32 +10,46 @@
 // and the block is W = [[Re U, -Im U], [Im U, Re U]], so a tile of 128 groups
 // is the product Out(128x64) = In(128x64) W^T.
 //
-// Splitting.  Row r of In (one group) is scaled by 2^(48 - E_r), where
-// 2^(E_r - 1) bounds its largest magnitude, and every value becomes the
-// integer X = round(|v| 2^(48 - E_r)) <= 2^47, written in base 256 with
-// balanced digits: X = sum_i a_i 256^(6 - i), a_1 in [0, 128], a_2..a_6 in
-// [-128, 127]; the value's sign multiplies every digit.  W's rows get scales
-// 2^F_n and digits b_j the same way on the host.  Every digit is an integer
-// of magnitude <= 128 and exact in FP16.
+// Two widths share the kernel, D = 7 digits (56-bit splitting, the FP64 mode)
+// and D = 6 (48-bit splitting, the fast double-float mode).
 //
-// Products.  C_d = sum_{i + j = d} A_i B_j^T for d = 2..8 (26 digit pairs;
-// the dropped pairs i + j >= 9 weigh below 2^-56 of the row scale), one FP32
-// tensor-memory accumulator per d.  One pair adds at most 64 * 128^2 = 2^20
-// in magnitude, so every accumulator is an exact integer below 2^23, and
-// those of d <= 5 (at most four pairs) lie in [-2^22, 2^22].
+// Splitting.  Row r of In (one group) is scaled by 2^(8D - E_r), where
+// 2^(E_r - 1) bounds its largest magnitude, and every value becomes the
+// integer X = round(|v| 2^(8D - E_r)) <= 2^(8D - 1), written in base 256 with
+// balanced digits: X = sum_i a_i 256^(D - i), a_1 in [0, 128], a_2..a_D in
+// [-128, 127]; the value's sign multiplies every digit.  Digit i thus weighs
+// 2^(E_r - 8 i) whatever D is.  W's rows get scales 2^F_n and digits b_j the
+// same way on the host.  Every digit is an integer of magnitude <= 128 and
+// exact in FP16.
+//
+// Products.  C_d = sum_{i + j = d} A_i B_j^T for d = 2..D+2 (26 digit pairs
+// for D = 6, 34 for D = 7), one FP32 tensor-memory accumulator per d; a pair
+// with i + j = d carries units of 2^(E_r + F_n - 8 d).  One pair adds at most
+// 64 * 128^2 = 2^20 units and no d has more than seven pairs, so every
+// accumulator is an exact integer below 2^23, and those of d <= 5 (at most
+// four pairs) lie in [-2^22, 2^22].
 //
 // Recombination (per output).  With the integer
-//   Y = C_2 2^40 + C_3 2^32 + C_4 2^24 + C_5 2^16 + C_6 2^8 + round(C_7 + C_8 / 256),
+//   Y = C_2 2^40 + C_3 2^32 + C_4 2^24 + C_5 2^16 + C_6 2^8
+//       + round(C_7 + C_8 / 256 [+ C_9 / 65536 for D = 7]),
 // |Y| < 2^61, the output is Y 2^(E_r + F_n - 56): one rounding of Y to a
 // double plus an exact exponent shift.  C_2..C_5 become integers with the
 // FP32 magic-number addition (C + 1.5 * 2^23 is exact for |C| <= 2^22 and its
 // bit pattern minus that of 1.5 * 2^23 is C); C_6 and the last term with a
 // float-to-integer conversion.
 //
-// Accuracy: the splitting rounds each input to 2^-48 of its row scale and each
-// matrix entry to 2^-48 of its row's; the result is within a few units of
-// 2^-48 of the group norm, with no FP64 arithmetic but the final conversion.
-// Rows whose largest magnitude is below 2^-920 are flushed to zero.
+// Accuracy.  The splitting rounds each input to a multiple of 2^(E_r - 8D)
+// and each matrix entry to one of 2^(F_n - 8D) (half a unit at most); the
+// digit products are exact, the dropped pairs (i + j > D + 2) add at most
+// 2^(E_r + F_n - 57.6) for D = 7 (2^(E_r + F_n - 50) for D = 6), and Y is
+// rounded once.  Over the 64 terms of an output the input rounding adds at
+// most 64 * 2^(E_r + F_n - 8D), so for D = 7 every output is within
+// 2^(E_r + F_n - 50) of the exact product: inside the worst-case rounding
+// error of an FP64 dot product of the same 64 terms (64 * 2^-53 * sum |v||w|,
+// up to 2^(E_r + F_n - 41)), with 56-bit inputs (2^-56 of the row scale) where
+// FP64 keeps 53 bits of each value.  D = 6 rounds inputs to 2^-48 of the row
+// scale (bound 2^(E_r + F_n - 42)).  Rows whose largest magnitude is below
+// 2^-920 are flushed to zero.
 //
 // Schedule (warp-specialised, one CTA per SM, persistent over tiles): eight
 // warps split (four threads per group row), eight warps recombine (two per
@@ -50,16 +64,17 @@
 // thus overlaps the recombination of tile t (whose int64 -> double
 // conversions run on the FP64 pipe), and a set is released to the MMAs as
 // soon as its accumulators are in registers.  The staging buffer holds the
-// raw amplitudes of a tile as two halves of 64 rows, each column-major; the
-// load warps refill a half with cp.async as soon as the splitters have read
-// it into registers (completion is signalled on the half's mbarrier), and
-// prefetch the next tile into L2 (one bulk prefetch per contiguous run).  The
-// splitters derive each row's largest exponent from the values they hold.
-// Every hand-off is an mbarrier (count-based arrivals by threads,
-// tcgen05.commit for MMA completion); waits suspend the thread until the
-// phase completes, have an iteration limit, and on a timeout raise a shared
-// abort flag that ends the waits of all other threads; the MMA warp waits for
-// its own MMAs before tensor memory is freed.
+// raw amplitudes of a tile's half (64 group rows, column-major): two such
+// buffers for D = 6, one for D = 7 (whose digit slices take the room of the
+// second); the load warps refill a buffer with cp.async as soon as the
+// splitters have read its half into registers (completion is signalled on the
+// half's mbarrier), and prefetch the next tile into L2 (one bulk prefetch per
+// contiguous run).  The splitters derive each row's largest exponent from the
+// values they hold.  Every hand-off is an mbarrier (count-based arrivals by
+// threads, tcgen05.commit for MMA completion); waits suspend the thread until
+// the phase completes, have an iteration limit, and on a timeout raise a
+// shared abort flag that ends the waits of all other threads; the MMA warp
+// waits for its own MMAs before tensor memory is freed.
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -85,15 +100,13 @@ constexpr int kRows = 128;                    // groups per tile (MMA M)
 constexpr int kK = 64;                        // real K
 constexpr int kN = 64;                        // real N (two halves of 32)
 constexpr int kNH = 32;                       // MMA N
-constexpr int kDigits = 6;
-constexpr int kAcc = 7;                       // accumulators for d = 2..8
-constexpr uint32_t kTmemCols = 512;           // two accumulator sets of 7 x 32 columns
+constexpr uint32_t kTmemCols = 512;           // two accumulator sets of (D + 1) x 32 columns
 constexpr uint32_t kSetY = 256;               // column of the second set
 constexpr uint32_t kSliceA = kRows * 128;     // bytes of one digit slice of In (fp16, 128 B per row)
 constexpr uint32_t kSliceB = kN * 128;        // bytes of one digit slice of W
 constexpr int kHalfRows = kRows / 2;          // the staging buffer holds the two halves of a tile's rows,
 constexpr uint32_t kHalfStage = kHalfRows * 32 * 16;   // each column-major: amplitude (row, column c) at 16 (64 c + row)
-constexpr uint32_t kStackB = kDigits * kNH * 128; // bytes of one half's stack of the six W' digit slices
+constexpr uint32_t kStackSlice = kNH * 128;   // bytes of one W' digit slice of one half (stacked along N)
 constexpr int kFlushExp = 100;                // biased exponent below which a row is flushed
 
 struct OzArgs {
@@ -104,7 +117,7 @@ struct OzArgs {
     uint8_t gpos[5];
     uint32_t* status;
     long long spin_limit;
-    const uint16_t* B;      // [6][64][64] fp16 digits of W': slice j, row n', column k
+    const uint16_t* B;      // [D][64][64] fp16 digits of W': slice j, row n', column k
     const int* F;           // [64] row scale exponents of W (original row order)
     int stall_test;         // failure-path test: the first staged half is never announced
 };
@@ -175,24 +188,34 @@ __device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
 }
 
 
-// The balanced-offset integer Z = X + 0x8080808080 of v (as two words) for a
-// row whose shift base is base_s = (largest biased exponent of the row) + 5:
-// q = M53 >> (base_s - e), X = (q + 1) >> 1, with the shift done as clamped
-// 32-bit shifts (a shift of 64 or more, which includes zero and subnormal v
-// with e = 0, gives q = 0); and the high word of v (its sign).
+// The balanced-offset integer Z of v (as two words) for a row whose largest
+// biased exponent is em: X = round(|v| 2^(8D - E_r)) = round(M53 2^(e - em + 8D - 54))
+// and Z = X + 0x80...80 (D - 1 bytes of 0x80, which makes the lower digits
+// balanced).  With q = (M53 << c) >> (base_s - e), c = 3 for D = 7 (M53 << 3
+// fits 56 bits) and c = 0 for D = 6, X = (q + 1) >> 1; the shift base is
+// base_s = em + 53 + c - 8D (em for D = 7, em + 5 for D = 6), and the shift is
+// done as clamped 32-bit shifts (64 or more, which includes zero and subnormal
+// v with e = 0, gives q = 0).  Also returns the high word of v (its sign).
 struct Zw {
     uint32_t zl, zh, hi;
 };
+template <int D>
 __device__ __forceinline__ Zw split_z(double v, uint32_t base_s) {
+    static_assert(D == 6 || D == 7, "6 or 7 digits");
     const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
-    const uint32_t s = base_s - ((hi << 1) >> 21);                // >= 5
+    const uint32_t s = base_s - ((hi << 1) >> 21);
     const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;
+    // (H, L): M53 << c as two words
+    const uint32_t H = (D == 7) ? __funnelshift_l(lo, mh, 3) : mh;
+    const uint32_t L = (D == 7) ? (lo << 3) : lo;
     uint32_t t, qh, ql;
-    asm("shf.r.clamp.b32 %0, %1, %2, %3;" : "=r"(t) : "r"(lo), "r"(mh), "r"(s));   // low word of M53 >> min(s, 32)
-    asm("shr.b32 %0, %1, %2;" : "=r"(qh) : "r"(mh), "r"(s));                         // 0 for s >= 32
+    asm("shf.r.clamp.b32 %0, %1, %2, %3;" : "=r"(t) : "r"(L), "r"(H), "r"(s));    // low word of (H:L) >> min(s, 32)
+    asm("shr.b32 %0, %1, %2;" : "=r"(qh) : "r"(H), "r"(s));                         // 0 for s >= 32
     const uint32_t s2 = (uint32_t)max((int)s - 32, 0);
-    asm("shr.b32 %0, %1, %2;" : "=r"(ql) : "r"(t), "r"(s2));                         // s >= 32: mh >> (s - 32)
-    const uint64_t Z = ((((uint64_t)qh << 32) | ql) + 0x10101010101ull) >> 1;
+    asm("shr.b32 %0, %1, %2;" : "=r"(ql) : "r"(t), "r"(s2));                         // s >= 32: H >> (s - 32)
+    // + 1 rounds, + 2 * 0x80...80 balances (both before the halving)
+    constexpr uint64_t kOff = (D == 7) ? 0x1010101010101ull : 0x10101010101ull;
+    const uint64_t Z = ((((uint64_t)qh << 32) | ql) + kOff) >> 1;
     return Zw{(uint32_t)Z, (uint32_t)(Z >> 32), hi};
 }
 
@@ -203,14 +226,16 @@ __device__ __forceinline__ uint32_t hadd2(uint32_t a, uint32_t b) {
     return d;
 }
 
-// The six signed digits of two values a, b as packed fp16 pairs (a in the
-// low half).  The bytes of the two Z are first interleaved (a0 b0 a1 b1 ...);
-// one byte permute against the constant with bytes 0x64 | sign << 7 then
-// makes each pair of bytes the fp16 numbers sign * (1024 + byte), and one
-// f16x2 addition of -sign * 1152 (-sign * 1024 for the leading digit) gives
-// sign * (byte - 128) (sign * byte) exactly.  Digit 0 is byte 1 of zh, digit 1
-// byte 0 of zh, digits 2..5 bytes 3..0 of zl.
-__device__ __forceinline__ void digit_pairs(const Zw& A, const Zw& B, uint32_t w[kDigits]) {
+// The D signed digits of two values a, b as packed fp16 pairs (a in the low
+// half).  The bytes of the two Z are first interleaved (a0 b0 a1 b1 ...); one
+// byte permute against the constant with bytes 0x64 | sign << 7 then makes
+// each pair of bytes the fp16 numbers sign * (1024 + byte), and one f16x2
+// addition of -sign * 1152 (-sign * 1024 for the leading digit) gives
+// sign * (byte - 128) (sign * byte) exactly.  The leading digit is byte D - 1
+// of Z; digits 1 .. D - 1 are bytes D - 2 .. 0 (zh holds bytes 4 and up, zl
+// bytes 0..3).
+template <int D>
+__device__ __forceinline__ void digit_pairs(const Zw& A, const Zw& B, uint32_t w[D]) {
     const uint32_t sg = __byte_perm(A.hi, B.hi, 0x7030u) & 0x80008000u;   // the signs at bits 15 and 31
     const uint32_t hs = 0x64006400u | sg;                         // bytes 1, 3: 0x64 | sign
     const uint32_t c0 = 0x64006400u | (sg ^ 0x80008000u);         // -sign * 1024
@@ -218,23 +243,36 @@ __device__ __forceinline__ void digit_pairs(const Zw& A, const Zw& B, uint32_t w
     const uint32_t ph = __byte_perm(A.zh, B.zh, 0x5140u);         // a0 b0 a1 b1 of zh
     const uint32_t p01 = __byte_perm(A.zl, B.zl, 0x5140u);        // a0 b0 a1 b1 of zl
     const uint32_t p23 = __byte_perm(A.zl, B.zl, 0x7362u);        // a2 b2 a3 b3 of zl
-    w[0] = hadd2(__byte_perm(ph, hs, 0x7352u), c0);
-    w[1] = hadd2(__byte_perm(ph, hs, 0x7150u), c1);
-    w[2] = hadd2(__byte_perm(p23, hs, 0x7352u), c1);
-    w[3] = hadd2(__byte_perm(p23, hs, 0x7150u), c1);
-    w[4] = hadd2(__byte_perm(p01, hs, 0x7352u), c1);
-    w[5] = hadd2(__byte_perm(p01, hs, 0x7150u), c1);
+    if (D == 7) {
+        const uint32_t ph2 = __byte_perm(A.zh, B.zh, 0x7362u);    // a2 b2 a3 b3 of zh
+        w[0] = hadd2(__byte_perm(ph2, hs, 0x7150u), c0);          // Z byte 6
+        w[1] = hadd2(__byte_perm(ph, hs, 0x7352u), c1);           // Z byte 5
+        w[2] = hadd2(__byte_perm(ph, hs, 0x7150u), c1);           // Z byte 4
+    } else {
+        w[0] = hadd2(__byte_perm(ph, hs, 0x7352u), c0);           // Z byte 5
+        w[1] = hadd2(__byte_perm(ph, hs, 0x7150u), c1);           // Z byte 4
+    }
+    w[D - 4] = hadd2(__byte_perm(p23, hs, 0x7352u), c1);          // Z byte 3
+    w[D - 3] = hadd2(__byte_perm(p23, hs, 0x7150u), c1);          // Z byte 2
+    w[D - 2] = hadd2(__byte_perm(p01, hs, 0x7352u), c1);          // Z byte 1
+    w[D - 1] = hadd2(__byte_perm(p01, hs, 0x7150u), c1);          // Z byte 0
 }
 
-// The integer Y of one output from its seven accumulators (raw FP32 bits).
-__device__ __forceinline__ long long combine_y(const uint32_t c[kAcc]) {
+// The integer Y of one output from its D + 1 accumulators C_2 .. C_{D+2}
+// (raw FP32 bits).
+template <int D>
+__device__ __forceinline__ long long combine_y(const uint32_t c[D + 1]) {
     const float M = 12582912.0f;   // 1.5 * 2^23; bits 0x4B400000
     const uint32_t u2 = __float_as_uint(__fadd_rn(__uint_as_float(c[0]), M));
     const uint32_t u3 = __float_as_uint(__fadd_rn(__uint_as_float(c[1]), M));
     const uint32_t u4 = __float_as_uint(__fadd_rn(__uint_as_float(c[2]), M));
     const uint32_t u5 = __float_as_uint(__fadd_rn(__uint_as_float(c[3]), M));
     const int c6 = __float2int_rn(__uint_as_float(c[4]));
-    const int c78 = __float2int_rn(__fmaf_rn(__uint_as_float(c[6]), 0.00390625f, __uint_as_float(c[5])));
+    // round(C_7 + C_8 / 256 [+ C_9 / 65536]): each FP32 step rounds below a
+    // quarter unit (|C_7 + ...| < 2^23)
+    float low = __fmaf_rn(__uint_as_float(c[6]), 0.00390625f, __uint_as_float(c[5]));
+    if (D == 7) low = __fmaf_rn(__uint_as_float(c[D]), 1.52587890625e-5f, low);
+    const int c78 = __float2int_rn(low);
     // u4 2^24 + u5 2^16 carry the offsets 0x4B400000 (2^24 + 2^16) = 0x4B8B40 2^32,
     // taken off H: H = C_2 256 + C_3 - 0x4B8B40 (mod 2^32), and Y is exact mod 2^64
     const int H = (int)(u2 * 256u + u3 - (257u * 0x4B400000u + 0x4B8B40u));
@@ -269,22 +307,38 @@ enum Bar {
     kBars
 };
 
+// (i, j0, j1) of the MMAs of one K-step and half, in issue order: (1,1) and
+// (2,1..D) start the sums C_2 .. C_{D+2}, then (1,2..D) and (i,1..D+2-i) for
+// i = 3..D add to them.
+template <int D>
+struct MmaTable {
+    int i[D + 1], j0[D + 1], j1[D + 1];
+    constexpr MmaTable() : i(), j0(), j1() {
+        i[0] = 1; j0[0] = 1; j1[0] = 1;
+        i[1] = 2; j0[1] = 1; j1[1] = D;
+        i[2] = 1; j0[2] = 2; j1[2] = D;
+        for (int m = 3; m <= D; ++m) {
+            i[m] = m;
+            j0[m] = 1;
+            j1[m] = D + 2 - m;
+        }
+    }
+};
+
 // The MMA-issuing thread.  The accumulators of one half lie side by side,
 // C_d at column 32 (d - 2), and each half's W' digit slices are stacked along
 // N (rows 32 (j - 1) + m), so one MMA of A_i against the stacked slices
 // j0..j1 writes C_{i + j0} .. C_{i + j1} at once: the digit products form a
-// convolution.  Per K-step and half: (1,1) and (2,1..6) start the sums, then
-// (1,2..6), (3,1..5), (4,1..4), (5,1..3), (6,1..2) add to them (26 pairs in 7
-// MMAs).  Per tile: both halves' K-steps over the real parts (each half once
+// convolution (D = 6: 26 pairs in 7 MMAs per K-step and half; D = 7: 34 in
+// 8).  Per tile: both halves' K-steps over the real parts (each half once
 // its set is free), a commit that releases the real-part digits, then the
 // imaginary-part K-steps of X (committed: X full) and of Y (committed: Y
 // full and every digit consumed).  False when a wait ran out.
+template <int D>
 __device__ __noinline__ bool issue_mmas(const OzArgs& a, uint32_t tmem, uint32_t a0, uint32_t b0, uint64_t* bars,
                                         uint32_t* abort_flag) {
-    // (i, j0, j1) in issue order
-    constexpr int kI[7] = {1, 2, 1, 3, 4, 5, 6};
-    constexpr int kJ0[7] = {1, 1, 2, 1, 1, 1, 1};
-    constexpr int kJ1[7] = {1, 6, 6, 5, 4, 3, 2};
+    constexpr MmaTable<D> tab;
+    constexpr uint32_t kStackB = (uint32_t)D * kStackSlice;
     const uint64_t da0 = tc::sdesc_sw128(a0);      // an offset of b bytes adds b >> 4
     auto issue = [&](int hh, int ks0, int ks1) {
         const uint32_t set = tmem + (hh ? kSetY : 0u);
@@ -293,11 +347,11 @@ __device__ __noinline__ bool issue_mmas(const OzArgs& a, uint32_t tmem, uint32_t
         for (int ks = 0; ks < kK / 16; ++ks) {
             if (ks < ks0 || ks >= ks1) continue;
 #pragma unroll
-            for (int m = 0; m < 7; ++m) {
-                const int i = kI[m], j0 = kJ0[m], j1 = kJ1[m];
+            for (int m = 0; m <= D; ++m) {
+                const int i = tab.i[m], j0 = tab.j0[m], j1 = tab.j1[m];
                 const uint32_t nn = (uint32_t)(j1 - j0 + 1) * kNH;
                 const uint64_t da = da0 + (((uint32_t)(i - 1) * kSliceA + 32u * ks) >> 4);
-                const uint64_t db = db0 + (((uint32_t)(j0 - 1) * (kNH * 128u) + 32u * ks) >> 4);
+                const uint64_t db = db0 + (((uint32_t)(j0 - 1) * kStackSlice + 32u * ks) >> 4);
                 const uint32_t dt = set + (uint32_t)(i + j0 - 2) * kNH;
                 mma_f16(dt, da, db, tc::idesc(0u, nn, kRows), (ks > 0 || m > 1) ? 1u : 0u);
             }
@@ -328,12 +382,26 @@ __device__ __noinline__ bool issue_mmas(const OzArgs& a, uint32_t tmem, uint32_t
     return true;
 }
 
+// Dynamic shared memory: D digit slices of In, D of W' (two stacked halves),
+// and two staging buffers (D = 6) or one (D = 7), plus 1 KB of alignment.
+template <int D>
+constexpr size_t oz_smem() {
+    return 1024 + (size_t)D * (kSliceA + kSliceB) + (D == 7 ? 1 : 2) * (size_t)kHalfStage;
+}
+static_assert(oz_smem<6>() <= 227 * 1024 && oz_smem<7>() <= 227 * 1024, "shared memory per CTA");
+
+// 19 warps of 96 registers a thread: a sub-partition holding five of the warps
+// uses 15,360 of its 16,384 registers (104 would exceed them).
+template <int D>
 __global__ void __maxnreg__(96) k_gate_tc5_c128(const __grid_constant__ OzArgs a) {
+    constexpr int kAcc = D + 1;                  // accumulators C_2 .. C_{D+2}
+    constexpr bool kOneStage = D == 7;           // one staging buffer for both halves of a tile
+    constexpr uint32_t kStackB = (uint32_t)D * kStackSlice;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    unsigned char* sA = base;                                   // 6 digit slices of In
-    unsigned char* sB = sA + kDigits * kSliceA;                 // per half: the 6 W' digit slices stacked
-    unsigned char* stage = sB + kDigits * kSliceB;              // raw amplitudes of one tile
+    unsigned char* sA = base;                                   // D digit slices of In
+    unsigned char* sB = sA + D * kSliceA;                       // per half: the D W' digit slices stacked
+    unsigned char* stage = sB + D * kSliceB;                    // raw amplitudes of one or two tile halves
     __shared__ __align__(8) uint64_t bars[kBars];
     __shared__ uint32_t tmem_base, abort_flag;
     __shared__ uint64_t hoff[32];
@@ -345,7 +413,7 @@ __global__ void __maxnreg__(96) k_gate_tc5_c128(const __grid_constant__ OzArgs a
 
     // W' digits into their swizzled operand layout; W row scales
 #pragma unroll 1
-    for (int i = tid; i < kDigits * kN * 8; i += blockDim.x) {
+    for (int i = tid; i < D * kN * 8; i += blockDim.x) {
         const int j = i / (kN * 8), n = (i / 8) % kN, ch = i % 8;
         const uint4 v = *reinterpret_cast<const uint4*>(a.B + ((size_t)(j * kN + n) * kK + ch * 8));
         const int hh = n / kNH, m = n % kNH;
@@ -418,7 +486,7 @@ __global__ void __maxnreg__(96) k_gate_tc5_c128(const __grid_constant__ OzArgs a
     if (warp == kMmaWarp) {
         // ---------------------------------------------------- MMA issuer
         if (lane == 0) {
-            if (!issue_mmas(a, tmem, smem_u32(sA), smem_u32(sB), bars, &abort_flag)) atomicExch(a.status, 1u);
+            if (!issue_mmas<D>(a, tmem, smem_u32(sA), smem_u32(sB), bars, &abort_flag)) atomicExch(a.status, 1u);
             // every MMA issued has completed before tensor memory is freed
             tc::mma_commit(&bars[kDrain]);
             if (!tc::mbar_wait(smem_u32(&bars[kDrain]), 0u, a.spin_limit)) atomicExch(a.status, 1u);
@@ -439,12 +507,16 @@ __global__ void __maxnreg__(96) k_gate_tc5_c128(const __grid_constant__ OzArgs a
             const char* g = tile_ptr(t);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                if (!first && !wait(h ? kStageFree1 : kStageFree0, pf[h])) {
+                // the buffer's previous half must have been read: with two
+                // buffers the same half of the previous tile, with one the
+                // other half (of this tile for h = 1, of the previous for h = 0)
+                const int fh = kOneStage ? 1 - h : h;
+                if (!(first && (h == 0 || !kOneStage)) && !wait(fh ? kStageFree1 : kStageFree0, pf[fh])) {
                     ok = false;
                     break;
                 }
                 const char* gr = g + ro[h];
-                const uint32_t dh = d + (uint32_t)h * kHalfStage;
+                const uint32_t dh = d + (kOneStage ? 0u : (uint32_t)h * kHalfStage);
 #pragma unroll 8
                 for (int c = 0; c < 32; ++c) cp_async16(dh + 16u * kHalfRows * c, gr + coloff[c]);
                 if (!(a.stall_test && first && h == 0)) cp_async_arrive(&bars[h ? kStage1 : kStage0]);
@@ -484,7 +556,8 @@ __global__ void __maxnreg__(96) k_gate_tc5_c128(const __grid_constant__ OzArgs a
                 }
                 const int r = kHalfRows * h + ri;
                 double2 v[8];
-                const double2* src = reinterpret_cast<const double2*>(srow + (uint32_t)h * kHalfStage);
+                const double2* src =
+                    reinterpret_cast<const double2*>(srow + (kOneStage ? 0u : (uint32_t)h * kHalfStage));
 #pragma unroll
                 for (int k = 0; k < 8; ++k) v[k] = src[kHalfRows * k];
                 mbar_arrive(&bars[h ? kStageFree1 : kStageFree0]);
@@ -495,17 +568,18 @@ __global__ void __maxnreg__(96) k_gate_tc5_c128(const __grid_constant__ OzArgs a
                 em = max(em, __shfl_xor_sync(0xFFFFFFFFu, em, 8));
                 em = max(em, __shfl_xor_sync(0xFFFFFFFFu, em, 16));
                 em >>= 21;
-                const uint32_t base_s = (em < (uint32_t)kFlushExp) ? 0x10000u : em + 5u;
+                const uint32_t base_s = (em < (uint32_t)kFlushExp) ? 0x10000u : (D == 7 ? em : em + 5u);
 #pragma unroll
                 for (int part = 0; part < 2; ++part) {
-                    uint32_t w[kDigits][4];      // packed fp16 pairs: slice i, values 2p, 2p + 1
+                    uint32_t w[D][4];            // packed fp16 pairs: slice i, values 2p, 2p + 1
 #pragma unroll
                     for (int p2 = 0; p2 < 4; ++p2) {
                         const double2 va = v[2 * p2], vb = v[2 * p2 + 1];
-                        uint32_t dg[kDigits];
-                        digit_pairs(split_z(part ? va.y : va.x, base_s), split_z(part ? vb.y : vb.x, base_s), dg);
+                        uint32_t dg[D];
+                        digit_pairs<D>(split_z<D>(part ? va.y : va.x, base_s), split_z<D>(part ? vb.y : vb.x, base_s),
+                                       dg);
 #pragma unroll
-                        for (int k = 0; k < kDigits; ++k) w[k][p2] = dg[k];
+                        for (int k = 0; k < D; ++k) w[k][p2] = dg[k];
                     }
                     // the previous tile's MMAs over this part are done
                     if (h == 0 && !first && !(part ? wait(kYFull, pyf) : wait(kReFree, prf))) {
@@ -514,7 +588,7 @@ __global__ void __maxnreg__(96) k_gate_tc5_c128(const __grid_constant__ OzArgs a
                     }
                     const uint32_t off = sw128_chunk(r, part * 4 + qq);
 #pragma unroll
-                    for (int k = 0; k < kDigits; ++k)
+                    for (int k = 0; k < D; ++k)
                         *reinterpret_cast<uint4*>(sA + k * kSliceA + off) = make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]);
                     if (part == 0 && qq == 0) {
                         // the row scale, for the recombination of this tile
@@ -544,6 +618,34 @@ __global__ void __maxnreg__(96) k_gate_tc5_c128(const __grid_constant__ OzArgs a
         // the accumulators of 4 complex columns m0 .. m0 + 3 of set hh as
         // the integers Y (re, im interleaved)
         auto load_y = [&](uint32_t set, int m0, long long y[8], Bar release) {
+            if constexpr (D == 7) {
+                // real parts, then imaginary parts: half the live accumulator
+                // registers of loading both at once (eight accumulators)
+#pragma unroll
+                for (int part = 0; part < 2; ++part) {
+                    uint32_t cc[kAcc][4];
+#pragma unroll
+                    for (int k = 0; k < kAcc; ++k) {
+                        const uint32_t ta = set + (uint32_t)(k * kNH + m0 + 16 * part);
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                                     : "=r"(cc[k][0]), "=r"(cc[k][1]), "=r"(cc[k][2]), "=r"(cc[k][3])
+                                     : "r"(ta));
+                    }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;");
+                    if (part == 1 && release != kBars) {
+                        asm volatile("tcgen05.fence::before_thread_sync;");
+                        mbar_arrive(&bars[release]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        uint32_t c1[kAcc];
+#pragma unroll
+                        for (int k = 0; k < kAcc; ++k) c1[k] = cc[k][u];
+                        y[2 * u + part] = combine_y<D>(c1);
+                    }
+                }
+                return;
+            }
             uint32_t re[kAcc][4], im[kAcc][4];
 #pragma unroll
             for (int k = 0; k < kAcc; ++k) {
@@ -569,8 +671,8 @@ __global__ void __maxnreg__(96) k_gate_tc5_c128(const __grid_constant__ OzArgs a
                     cr[k] = re[k][u];
                     ci[k] = im[k][u];
                 }
-                y[2 * u] = combine_y(cr);
-                y[2 * u + 1] = combine_y(ci);
+                y[2 * u] = combine_y<D>(cr);
+                y[2 * u + 1] = combine_y<D>(ci);
             }
         };
         auto store = [&](char* gb, int c0, const long long y[8], int eterm) {
@@ -628,7 +730,8 @@ uint16_t fp16_bits(int d) {
 
 // Balanced base-256 digits of one row of W (host side, same rule as the
 // device splitting): returns the scale exponent F and fills digits[j][k].
-int split_row_host(const double* w, int16_t digits[kDigits][kK]) {
+template <int D>
+int split_row_host(const double* w, int16_t digits[D][kK]) {
     int emax = 0;
     for (int k = 0; k < kK; ++k) {
         uint64_t b;
@@ -636,24 +739,26 @@ int split_row_host(const double* w, int16_t digits[kDigits][kK]) {
         emax = std::max(emax, (int)((b >> 52) & 0x7FF));
     }
     if (emax < kFlushExp) {
-        std::memset(digits, 0, sizeof(int16_t) * kDigits * kK);
+        std::memset(digits, 0, sizeof(int16_t) * D * kK);
         return 0;
     }
     const int F = emax - 1021;
+    uint64_t off = 0;   // D - 1 bytes of 0x80
+    for (int j = 1; j < D; ++j) off = (off << 8) | 0x80u;
     for (int k = 0; k < kK; ++k) {
-        const uint64_t X = (uint64_t)std::llround(std::ldexp(std::fabs(w[k]), 48 - F));   // <= 2^47, exact scaling
-        const uint64_t Z = X + 0x8080808080ull;
+        // <= 2^(8D - 1), exact scaling, one rounding
+        const uint64_t X = (uint64_t)std::llround(std::ldexp(std::fabs(w[k]), 8 * D - F));
+        const uint64_t Z = X + off;
         const int sg = std::signbit(w[k]) ? -1 : 1;
-        digits[0][k] = (int16_t)(sg * (int)(Z >> 40));
-        for (int j = 1; j < kDigits; ++j) digits[j][k] = (int16_t)(sg * ((int)((Z >> (8 * (5 - j))) & 0xFF) - 128));
+        digits[0][k] = (int16_t)(sg * (int)(Z >> (8 * (D - 1))));
+        for (int j = 1; j < D; ++j)
+            digits[j][k] = (int16_t)(sg * ((int)((Z >> (8 * (D - 1 - j))) & 0xFF) - 128));
     }
     return F;
 }
 
-}  // namespace
-
-// Apply a 5-qubit block to a complex128 state with the tensor cores.
-void launch_gate_tc5_c128(qe_state* s, const int* qubits, const cd* U) {
+template <int D>
+void launch_impl(qe_state* s, const int* qubits, const cd* U, const char* tag) {
     if (s->dtype != QE_C128) fail(QE_ERR_UNSUPPORTED, "this tensor-core path is for complex128 states");
     if (s->n < 12) fail(QE_ERR_UNSUPPORTED, "tensor-core gates need n >= 12");
     const tc::Geometry g = tc::tile_geometry(qubits);
@@ -666,7 +771,7 @@ void launch_gate_tc5_c128(qe_state* s, const int* qubits, const cd* U) {
     a.ntiles = 1ull << (s->n - 12);
     // W = [[Re U, -Im U], [Im U, Re U]], row n (output), column k (input)
     struct HostW {
-        uint16_t B[kDigits * kN * kK];
+        uint16_t B[D * kN * kK];
         int F[kN];
     };
     static thread_local HostW hw;
@@ -676,12 +781,12 @@ void launch_gate_tc5_c128(qe_state* s, const int* qubits, const cd* U) {
             const cd u = U[(n & 31) * 32 + (k & 31)];
             w[k] = (n < 32) ? ((k < 32) ? u.real() : -u.imag()) : ((k < 32) ? u.imag() : u.real());
         }
-        int16_t dg[kDigits][kK];
-        hw.F[n] = split_row_host(w, dg);
+        int16_t dg[D][kK];
+        hw.F[n] = split_row_host<D>(w, dg);
         // operand row n' of W' (two halves of 32 rows, see the epilogue)
         const int c = n & 31, hh = c >> 4, m = (c & 15) + ((n >> 5) << 4);
         const int np = hh * kNH + m;
-        for (int j = 0; j < kDigits; ++j)
+        for (int j = 0; j < D; ++j)
             for (int k = 0; k < kK; ++k) {
                 hw.B[((size_t)j * kN + np) * kK + k] = fp16_bits(dg[j][k]);
             }
@@ -702,18 +807,28 @@ void launch_gate_tc5_c128(qe_state* s, const int* qubits, const cd* U) {
     const char* stall = std::getenv("QE_TEST_STALL_TC128");
     a.stall_test = (stall != nullptr && stall[0] == '1') ? 1 : 0;
     if (a.stall_test) a.spin_limit = 1ll << 12;
-    const size_t smem = 1024 + (size_t)kDigits * (kSliceA + kSliceB) + 2 * (size_t)kHalfStage;
-    QE_CUDA(cudaFuncSetAttribute(k_gate_tc5_c128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem = oz_smem<D>();
+    QE_CUDA(cudaFuncSetAttribute(k_gate_tc5_c128<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const uint64_t grid = std::min<uint64_t>(a.ntiles, (uint64_t)num_sms());
     {
-        Launch Lc(s, "gate_tc_k5_c128", 2.0 * dim(s) * amp_bytes(s));
-        k_gate_tc5_c128<<<(unsigned)grid, kOzThreads, smem, s->stream>>>(a);
+        Launch Lc(s, tag, 2.0 * dim(s) * amp_bytes(s));
+        k_gate_tc5_c128<D><<<(unsigned)grid, kOzThreads, smem, s->stream>>>(a);
         QE_CUDA(cudaGetLastError());
     }
     // checked before the next tensor-core launch or at the end of the flush,
     // so that the host plans the next block while this one runs
     QE_CUDA(cudaMemcpyAsync(status_word_host(s), status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s->stream));
     s->status_pending = true;
+}
+
+}  // namespace
+
+// Apply a 5-qubit block to a complex128 state with the tensor cores: 56-bit
+// splitting (seven digits) in the FP64 mode, 48-bit (six) in the fast
+// double-float mode.
+void launch_gate_tc5_c128(qe_state* s, const int* qubits, const cd* U) {
+    if (s->arith == QE_ARITH_DF64) launch_impl<6>(s, qubits, U, "gate_tc_k5_c128_df");
+    else launch_impl<7>(s, qubits, U, "gate_tc_k5_c128");
 }
 
 }  // namespace qe

@@ -18,6 +18,7 @@ _lib = None
 
 C64, C128 = 0, 1
 POLICY_AUTO, POLICY_ANALYTIC, POLICY_EMULATE, POLICY_SIMULATE = 0, 1, 2, 3
+ARITH_FP64, ARITH_DF64 = 0, 1
 
 STATUS = {0: "QE_OK", -1: "QE_ERR_ARG", -2: "QE_ERR_OOM", -3: "QE_ERR_CUDA",
           -4: "QE_ERR_TIMEOUT", -5: "QE_ERR_STATE", -6: "QE_ERR_UNSUPPORTED"}
@@ -55,6 +56,8 @@ SIGNATURES = {
     "qe_flush": (_i, [_vp]),
     "qe_sync": (_i, [_vp]),
     "qe_set_policy": (_i, [_vp, _i, _i]),
+    "qe_set_arith": (_i, [_vp, _i]),
+    "qe_get_arith": (_i, [_vp, C.POINTER(_i)]),
     "qe_get_stats": (_i, [_vp, C.POINTER(Stats)]),
     "qe_reset_stats": (_i, [_vp]),
     "qe_profile_enable": (_i, [_vp, _i]),
@@ -251,6 +254,16 @@ class State:
     def set_policy(self, policy=POLICY_AUTO, max_k=None):
         """max_k None (0): the library's default fusion width."""
         _check(load().qe_set_policy(self._h, int(policy), int(max_k or 0)))
+
+    def set_arith(self, arith):
+        """ARITH_FP64 (default for complex128) or ARITH_DF64 (the fast
+        double-float mode); see qe_set_arith."""
+        _check(load().qe_set_arith(self._h, int(arith)))
+
+    def arith(self):
+        a = C.c_int()
+        _check(load().qe_get_arith(self._h, C.byref(a)))
+        return a.value
 
     def set_cost_model(self, model):
         """Attach a CostModel (or None): QE_POLICY_AUTO then lets it choose."""

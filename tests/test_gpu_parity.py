@@ -3,8 +3,10 @@
 Every input comes from ``inputs`` (seeded); the oracle computes the expected
 values; the GPU result is compared element by element.
 
-Tolerances (complex128, double-float arithmetic on the FP32 pipes):
+Tolerances (complex128, FP64 mode and double-float mode alike):
   max |gpu - oracle| <= 1e-12 and fidelity >= 1 - 1e-10 (the FP64 bar);
+  the FP64 mode is also checked against extended-precision references at the
+  level of FP64 rounding (see the accuracy tests at the end);
   permutations (CNOT/MCX/SWAP, add-constant, bit reversal) are bit-exact.
 complex64: FP32 arithmetic, max-abs <= 2e-6 per operation sequence used here
 (about 2^-24 per gate times the few dozen gates of each test), stated per test.
@@ -41,10 +43,18 @@ def close(got, ref, tol=TOL, fid=FID):
     return err
 
 
-def make(qe, n, dtype="c128", psi=None, max_k=1, native=False, tile=False):
+# complex128 arithmetic: "fp64" (default: FP64 mode, dense blocks on the
+# tensor cores), "df64" (the double-float mode), "f64" (FP64 mode without
+# tensor cores: native FP64 kernels only)
+ARITHS = ["fp64", "df64", "f64"]
+
+
+def make(qe, n, dtype="c128", psi=None, max_k=1, native=False, tile=False, arith=None):
     import os
     if native:
-        os.environ["QE_C128_ARITH"] = "f64"
+        arith = "f64"
+    if arith and arith != "fp64":
+        os.environ["QE_C128_ARITH"] = arith
     if tile:
         os.environ["QE_DENSE_TILE"] = "1"
     try:
@@ -93,27 +103,29 @@ def test_init_random_c64(qe):
 
 
 # ------------------------------------------------------- single gates
-@pytest.mark.parametrize("native,tile", [(False, False), (True, False), (False, True)])
+@pytest.mark.parametrize("arith,tile", [("fp64", False), ("f64", False), ("df64", False), ("f64", True),
+                                        ("df64", True)])
 @pytest.mark.parametrize("q", [0, 1, 3, 4, 5, 9, 10, 13])
-def test_1q_dense_every_position(qe, q, native, tile):
+def test_1q_dense_every_position(qe, q, arith, tile):
     n = 14
     psi = I.random_state(n, q)
     U = I.haar_u2(np.random.default_rng(q))
-    with make(qe, n, psi=psi, native=native, tile=tile) as st:
+    with make(qe, n, psi=psi, arith=arith, tile=tile) as st:
         st.apply_gate([q], U)
         got = st.get()
     close(got, oracle.apply_gate(psi, [q], U))
 
 
+@pytest.mark.parametrize("arith", ARITHS)
 @pytest.mark.parametrize("tile", [False, True])
 @pytest.mark.parametrize("qubits", [[0, 1], [1, 0], [4, 11], [12, 2, 7], [0, 5, 10, 13],
                                     [3, 4, 5, 6, 7], [13, 0, 9, 1, 6], [10, 11, 12, 13]])
-def test_kq_dense(qe, qubits, tile):
+def test_kq_dense(qe, qubits, tile, arith):
     n = 14
     rng = np.random.default_rng(len(qubits) * 100 + qubits[0])
     U = rand_unitary(1 << len(qubits), rng)
     psi = I.random_state(n, 3)
-    with make(qe, n, psi=psi, max_k=5, tile=tile) as st:
+    with make(qe, n, psi=psi, max_k=5, tile=tile, arith=arith) as st:
         st.apply_gate(qubits, U)
         got = st.get()
     close(got, oracle.apply_gate(psi, qubits, U))
@@ -130,7 +142,8 @@ def test_kq_dense_small_state(qe):
     close(got, oracle.apply_gate(psi, [5, 0, 3], U))
 
 
-def test_structured_gates(qe):
+@pytest.mark.parametrize("arith", ARITHS)
+def test_structured_gates(qe, arith):
     n = 13
     psi = I.random_state(n, 8)
     ref = psi.copy()
@@ -138,7 +151,7 @@ def test_structured_gates(qe):
              I.single(7, I.mat_rz(0.4)), I.single(0, I.mat_t()), I.single(4, I.mat_s()),
              I.single(6, I.mat_x()), I.single(8, I.mat_y()), I.single(10, I.mat_z()),
              I.Gate((4, 9), np.eye(4)[[0, 2, 1, 3]].astype(complex), (), "swap")]
-    with make(qe, n, psi=psi) as st:
+    with make(qe, n, psi=psi, arith=arith) as st:
         for g in gates:
             st.apply(g)
             ref = oracle.apply_gate(ref, g.qubits, g.matrix)
@@ -163,12 +176,13 @@ def test_permutation_gates_bit_exact(qe):
     assert np.array_equal(got, ref)
 
 
+@pytest.mark.parametrize("arith", ["fp64", "df64"])
 @pytest.mark.parametrize("controls,targets", [([3], [0]), ([0, 9], [4]), ([2], [5, 11]), ([1, 4, 7], [0, 12])])
-def test_controlled_dense(qe, controls, targets):
+def test_controlled_dense(qe, controls, targets, arith):
     n = 13
     U = rand_unitary(1 << len(targets), np.random.default_rng(len(controls)))
     psi = I.random_state(n, 10)
-    with make(qe, n, psi=psi) as st:
+    with make(qe, n, psi=psi, arith=arith) as st:
         st.apply_controlled(controls, targets, U)
         got = st.get()
     close(got, oracle.apply_controlled(psi, controls, targets, U))
@@ -214,15 +228,16 @@ def test_fused_circuit_with_controlled_gates(qe, dtype):
         assert oracle.fidelity(ref, got) > 1 - 1e-8
 
 
+@pytest.mark.parametrize("arith", ["fp64", "df64"])
 @pytest.mark.parametrize("max_k,tile", [(1, False), (2, False), (3, False), (4, False), (5, False),
                                         (2, True)])
-def test_random_circuit_fused_vs_oracle(qe, max_k, tile):
+def test_random_circuit_fused_vs_oracle(qe, max_k, tile, arith):
     n = 14
     gates = I.random_circuit(n, 10, seed=11)
     ref = oracle.zero_state(n)
     for g in gates:
         ref = oracle.apply_gate(ref, g.qubits, g.matrix)
-    with make(qe, n, max_k=max_k, tile=tile) as st:
+    with make(qe, n, max_k=max_k, tile=tile, arith=arith) as st:
         for g in gates:
             st.apply(g)
         got = st.get()
@@ -259,11 +274,12 @@ def test_random_circuit_c64(qe):
 
 
 # ----------------------------------------------------------------- QFT
+@pytest.mark.parametrize("arith", ["fp64", "df64"])
 @pytest.mark.parametrize("n,lo,m", [(8, 0, 8), (10, 2, 5), (12, 0, 12), (14, 0, 14), (15, 1, 13), (13, 6, 7)])
 @pytest.mark.parametrize("inverse", [False, True])
-def test_qft_emulated_vs_dft(qe, n, lo, m, inverse):
+def test_qft_emulated_vs_dft(qe, n, lo, m, inverse, arith):
     psi = I.random_state(n, n + lo + m)
-    with make(qe, n, psi=psi) as st:
+    with make(qe, n, psi=psi, arith=arith) as st:
         st.set_policy(qe.POLICY_EMULATE, 1)
         st.apply_qft(lo, m, inverse)
         got = st.get()
@@ -292,10 +308,11 @@ def test_qft_basis_state_closed_form(qe):
     assert np.max(np.abs(got - want)) < 1e-15
 
 
-def test_qft_many_passes_sampled(qe):
+@pytest.mark.parametrize("arith", ["fp64", "df64"])
+def test_qft_many_passes_sampled(qe, arith):
     # 24 register qubits: three FFT passes plus the bit reversal
     n, lo, m = 25, 1, 24
-    with make(qe, n) as st:
+    with make(qe, n, arith=arith) as st:
         st.set_policy(qe.POLICY_EMULATE, 1)
         st.init_random(3)
         psi = st.get()
@@ -366,12 +383,12 @@ def test_add_const_c64_and_roundtrip(qe):
 
 
 # ----------------------------------------------- expectation and probs
-@pytest.mark.parametrize("dtype", ["c128", "c64"])
-def test_tfim_expectation(qe, dtype):
+@pytest.mark.parametrize("dtype,arith", [("c128", "fp64"), ("c128", "df64"), ("c64", None)])
+def test_tfim_expectation(qe, dtype, arith):
     n = 12
     psi = I.random_state(n, 21)
     xm, zm, cf = I.tfim_terms(n)
-    with make(qe, n, dtype, psi=psi) as st:
+    with make(qe, n, dtype, psi=psi, arith=arith) as st:
         e = st.expectation(xm, zm, cf)
     ref = oracle.expectation(psi, xm, zm, cf)
     assert abs(e - ref) < (1e-12 if dtype == "c128" else 1e-5)
@@ -387,20 +404,21 @@ def test_tfim_closed_forms(qe):
         assert abs(st.expectation(xm, zm, cf) - 0.7 * n) < 1e-12
 
 
-def test_general_pauli_terms(qe):
+@pytest.mark.parametrize("arith", ["fp64", "df64"])
+def test_general_pauli_terms(qe, arith):
     n = 10
     rng = np.random.default_rng(5)
     xm = rng.integers(0, 1 << n, size=13).astype(np.uint64)
     zm = rng.integers(0, 1 << n, size=13).astype(np.uint64)
     cf = rng.standard_normal(13)
     psi = I.random_state(n, 31)
-    with make(qe, n, psi=psi) as st:
+    with make(qe, n, psi=psi, arith=arith) as st:
         e = st.expectation(xm, zm, cf)
     assert abs(e - oracle.expectation(psi, xm, zm, cf)) < 1e-12
 
 
-@pytest.mark.parametrize("dtype,tol", [("c128", 1e-12), ("c64", 1e-5)])
-def test_expectation_parities_outside_the_tile(qe, dtype, tol):
+@pytest.mark.parametrize("dtype,tol,arith", [("c128", 1e-12, "fp64"), ("c128", 1e-12, "df64"), ("c64", 1e-5, None)])
+def test_expectation_parities_outside_the_tile(qe, dtype, tol, arith):
     # n = 16 > the 11/12-qubit tile: nearest-neighbour ZZ masks inside,
     # straddling and entirely outside the tile; Z strings on high qubits only;
     # X/Y terms whose Z parts lie inside, outside, or both
@@ -416,20 +434,21 @@ def test_expectation_parities_outside_the_tile(qe, dtype, tol):
         xm.append(1 << q); zm.append(0); cf.append(0.7)
     xm, zm, cf = (np.array(xm, dtype=np.uint64), np.array(zm, dtype=np.uint64), np.array(cf))
     psi = I.random_state(n, 44)
-    with make(qe, n, dtype, psi=psi) as st:
+    with make(qe, n, dtype, psi=psi, arith=arith) as st:
         e = st.expectation(xm, zm, cf)
     assert abs(e - oracle.expectation(psi, xm, zm, cf)) < tol
 
 
+@pytest.mark.parametrize("arith", ["fp64", "df64"])
 @pytest.mark.parametrize("qubits", [[0], [3, 0], [11, 2, 6], [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11]])
-def test_probs(qe, qubits):
+def test_probs(qe, qubits, arith):
     n = 12
     psi = I.random_state(n, 17)
-    with make(qe, n, psi=psi) as st:
+    with make(qe, n, psi=psi, arith=arith) as st:
         p = st.probs(qubits)
         nrm = st.norm2()
     ref = oracle.probs(psi, qubits)
-    # per-thread double-float partials carry about 44 significant bits
+    # FP64 sums, or double-float partials of about 44 significant bits
     assert np.max(np.abs(p - ref)) < 1e-13
     assert abs(nrm - 1) < 1e-13
 
@@ -519,17 +538,22 @@ def test_tensor_core_c64_wait_timeout_reports_and_recovers(qe, monkeypatch):
     assert oracle.fidelity(ref, got) > 1 - 1e-8
 
 
-# ------------------------------------------ tensor cores (complex128, k = 4, 5)
+# ------------------------------------------ tensor cores (complex128, k = 1..5)
 # Exact integer-digit products on the FP16 tensor pipe: inputs and matrix
-# entries are rounded to 2^-48 of their row scale, so the FP64 bar holds.
+# entries are rounded to 2^-56 (FP64 mode, seven digits) or 2^-48 (double-
+# float mode, six digits) of their row scale, so the FP64 bar holds.
+TC128 = {"fp64": "gate_tc_k5_c128", "df64": "gate_tc_k5_c128_df"}
+
+
+@pytest.mark.parametrize("arith", ["fp64", "df64"])
 @pytest.mark.parametrize("qubits", [[0, 1, 2, 3, 4], [10, 11, 12, 13, 14], [4, 0, 15, 7, 12],
                                     [2, 9, 5, 14], [15, 14, 13, 12], [6, 3, 11, 1, 8],
                                     [2, 9, 13], [0, 1, 2]])
-def test_tensor_core_blocks_c128(qe, qubits):
+def test_tensor_core_blocks_c128(qe, qubits, arith):
     n = 16
     U = rand_unitary(1 << len(qubits), np.random.default_rng(100 + sum(qubits)))
     psi = I.random_state(n, 13)
-    with make(qe, n, "c128", psi=psi, max_k=5) as st:
+    with make(qe, n, "c128", psi=psi, max_k=5, arith=arith) as st:
         st.reset_stats()
         st.profile(True)
         st.apply_gate(qubits, U)
@@ -539,7 +563,7 @@ def test_tensor_core_blocks_c128(qe, qubits):
         launches = st.stats()["launches"]
     ref = oracle.apply_gate(psi, qubits, U)
     assert launches == 1
-    assert prof.get("gate_tc_k5_c128", (0,))[0] == 1
+    assert prof.get(TC128[arith], (0,))[0] == 1
     close(got, ref)
 
 
@@ -547,12 +571,13 @@ def test_tensor_core_blocks_c128(qe, qubits):
 # (a flag nothing else sets), the splitters give up after a short limit, every
 # role leaves through the abort flag and tensor memory is freed; the host
 # reports QE_ERR_TIMEOUT and the same context then runs the block correctly.
-def test_tensor_core_c128_wait_timeout_reports_and_recovers(qe, monkeypatch):
+@pytest.mark.parametrize("arith", ["fp64", "df64"])
+def test_tensor_core_c128_wait_timeout_reports_and_recovers(qe, monkeypatch, arith):
     from paper_1604_06460_gb300.qe import QEError
     n, qubits = 14, [0, 3, 6, 9, 12]
     U = rand_unitary(32, np.random.default_rng(77))
     psi = I.random_state(n, 21)
-    with make(qe, n, "c128", psi=psi, max_k=5) as st:
+    with make(qe, n, "c128", psi=psi, max_k=5, arith=arith) as st:
         monkeypatch.setenv("QE_TEST_STALL_TC128", "1")
         with pytest.raises(QEError) as err:
             st.apply_gate(qubits, U)
@@ -565,24 +590,26 @@ def test_tensor_core_c128_wait_timeout_reports_and_recovers(qe, monkeypatch):
     close(got, oracle.apply_gate(psi, qubits, U))
 
 
+@pytest.mark.parametrize("arith", ["fp64", "df64"])
 @pytest.mark.parametrize("n,qubits", [(12, [0, 4, 7, 9, 11]), (12, [11, 10, 9, 8, 7]), (13, [12, 0, 6, 3, 9]),
                                       (13, [12, 11, 1])])
-def test_tensor_core_c128_smallest_states(qe, n, qubits):
+def test_tensor_core_c128_smallest_states(qe, n, qubits, arith):
     # n = 12: one tile holds the whole state (a single CTA); n = 13: two tiles;
     # the highest qubits as gate qubits
     U = rand_unitary(1 << len(qubits), np.random.default_rng(n * 31 + len(qubits)))
     psi = I.random_state(n, 5)
-    with make(qe, n, "c128", psi=psi, max_k=5) as st:
+    with make(qe, n, "c128", psi=psi, max_k=5, arith=arith) as st:
         st.profile(True)
         st.apply_gate(qubits, U)
         got = st.get()
         prof = st.profile_read()
         st.profile(False)
-    assert prof.get("gate_tc_k5_c128", (0,))[0] == 1
+    assert prof.get(TC128[arith], (0,))[0] == 1
     close(got, oracle.apply_gate(psi, qubits, U))
 
 
-def test_tensor_core_c128_special_values(qe):
+@pytest.mark.parametrize("arith", ["fp64", "df64"])
+def test_tensor_core_c128_special_values(qe, arith):
     # a basis state (all but one amplitude zero), amplitudes that are powers of
     # two (the splitting's binade edges), +-1 entries, and rows below the flush
     # threshold next to ordinary ones
@@ -602,7 +629,7 @@ def test_tensor_core_c128_special_values(qe):
             psi = I.random_state(n, 21)
             psi[: 1 << 10] *= 1e-290         # groups far below the flush threshold
             psi[1 << 10: 1 << 11] *= 1e-200  # small but kept
-        with make(qe, n, "c128", psi=psi, max_k=5) as st:
+        with make(qe, n, "c128", psi=psi, max_k=5, arith=arith) as st:
             st.apply_gate(qubits, U)
             got = st.get()
         ref = oracle.apply_gate(psi, qubits, U)
@@ -615,25 +642,26 @@ def test_tensor_core_c128_special_values(qe):
             assert rel < 1e-12
 
 
-def test_tensor_core_fused_circuit_c128(qe):
+@pytest.mark.parametrize("arith", ["fp64", "df64"])
+def test_tensor_core_fused_circuit_c128(qe, arith):
     n = 14
     gates = I.random_circuit(n, 8, seed=22)
     ref = oracle.zero_state(n)
     for g in gates:
         ref = oracle.apply_gate(ref, g.qubits, g.matrix)
-    with make(qe, n, "c128", max_k=5) as st:
+    with make(qe, n, "c128", max_k=5, arith=arith) as st:
         st.profile(True)
         for g in gates:
             st.apply(g)
         got = st.get()
         prof = st.profile_read()
         st.profile(False)
-    assert prof.get("gate_tc_k5_c128", (0,))[0] > 0
+    assert prof.get(TC128[arith], (0,))[0] > 0
     close(got, ref)
 
 
-@pytest.mark.parametrize("dtype,tol", [("c128", 1e-12), ("c64", 1e-5)])
-def test_many_pauli_terms_all_layouts(qe, dtype, tol):
+@pytest.mark.parametrize("dtype,tol,arith", [("c128", 1e-12, "fp64"), ("c128", 1e-12, "df64"), ("c64", 1e-5, None)])
+def test_many_pauli_terms_all_layouts(qe, dtype, tol, arith):
     # Z-only terms in several weight groups (more than fit one launch), X/Y
     # terms inside the low tile, with high qubits, and wider than one tile
     n = 15
@@ -657,6 +685,107 @@ def test_many_pauli_terms_all_layouts(qe, dtype, tol):
         cf.append(float(rng.standard_normal()))
     xm, zm, cf = (np.array(xm, dtype=np.uint64), np.array(zm, dtype=np.uint64), np.array(cf))
     psi = I.random_state(n, 5)
-    with make(qe, n, dtype, psi=psi) as st:
+    with make(qe, n, dtype, psi=psi, arith=arith) as st:
         e = st.expectation(xm, zm, cf)
     assert abs(e - oracle.expectation(psi, xm, zm, cf)) < tol
+
+
+# --------------------------------------------- FP64-mode accuracy (53 bits)
+# The FP64 mode must be as accurate as FP64 arithmetic, not merely within the
+# 1e-12 bar.  References here are the plain definitions evaluated in extended
+# precision (numpy longdouble: 64-bit significands on x86, 113 on AArch64), so
+# FP64 rounding of the reference itself does not mask the kernel's error.
+def _ld_apply(psi, qubits, U):
+    """Dense k-qubit gate on a state, the sum over the group evaluated in
+    long double (matrix bit j <-> qubits[j], as the oracle)."""
+    n = int(np.log2(psi.size))
+    k = len(qubits)
+    x = np.arange(psi.size)
+    groups = x[(x & sum(1 << q for q in qubits)) == 0]
+    dep = np.array([sum(((c >> j) & 1) << qubits[j] for j in range(k)) for c in range(1 << k)])
+    idx = groups[:, None] + dep[None, :]                 # (groups, 2^k)
+    A = psi[idx].astype(np.clongdouble)
+    Ul = np.asarray(U, dtype=np.clongdouble)
+    out = np.zeros_like(A)
+    for c in range(1 << k):                              # out[g, r] = sum_c U[r, c] A[g, c]
+        out += A[:, c:c + 1] * Ul[None, :, c]
+    res = np.empty(psi.size, dtype=np.clongdouble)
+    res[idx] = out
+    return res, idx
+
+
+def _rel_group_error(got, ref_ld, idx):
+    err = np.abs(got.astype(np.clongdouble) - ref_ld)[idx]
+    scale = np.sqrt(np.sum(np.abs(ref_ld[idx]) ** 2, axis=1))
+    return float(np.max(np.max(err, axis=1) / scale))
+
+
+@pytest.mark.parametrize("qubits", [[1, 4, 7, 10, 13], [0, 1, 2, 3, 4], [15, 3, 8, 0], [6, 12, 2], [2, 11], [9]])
+def test_fp64_mode_blocks_at_fp64_rounding(qe, qubits):
+    # 3-5-qubit blocks: inputs rounded to 2^-56 of the group scale, exact
+    # digit products, one rounding of each output; 1-2-qubit blocks: native
+    # FP64.  Either way the error relative to the group's norm is a few units
+    # of 2^-53 at most (FP64 dot products of the same terms carry the same
+    # order), where the 48-bit double-float splitting leaves ~1e-14
+    n = 16
+    rng = np.random.default_rng(900 + len(qubits))
+    U = rand_unitary(1 << len(qubits), rng)
+    psi = I.random_state(n, 29)
+    ref, idx = _ld_apply(psi, qubits, U)
+    with make(qe, n, "c128", psi=psi, max_k=5) as st:
+        st.apply_gate(qubits, U)
+        got = st.get()
+    rel = _rel_group_error(got, ref, idx)
+    assert rel < 4 * 2.0 ** -53, f"relative group error {rel:.3e}"
+
+
+def test_fp64_mode_fft_at_fp64_rounding(qe):
+    # the QFT definition (Sec. III-B) in long double for a 10-qubit register
+    # inside a 12-qubit state; native FP64 butterflies and FP64 twiddles keep
+    # the error within a few units of 2^-53 per radix-2 stage
+    n, lo, m = 12, 1, 10
+    psi = I.random_state(n, 61)
+    N = 1 << m
+    pi = np.longdouble("3.14159265358979323846264338327950288")
+    k = np.arange(N)
+    W = np.exp(np.clongdouble(2j) * pi * ((k[:, None] * k[None, :]) % N).astype(np.longdouble) / N)
+    W /= np.sqrt(np.longdouble(N))
+    x = np.arange(psi.size)
+    reg = (x >> lo) & (N - 1)
+    rest = x & ~((N - 1) << lo)
+    ref = np.empty(psi.size, dtype=np.clongdouble)
+    for r in np.unique(rest):
+        sel = np.nonzero(rest == r)[0]
+        order = sel[np.argsort(reg[sel])]
+        ref[order] = W @ psi[order].astype(np.clongdouble)
+    with make(qe, n, "c128", psi=psi) as st:
+        st.set_policy(qe.POLICY_EMULATE, 1)
+        st.apply_qft(lo, m)
+        got = st.get()
+    err = float(np.max(np.abs(got.astype(np.clongdouble) - ref)))
+    rms = float(np.sqrt(np.mean(np.abs(ref) ** 2)))
+    assert err / rms < m * 4 * 2.0 ** -53, f"relative error {err / rms:.3e}"
+
+
+def test_fp64_mode_reductions_at_fp64_rounding(qe):
+    # TFIM energy and marginals against long-double sums of the oracle's terms
+    n = 14
+    psi = I.random_state(n, 73)
+    xm, zm, cf = I.tfim_terms(n)
+    p = np.abs(psi.astype(np.clongdouble)) ** 2
+    x = np.arange(psi.size)
+    e_ref = np.longdouble(0)
+    for i in range(n - 1):
+        s = 1 - 2 * (((x >> i) ^ (x >> (i + 1))) & 1)
+        e_ref += np.sum(p * s)
+    for i in range(n):
+        y = x ^ (1 << i)
+        e_ref += np.longdouble(0.7) * np.sum((np.conj(psi[y].astype(np.clongdouble)) * psi.astype(np.clongdouble)).real)
+    probs_ref = np.zeros(8, dtype=np.longdouble)
+    for r in range(8):
+        probs_ref[r] = np.sum(p[((x >> 3) & 7) == r])
+    with make(qe, n, "c128", psi=psi) as st:
+        e = st.expectation(xm, zm, cf)
+        pr = st.probs([3, 4, 5])
+    assert abs(np.longdouble(e) - e_ref) < 64 * 2.0 ** -53 * n
+    assert float(np.max(np.abs(pr.astype(np.longdouble) - probs_ref))) < 16 * 2.0 ** -53

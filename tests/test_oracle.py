@@ -384,6 +384,34 @@ def test_gaussian_state_normalised_and_slices():
     big = oracle.gaussian_slice(99, 1 << 40, 1 << 16)
     assert abs(np.mean(big.real ** 2) - 1) < 0.03 and abs(np.mean(big.imag ** 2) - 1) < 0.03
     assert abs(np.mean(big.real)) < 0.02 and abs(np.mean(big.imag)) < 0.02
+    # re and im independent: zero correlation, |z|^2 exponential with mean 2
+    assert abs(np.mean(big.real * big.imag)) < 0.02
+    assert abs(np.mean(np.abs(big) ** 2) - 2) < 0.05
+
+
+def test_gaussian_amplitude_by_hand_from_the_first_known_answer():
+    # Amplitude 0 of seed 0 uses counter (0, 0, 0, 0) and key (0, 0): the first
+    # published Philox4x32-10 vector.  Its words give, by the stated recipe,
+    # u1 = ((w1:w0 >> 11) + 1) 2^-53 in (0, 1], u2 = (w3:w2 >> 11) 2^-53 in
+    # [0, 1), re + i im = sqrt(-2 ln u1) (cos 2 pi u2 + i sin 2 pi u2).  A
+    # swapped word order, a lost "+ 1", u1/u2 exchanged or one phase for both
+    # parts each change this value.
+    import math
+    row = [l.split() for l in open(os.path.join(GOLD, "philox4x32_10_kat.txt"))
+           if l.strip() and not l.startswith("#")][0]
+    v = [int(x, 16) for x in row]
+    assert v[0:6] == [0] * 6
+    w0, w1, w2, w3 = v[6:10]
+    a = (w1 << 32) | w0
+    b = (w3 << 32) | w2
+    u1 = ((a >> 11) + 1) / 2.0 ** 53
+    u2 = (b >> 11) / 2.0 ** 53
+    r = math.sqrt(-2.0 * math.log(u1))
+    want = complex(r * math.cos(2 * math.pi * u2), r * math.sin(2 * math.pi * u2))
+    got = complex(oracle.gaussian_slice(0, 0, 1)[0])
+    assert abs(got - want) < 1e-15 * max(1.0, abs(want))
+    # the raw words: 0xe169c58d6627e8d5 and 0x9b00dbd8bc57ac4c
+    assert a == 0xE169C58D6627E8D5 and b == 0x9B00DBD8BC57AC4C
 
 
 # --- the cost model's network: pinned by finite differences -------------------
@@ -416,3 +444,21 @@ def test_mlp_forward_closed_form():
     x = np.array([[0.7]])
     want = -2.0 * np.tanh(1.5 * np.tanh(0.3 * 0.7 - 0.2) + 0.1) + 0.25
     assert abs(oracle.mlp_forward(p, x, h1, h2)[0] - want) < 1e-15
+
+
+def test_threaded_gate_loops_are_bit_identical():
+    # the OpenMP gate loops split the independent groups among threads; every
+    # group is computed by the same loop, so the state is bit-identical
+    n = 12
+    gates = I.random_circuit(n, 3, seed=4)
+    out = []
+    for t in (1, max(2, oracle.max_threads())):
+        oracle.set_threads(t)
+        psi = oracle.gaussian_state(n, 9)
+        for g in gates:
+            oracle.apply_gate(psi, g.qubits, g.matrix, inplace=True)
+        oracle.apply_controlled(psi, [1, 5], [3], I.haar_u2(np.random.default_rng(2)), inplace=True)
+        oracle.apply_mcx(psi, [0, 7], 11, inplace=True)
+        out.append(psi)
+    oracle.set_threads(oracle.max_threads())
+    assert np.array_equal(out[0], out[1])
