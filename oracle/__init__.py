@@ -61,6 +61,9 @@ def _load():
             "or_qft_circuit": (None, [dp, i, i, i, i]),
             "or_add_const": (None, [dp, i, i, dp, u64]),
             "or_add_const_circuit": (None, [dp, i, i, dp, u64]),
+            "or_mul": (None, [dp, i, i, dp, dp, dp]),
+            "or_div": (None, [dp, i, i, dp, dp, dp]),
+            "or_mul_circuit": (None, [dp, i, i, dp, dp, dp]),
             "or_expectation": (d, [dp, i, i, dp, dp, dp]),
             "or_probs": (None, [dp, i, i, dp, dp]),
             "or_mlp_param_count": (i, [i, i, i]),
@@ -208,6 +211,41 @@ def add_const_circuit(psi, qubits, c):
     q = _ints(qubits)
     _load().or_add_const_circuit(_ptr(a), n, q.size, _ptr(q), int(c) & ((1 << 64) - 1))
     return a
+
+
+def _regs(qa, qb, qc):
+    a, b, c = _ints(qa), _ints(qb), _ints(qc)
+    if not (a.size == b.size == c.size):
+        raise ValueError("registers a, b, c need the same width")
+    return a, b, c
+
+
+def mul(psi, qa, qb, qc):
+    """c -> (c + a b) mod 2^N on every basis state (Sec. III-A multiplication)."""
+    s, n = _state(psi)
+    s = s.copy()
+    a, b, c = _regs(qa, qb, qc)
+    _load().or_mul(_ptr(s), n, a.size, _ptr(a), _ptr(b), _ptr(c))
+    return s
+
+
+def div(psi, qa, qb, qc):
+    """The restoring division (a, b, 0) -> (a mod b, b, a div b) on every
+    basis state (Sec. III-A division; see oracle.c for c != 0)."""
+    s, n = _state(psi)
+    s = s.copy()
+    a, b, c = _regs(qa, qb, qc)
+    _load().or_div(_ptr(s), n, a.size, _ptr(a), _ptr(b), _ptr(c))
+    return s
+
+
+def mul_circuit(psi, qa, qb, qc):
+    """The multiplication as multi-controlled NOTs (repeated add and shift)."""
+    s, n = _state(psi)
+    s = s.copy()
+    a, b, c = _regs(qa, qb, qc)
+    _load().or_mul_circuit(_ptr(s), n, a.size, _ptr(a), _ptr(b), _ptr(c))
+    return s
 
 
 def expectation(psi, xmask, zmask, coeff):

@@ -364,6 +364,80 @@ void or_add_const_circuit(cplx* psi, int n, int m, const int* qubits, uint64_t c
 }
 
 /* ------------------------------------------------------------------ */
+/* Emulated multiplication and division (Sec. III-A).  Three registers a, b,
+ * c of N qubits each (bit j of a value <-> qa[j], qb[j], qc[j]).
+ *
+ * Multiplication: the paper maps (a, b, 0) to (a, b, ab), the product kept to
+ * the N bits of c.  On every basis state the emulator adds the product:
+ * c -> (c + a b) mod 2^N, which is that map on c = 0, a permutation of the
+ * basis states, and what the repeated add-and-shift circuit computes.
+ *
+ * Division: the paper maps (a, b, 0) to (r, b, a / b) with a = (a / b) b + r.
+ * On every basis state the emulator runs the restoring division, for i from
+ * N - 1 down to 0:  c_i ^= [b != 0 and a >= b 2^i];  then, if c_i = 1,
+ * a -> (a - b 2^i) mod 2^N.  Each step is a permutation, so the whole map is
+ * one; on c = 0 it leaves the quotient in c and the remainder in a (b = 0:
+ * nothing changes). */
+static uint64_t mul_target(uint64_t a, uint64_t b, uint64_t c, int N) {
+    uint64_t mask = (N >= 64) ? ~(uint64_t)0 : (((uint64_t)1 << N) - 1);
+    return (c + a * b) & mask;
+}
+static void div_target(uint64_t* a, uint64_t b, uint64_t* c, int N) {
+    uint64_t mask = (N >= 64) ? ~(uint64_t)0 : (((uint64_t)1 << N) - 1);
+    for (int i = N - 1; i >= 0; --i) {
+        uint64_t bi = b << i;                               /* b 2^i, N + i < 64 bits */
+        uint64_t t = (b != 0 && *a >= bi) ? 1u : 0u;
+        *c ^= t << i;
+        if ((*c >> i) & 1u) *a = (*a - bi) & mask;
+    }
+}
+void or_mul(cplx* psi, int n, int N, const int* qa, const int* qb, const int* qc) {
+    uint64_t dim = (uint64_t)1 << n, M = ((uint64_t)1 << N) - 1;
+    uint64_t cmask = deposit(M, N, qc);
+    cplx* out = (cplx*)malloc(dim * sizeof(cplx));
+    for (uint64_t x = 0; x < dim; ++x) {
+        uint64_t a = extract(x, N, qa), b = extract(x, N, qb), c = extract(x, N, qc);
+        uint64_t x2 = (x & ~cmask) | deposit(mul_target(a, b, c, N), N, qc);
+        out[x2] = psi[x];
+    }
+    memcpy(psi, out, dim * sizeof(cplx));
+    free(out);
+}
+void or_div(cplx* psi, int n, int N, const int* qa, const int* qb, const int* qc) {
+    uint64_t dim = (uint64_t)1 << n, M = ((uint64_t)1 << N) - 1;
+    uint64_t amask = deposit(M, N, qa), cmask = deposit(M, N, qc);
+    cplx* out = (cplx*)malloc(dim * sizeof(cplx));
+    for (uint64_t x = 0; x < dim; ++x) {
+        uint64_t a = extract(x, N, qa), b = extract(x, N, qb), c = extract(x, N, qc);
+        div_target(&a, b, &c, N);
+        uint64_t x2 = (x & ~(amask | cmask)) | deposit(a, N, qa) | deposit(c, N, qc);
+        out[x2] = psi[x];
+    }
+    memcpy(psi, out, dim * sizeof(cplx));
+    free(out);
+}
+
+/* The multiplication as a gate circuit (the simulated baseline, Sec. III-A's
+ * repeated addition and shift): c += a b is c += 2^(i+j) for every pair of
+ * set bits a_i, b_j with i + j < N, i.e. an increment of the sub-register
+ * (qc[i+j], ..., qc[N-1]) under the two controls a_i, b_j; an increment
+ * flips qc[k] when all lower bits of the sub-register are 1, from the top
+ * bit down (multi-controlled NOTs). */
+void or_mul_circuit(cplx* psi, int n, int N, const int* qa, const int* qb, const int* qc) {
+    int* ctl = (int*)malloc((N + 2) * sizeof(int));
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; i + j < N; ++j)
+            for (int k = N - 1; k >= i + j; --k) {
+                int nc = 0;
+                ctl[nc++] = qa[i];
+                ctl[nc++] = qb[j];
+                for (int l = i + j; l < k; ++l) ctl[nc++] = qc[l];
+                or_apply_mcx(psi, n, nc, ctl, qc[k]);
+            }
+    free(ctl);
+}
+
+/* ------------------------------------------------------------------ */
 /* Expectation value of a Hermitian Pauli sum (Sec. III-D):
  *   <psi| sum_t w_t P_t |psi>,  P_t = tensor over q of
  *   I, X, Z, Y for (x_q, z_q) = (0,0), (1,0), (0,1), (1,1).

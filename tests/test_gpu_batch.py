@@ -26,7 +26,7 @@ def qe():
 def oracle_energy(n, layers, seed, hx):
     psi = oracle.zero_state(n)
     for g in I.ansatz_circuit(n, layers, seed):
-        psi = oracle.apply_gate(psi, g.qubits, g.matrix)
+        oracle.apply_gate(psi, g.qubits, g.matrix, inplace=True)
     xm, zm, cf = I.tfim_terms(n, hx)
     return oracle.expectation(psi, xm, zm, cf)
 
@@ -69,3 +69,23 @@ def test_batch_rejects_bad_input(qe):
         qe.Batch([24], [np.zeros((1, 24, 2))], 0.7, "c128")
     with pytest.raises(qe.QEError):
         qe.Batch([3], [np.full((1, 3, 2), np.nan)], 0.7, "c128")
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-11), ("c64", 5e-4)])
+def test_batch_hbm_circuits_at_benchmark_sizes(qe, dtype, tol):
+    # the benchmark's workload shape (8 layers, n drawn from 10..22) at the
+    # default plan: circuits of 16-22 qubits live in HBM and take the
+    # multi-CTA passes; sampled ones are checked against the oracle
+    layers, hx, seed = 8, 0.7, 3
+    ns = list(I.batch_sizes(48, 10, 22, seed)) + [16, 19, 22]
+    angles = [I.ansatz_angles(int(n), layers, seed * 100000 + i) for i, n in enumerate(ns)]
+    with qe.Batch(ns, angles, hx, dtype) as b:
+        e = b.run()
+    picks = [len(ns) - 3, len(ns) - 2, len(ns) - 1] + [i for i, n in enumerate(ns) if 16 <= n <= 21][:2]
+    for i in picks:
+        psi = oracle.zero_state(int(ns[i]))
+        for g in I.ansatz_circuit(int(ns[i]), layers, seed * 100000 + i):
+            oracle.apply_gate(psi, g.qubits, g.matrix, inplace=True)
+        xm, zm, cf = I.tfim_terms(int(ns[i]), hx)
+        ref = oracle.expectation(psi, xm, zm, cf)
+        assert abs(e[i] - ref) < tol * max(1.0, abs(ref)), (i, ns[i], e[i], ref)

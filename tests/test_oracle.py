@@ -462,3 +462,78 @@ def test_threaded_gate_loops_are_bit_identical():
         out.append(psi)
     oracle.set_threads(oracle.max_threads())
     assert np.array_equal(out[0], out[1])
+
+
+# --- Sec. III-A multiplication and division permutations ----------------------
+def _reg_value(x, qs):
+    return sum(((x >> q) & 1) << j for j, q in enumerate(qs))
+
+
+def _basis_images(fn, n, qa, qb, qc):
+    """Image index of every basis state under the oracle map fn."""
+    out = []
+    for x in range(1 << n):
+        e = np.zeros(1 << n, complex)
+        e[x] = 1
+        y = fn(e, qa, qb, qc)
+        nz = np.nonzero(y)[0]
+        assert nz.size == 1 and y[nz[0]] == 1
+        out.append(int(nz[0]))
+    return out
+
+
+@pytest.mark.parametrize("N,order", [(1, "abc"), (2, "abc"), (3, "abc"), (2, "mixed")])
+def test_mul_is_the_paper_map_on_c0_and_a_permutation(N, order):
+    # (a, b, 0) -> (a, b, ab mod 2^N), Python's integer product as reference;
+    # every basis state goes to a distinct basis state
+    if order == "abc":   # paper's layout: c in the low qubits, then b, then a
+        qc, qb, qa = list(range(N)), list(range(N, 2 * N)), list(range(2 * N, 3 * N))
+    else:
+        qa, qb, qc = [4, 0], [2, 5], [1, 3]
+    n = 3 * N
+    img = _basis_images(oracle.mul, n, qa, qb, qc)
+    assert sorted(img) == list(range(1 << n))
+    for x in range(1 << n):
+        a, b, c = _reg_value(x, qa), _reg_value(x, qb), _reg_value(x, qc)
+        y = img[x]
+        assert _reg_value(y, qa) == a and _reg_value(y, qb) == b
+        if c == 0:
+            assert _reg_value(y, qc) == (a * b) % (1 << N)
+
+
+@pytest.mark.parametrize("N,order", [(1, "abc"), (2, "abc"), (3, "abc"), (3, "mixed")])
+def test_div_is_the_paper_map_on_c0_and_a_permutation(N, order):
+    # (a, b, 0) -> (a mod b, b, a div b) for b != 0 (Python's divmod), the
+    # identity for b = 0; a permutation of all basis states
+    if order == "abc":
+        qc, qb, qa = list(range(N)), list(range(N, 2 * N)), list(range(2 * N, 3 * N))
+    else:
+        qa, qb, qc = [8, 1, 4], [0, 6, 2], [5, 3, 7]
+    n = 3 * N
+    img = _basis_images(oracle.div, n, qa, qb, qc)
+    assert sorted(img) == list(range(1 << n))
+    for x in range(1 << n):
+        a, b, c = _reg_value(x, qa), _reg_value(x, qb), _reg_value(x, qc)
+        y = img[x]
+        assert _reg_value(y, qb) == b
+        if c == 0:
+            q, r = divmod(a, b) if b else (0, a)
+            assert (_reg_value(y, qa), _reg_value(y, qc)) == (r, q)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_mul_circuit_equals_permutation_bit_exact(N):
+    qc, qb, qa = list(range(N)), list(range(N, 2 * N)), list(range(2 * N, 3 * N))
+    psi = oracle.gaussian_state(3 * N, 50 + N)
+    assert np.array_equal(oracle.mul_circuit(psi, qa, qb, qc), oracle.mul(psi, qa, qb, qc))
+
+
+def test_mul_applied_2_to_the_N_times_is_the_identity():
+    # c -> c + 2^N ab = c (mod 2^N)
+    N = 3
+    qc, qb, qa = [0, 1, 2], [3, 4, 5], [6, 7, 8]
+    psi = oracle.gaussian_state(9, 4)
+    x = psi.copy()
+    for _ in range(1 << N):
+        x = oracle.mul(x, qa, qb, qc)
+    assert np.array_equal(x, psi)
