@@ -478,13 +478,20 @@ def main():
         torch.cuda.empty_cache()
         line["accuracy_vs_oracle"] = step_accuracy(qe, I, max_k=max_k)
         line["cpu_baseline"] = cpu_baseline(n, depth)
+        # the config-2 oracle reference (minutes of host work) runs on the
+        # host cores while the GPU runs the other configurations
+        from concurrent.futures import ThreadPoolExecutor
+        pool = ThreadPoolExecutor(max_workers=1)
+        ref28 = pool.submit(_config2_oracle, 28, 30, max(1, (os.cpu_count() or 2) - 1))
         for key, fn in (("config0_gate_by_gate", bench_config0), ("batch_config3", bench_batch),
-                        ("tensor_core_config2", bench_tensor_cores), ("config4_and_cost_model", bench_config4)):
+                        ("config4_and_cost_model", bench_config4),
+                        ("tensor_core_config2", lambda q, i: bench_tensor_cores(q, i, oracle_reference=ref28))):
             try:
                 line[key] = fn(qe, I)
             except Exception as exc:   # report, keep the headline line
                 line[key] = {"error": f"{type(exc).__name__}: {exc}"}
             torch.cuda.empty_cache()
+        pool.shutdown()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -693,6 +700,29 @@ def compare(st, qe, n, reg, cconst):
                         "register": [reg[0], reg[-1] + 1], "c": cconst,
                         "bit_exact": bool(torch.equal(emu, st.tensor))}
     del emu
+    # multiplication and division of N = n/3-qubit registers in the paper's
+    # layout (index = a b c, c in the low qubits; Sec. III-A, Sec. IV-B)
+    N = n // 3
+    qc, qb, qa = list(range(N)), list(range(N, 2 * N)), list(range(2 * N, 3 * N))
+    st.set_policy(qe.POLICY_EMULATE, 1)
+    st.init_random(7)
+    t_emu = timed(lambda: st.mul(qa, qb, qc))
+    emu = st.tensor.clone()
+    st.set_policy(qe.POLICY_SIMULATE, 1)
+    st.init_random(7)
+    st.reset_stats()
+    t_sim = timed(lambda: st.mul(qa, qb, qc))
+    gates = st.stats()["gates_applied"]
+    out["mul"] = {"N": N, "emulated_ms": t_emu, "simulated_ms": t_sim, "speedup": t_sim / t_emu,
+                  "simulated_gates": gates, "emulated_GB_per_s": 2 * (16 << n) / t_emu / 1e6,
+                  "bit_exact": bool(torch.equal(emu, st.tensor))}
+    del emu
+    st.set_policy(qe.POLICY_EMULATE, 1)
+    st.init_random(8)
+    t_div = timed(lambda: st.div(qa, qb, qc))
+    out["div"] = {"N": N, "emulated_ms": t_div, "emulated_GB_per_s": 4 * (16 << n) / t_div / 1e6,
+                  "note": "planes of 2^(2N) amplitudes through the scratch buffer (gather + copy back: "
+                          "4 x state bytes); no simulated division (its circuit needs work qubits)"}
     st.set_policy(qe.POLICY_AUTO, 2)
     return out
 
@@ -792,11 +822,25 @@ def bench_batch(qe, I, count=4096, layers=8, seed=3):
     return out
 
 
-def bench_tensor_cores(qe, I, n=32, depth=30, n_err=28):
+def _config2_oracle(n_err, depth, threads=None):
+    """The FP64 oracle's state of the config-2 circuit at n_err qubits, gate
+    by gate on the host cores; returns (state, seconds)."""
+    import oracle
+    from paper_1604_06460_gb300 import inputs as I
+    t0 = time.perf_counter()
+    oracle.set_threads(threads or os.cpu_count() or 1)
+    ref = oracle.zero_state(n_err)
+    for g in I.random_circuit(n_err, depth, seed=5):
+        oracle.apply_gate(ref, g.qubits, g.matrix, inplace=True)
+    return ref, time.perf_counter() - t0
+
+
+def bench_tensor_cores(qe, I, n=32, depth=30, n_err=28, oracle_reference=None):
     """complex64 state, depth-30 random circuit fused into 5-qubit blocks on
     the tcgen05 tensor cores (3xTF32, FP32 accumulation); the error at n_err
     on the same seed against the FP64 oracle, run gate by gate on the host
-    cores."""
+    cores (oracle_reference: a future of that run started earlier, so that it
+    overlaps the GPU work of other configurations)."""
     import torch
     import oracle
     gates = I.random_circuit(n, depth, seed=5)
@@ -833,12 +877,7 @@ def bench_tensor_cores(qe, I, n=32, depth=30, n_err=28):
         for g in gates:
             st.apply(g)
         got = st.get()
-    t0 = time.perf_counter()
-    oracle.set_threads(os.cpu_count() or 1)
-    ref = oracle.zero_state(n_err)
-    for g in gates:
-        oracle.apply_gate(ref, g.qubits, g.matrix, inplace=True)
-    t_or = time.perf_counter() - t0
+    ref, t_or = oracle_reference.result() if oracle_reference is not None else _config2_oracle(n_err, depth)
     max_abs, ov, nr, ng = 0.0, 0j, 0.0, 0.0
     chunk = 1 << 22
     for i0 in range(0, ref.size, chunk):

@@ -132,6 +132,28 @@ int qe_apply_qft(qe_state* s, int lo, int m, int inverse);
  * multi-controlled NOTs, as the policy decides.  1 <= m <= n. */
 int qe_apply_add_const(qe_state* s, int m, const int* qubits, uint64_t c);
 
+/* Multiplication and division of two N-qubit registers into a third
+ * (Sec. III-A), 1 <= N <= 16, the 3N qubits qa[], qb[], qc[] distinct and
+ * < n (bit j of a register value <-> qa[j], qb[j], qc[j]).
+ *   qe_apply_mul: c -> (c + a b) mod 2^N on every basis state: the paper's
+ *     (a, b, 0) -> (a, b, ab) with the product kept to N bits, extended to
+ *     c != 0 as the repeated add-and-shift circuit computes it.  Emulated as
+ *     one permutation, or simulated as that circuit of multi-controlled NOTs
+ *     (an increment of c[i+j ..] under controls a_i, b_j for every i + j < N),
+ *     as the policy decides.
+ *   qe_apply_div: the restoring division, for i = N-1 down to 0:
+ *     c_i ^= [b != 0 and a >= b 2^i], then a -> (a - b 2^i) mod 2^N if c_i = 1;
+ *     on c = 0 this is the paper's (a, b, 0) -> (a mod b, b, a div b) (b = 0
+ *     leaves the state unchanged).  Emulated only: QE_ERR_UNSUPPORTED under
+ *     QE_POLICY_SIMULATE.
+ * Both are permutations of the amplitudes, bit-exact.  A permutation whose
+ * plane (the 2^N values of c, or the 2^(2N) of (a, c)) exceeds 64 KB goes
+ * through a device scratch buffer of at most 1 GiB owned by the state.
+ * QE_ERR_ARG for N out of range, a qubit >= n, a repeated qubit or
+ * overlapping registers. */
+int qe_apply_mul(qe_state* s, int N, const int* qa, const int* qb, const int* qc);
+int qe_apply_div(qe_state* s, int N, const int* qa, const int* qb, const int* qc);
+
 /* <psi| sum_t coeff[t] P_t |psi> for Pauli strings P_t given by bit masks
  * over the qubits: (x,z) = (0,0) I, (1,0) X, (0,1) Z, (1,1) Y (Sec. III-D:
  * the expectation computed in one step instead of by repeated sampling).

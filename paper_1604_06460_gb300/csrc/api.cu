@@ -520,6 +520,22 @@ static void qft_simulated(qe_state* s, int lo, int m, int inverse) {
     s->stats.gates += (uint64_t)m + (uint64_t)m * (m - 1) / 2;
 }
 
+// c += a b as multi-controlled NOTs (repeated addition and shift, Sec. III-A):
+// for every pair of bits a_i, b_j with i + j < N, an increment of the
+// sub-register c[i+j ..] under the controls a_i, b_j.
+static void mul_simulated(qe_state* s, int N, const int* qa, const int* qb, const int* qc) {
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; i + j < N; ++j)
+            for (int k = N - 1; k >= i + j; --k) {
+                uint64_t cm = (1ull << qa[i]) | (1ull << qb[j]);
+                for (int l = i + j; l < k; ++l) cm |= 1ull << qc[l];
+                int t = qc[k];
+                int perm[2] = {1, 0};
+                launch_permute(s, cm, 1, &t, perm);
+                s->stats.gates += 1;
+            }
+}
+
 static void add_simulated(qe_state* s, int m, const int* qubits, uint64_t c) {
     // ripple of multi-controlled NOTs: adding 2^j increments (qubits[j..m-1])
     for (int j = 0; j < m; ++j) {
@@ -775,6 +791,36 @@ int qe_apply_add_const(qe_state* s, int m, const int* qubits, uint64_t c) {
     flush(s);
     if (choose_emulate_add(s, m, qubits, c)) launch_add_const(s, m, qubits, c);
     else add_simulated(s, m, qubits, c);
+    QE_API_END
+}
+
+static void check_arith_registers(const qe_state* s, int N, const int* qa, const int* qb, const int* qc) {
+    if (N < 1 || N > 16 || 3 * N > s->n) fail(QE_ERR_ARG, "register width N must be in [1, min(16, n/3)]");
+    uint64_t ma = 0, mb = 0, mc = 0;
+    check_qubits(s, N, qa, &ma);
+    check_qubits(s, N, qb, &mb);
+    check_qubits(s, N, qc, &mc);
+    if ((ma & mb) || (ma & mc) || (mb & mc)) fail(QE_ERR_ARG, "registers a, b, c overlap");
+}
+
+int qe_apply_mul(qe_state* s, int N, const int* qa, const int* qb, const int* qc) {
+    QE_API_BEGIN
+    check_state(s);
+    check_arith_registers(s, N, qa, qb, qc);
+    flush(s);
+    if (choose_emulate_mul(s, N)) launch_mul(s, N, qa, qb, qc);
+    else mul_simulated(s, N, qa, qb, qc);
+    QE_API_END
+}
+
+int qe_apply_div(qe_state* s, int N, const int* qa, const int* qb, const int* qc) {
+    QE_API_BEGIN
+    check_state(s);
+    check_arith_registers(s, N, qa, qb, qc);
+    if (s->policy == QE_POLICY_SIMULATE)
+        fail(QE_ERR_UNSUPPORTED, "the division is only emulated (its reversible circuit needs work qubits)");
+    flush(s);
+    launch_div(s, N, qa, qb, qc);
     QE_API_END
 }
 

@@ -55,6 +55,32 @@ double analytic_add_emulate(const qe_state* s, int m) {
     return 2.0 * N * B / kBandwidth;
 }
 
+// The multiplication's gate circuit: for every pair i + j < N an increment
+// of c[i+j ..] under controls a_i, b_j, i.e. multi-controlled NOTs on qubit
+// c_k with 2 + (k - i - j) controls, each touching 2^-(controls) of the state.
+double analytic_mul_simulate(const qe_state* s, int N) {
+    const double Nn = std::ldexp(1.0, s->n), B = s->dtype == QE_C128 ? 16.0 : 8.0;
+    double bytes = 0.0;
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; i + j < N; ++j)
+            for (int k = N - 1; k >= i + j; --k) bytes += 2.0 * std::ldexp(Nn, -(2 + k - i - j)) * B;
+    return bytes / kBandwidth;
+}
+
+// One permutation pass (two through the scratch buffer when a plane exceeds
+// shared memory).
+double analytic_mul_emulate(const qe_state* s, int N) {
+    const double Nn = std::ldexp(1.0, s->n), B = s->dtype == QE_C128 ? 16.0 : 8.0;
+    const double plane = std::ldexp(B, N);
+    return (plane <= 65536.0 ? 2.0 : 4.0) * Nn * B / kBandwidth;
+}
+
+bool choose_emulate_mul(qe_state* s, int N) {
+    if (s->policy == QE_POLICY_EMULATE) return true;
+    if (s->policy == QE_POLICY_SIMULATE) return false;
+    return analytic_mul_emulate(s, N) <= analytic_mul_simulate(s, N);
+}
+
 // Learned choice: predicted log-times of the two paths.
 static bool model_prefers_first(qe_state* s, int op_a, int op_b, int lo, int hi, int m, uint64_t c) {
     float X[2 * kCostFeatures], y[2];

@@ -132,6 +132,9 @@ void launch_bitrev(qe_state* s, int lo, int m);
 
 // register + c mod 2^m, register bit j <-> qubits[j]
 void launch_add_const(qe_state* s, int m, const int* qubits, uint64_t c);
+// emulated multiplication c += a b and restoring division of N-qubit registers
+void launch_mul(qe_state* s, int N, const int* qa, const int* qb, const int* qc);
+void launch_div(qe_state* s, int N, const int* qa, const int* qb, const int* qc);
 
 // batch of ansatz circuits (struct qe_batch is defined in batch.cu)
 void batch_create(qe_batch* b);
@@ -148,5 +151,14 @@ double reduce_norm2(qe_state* s);
 double reduce_expectation(qe_state* s, int nterms, const uint64_t* xm, const uint64_t* zm,
                           const double* cf);
 void reduce_probs(qe_state* s, int m, const int* qubits, double* out);
+// the 2^m marginals into device memory (enqueued only); partial needs room for
+// probs_partials_needed(s, m) block partials
+uint64_t probs_partials_needed(const qe_state* s, int m);
+void reduce_probs_device(qe_state* s, int m, const int* qubits, double2* partial, double* dout);
+
+// measurement (Sec. II): inverse-CDF sampling with caller-given uniforms, and
+// the collapse onto an outcome
+void sample_shots(qe_state* s, int m, const int* qubits, int nshots, const double* u, uint64_t* out);
+double collapse(qe_state* s, int m, const int* qubits, uint64_t outcome);
 
 }  // namespace qe

@@ -12,7 +12,11 @@ double analytic_qft_emulate(const qe_state* s, int m);
 double analytic_add_simulate(const qe_state* s, int m, uint64_t c);
 double analytic_add_emulate(const qe_state* s, int m);
 
+double analytic_mul_simulate(const qe_state* s, int N);
+double analytic_mul_emulate(const qe_state* s, int N);
+
 bool choose_emulate_qft(qe_state* s, int lo, int m);
+bool choose_emulate_mul(qe_state* s, int N);
 bool choose_emulate_add(qe_state* s, int m, const int* qubits, uint64_t c);
 
 }  // namespace qe

@@ -497,8 +497,33 @@ __global__ void __launch_bounds__(kRThreads) k_probs_partial_f64(const __grid_co
     (void)shc;
 }
 
+// Blocks of the probability reduction for m register qubits: about 8 blocks
+// per SM in total, at least 2^14 amplitudes per block.
+uint64_t probs_chunks(const qe_state* s, int m) {
+    const uint64_t bins = 1ull << m;
+    const uint64_t want_blocks = (uint64_t)num_sms() * 8;
+    uint64_t chunks = std::max<uint64_t>(1, want_blocks / bins);
+    return std::min<uint64_t>(chunks, std::max<uint64_t>(1, (1ull << (s->n - m)) >> 14));
+}
+
+template <class S>
+void probs_device(qe_state* s, int m, const int* qubits, double2* partial, double* dout);
+
 template <class S>
 void probs_impl(qe_state* s, int m, const int* qubits, double* host_out) {
+    const uint64_t bins = 1ull << m;
+    const uint64_t nblocks = bins * probs_chunks(s, m);
+    char* scr = (char*)ensure_scratch(s, nblocks * sizeof(double2) + bins * sizeof(double));
+    double* dout = (double*)(scr + nblocks * sizeof(double2));
+    probs_device<S>(s, m, qubits, (double2*)scr, dout);
+    QE_CUDA(cudaMemcpyAsync(host_out, dout, bins * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    QE_CUDA(cudaStreamSynchronize(s->stream));
+}
+
+// The 2^m marginal probabilities into device memory dout (partial: room for
+// 2^m * probs_chunks(s, m) block partials); enqueued only.
+template <class S>
+void probs_device(qe_state* s, int m, const int* qubits, double2* partial, double* dout) {
     static thread_local ProbArgs<S> a;
     a.x = reinterpret_cast<const S*>(s->d);
     a.m = m;
@@ -511,16 +536,11 @@ void probs_impl(qe_state* s, int m, const int* qubits, double* host_out) {
     for (int j = 0; j < m; ++j) a.q_sorted[j] = (uint8_t)tmp[j];
     const uint64_t bins = 1ull << m;
     a.per_bin = 1ull << (s->n - m);
-    // about 8 blocks per SM in total, at least 2^14 amplitudes per block
-    uint64_t want_blocks = (uint64_t)num_sms() * 8;
-    uint64_t chunks = std::max<uint64_t>(1, want_blocks / bins);
-    chunks = std::min<uint64_t>(chunks, std::max<uint64_t>(1, a.per_bin >> 14));
+    const uint64_t chunks = probs_chunks(s, m);
     a.chunks = chunks;
     a.chunk_len = (a.per_bin + chunks - 1) / chunks;
     const uint64_t nblocks = bins * chunks;
-    char* scr = (char*)ensure_scratch(s, nblocks * sizeof(double2) + bins * sizeof(double));
-    a.partial = (double2*)scr;
-    double* dout = (double*)(scr + nblocks * sizeof(double2));
+    a.partial = partial;
     if (nblocks > 0x7FFFFFFFull) fail(QE_ERR_UNSUPPORTED, "too many probability blocks");
     {
         Launch L(s, "probs_partial", (double)dim(s) * amp_bytes(s));
@@ -537,8 +557,6 @@ void probs_impl(qe_state* s, int m, const int* qubits, double* host_out) {
         k_sum_partials<<<g2, kSumThreads, 0, s->stream>>>(a.partial, bins, chunks, nullptr, dout);
         QE_CUDA(cudaGetLastError());
     }
-    QE_CUDA(cudaMemcpyAsync(host_out, dout, bins * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-    QE_CUDA(cudaStreamSynchronize(s->stream));
 }
 
 // Terms whose X/Y qubits do not fit one tile layout: grid-stride over x with
@@ -802,6 +820,13 @@ double reduce_norm2(qe_state* s) {
     if (s->dtype == QE_C128) probs_impl<double2>(s, 0, nullptr, &out);
     else probs_impl<float2>(s, 0, nullptr, &out);
     return out;
+}
+
+uint64_t probs_partials_needed(const qe_state* s, int m) { return (1ull << m) * probs_chunks(s, m); }
+
+void reduce_probs_device(qe_state* s, int m, const int* qubits, double2* partial, double* dout) {
+    if (s->dtype == QE_C128) probs_device<double2>(s, m, qubits, partial, dout);
+    else probs_device<float2>(s, m, qubits, partial, dout);
 }
 
 void reduce_probs(qe_state* s, int m, const int* qubits, double* out) {

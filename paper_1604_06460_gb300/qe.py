@@ -50,6 +50,8 @@ SIGNATURES = {
     "qe_apply_controlled": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
     "qe_apply_qft": (_i, [_vp, _i, _i, _i]),
     "qe_apply_add_const": (_i, [_vp, _i, _vp, _u64]),
+    "qe_apply_mul": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "qe_apply_div": (_i, [_vp, _i, _vp, _vp, _vp]),
     "qe_expectation": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
     "qe_probs": (_i, [_vp, _i, _vp, _vp]),
     "qe_norm2": (_i, [_vp, _vp]),
@@ -225,6 +227,22 @@ class State:
     def add_const(self, qubits, c):
         q = _i32(qubits)
         _check(load().qe_apply_add_const(self._h, q.size, _ptr(q), int(c) & ((1 << 64) - 1)))
+
+    def _regs(self, qa, qb, qc):
+        a, b, c = _i32(qa), _i32(qb), _i32(qc)
+        if not (a.size == b.size == c.size):
+            raise ValueError("registers a, b, c need the same width")
+        return a, b, c
+
+    def mul(self, qa, qb, qc):
+        """c -> (c + a b) mod 2^N (qe_apply_mul)."""
+        a, b, c = self._regs(qa, qb, qc)
+        _check(load().qe_apply_mul(self._h, a.size, _ptr(a), _ptr(b), _ptr(c)))
+
+    def div(self, qa, qb, qc):
+        """The restoring division (a, b, 0) -> (a mod b, b, a div b) (qe_apply_div)."""
+        a, b, c = self._regs(qa, qb, qc)
+        _check(load().qe_apply_div(self._h, a.size, _ptr(a), _ptr(b), _ptr(c)))
 
     def expectation(self, xmask, zmask, coeff):
         xm = np.ascontiguousarray(np.asarray(xmask, dtype=np.uint64))
