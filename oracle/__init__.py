@@ -66,6 +66,8 @@ def _load():
             "or_mul_circuit": (None, [dp, i, i, dp, dp, dp]),
             "or_expectation": (d, [dp, i, i, dp, dp, dp]),
             "or_probs": (None, [dp, i, i, dp, dp]),
+            "or_sample": (None, [dp, i, i, dp, i, dp, dp]),
+            "or_collapse": (d, [dp, i, i, dp, u64]),
             "or_mlp_param_count": (i, [i, i, i]),
             "or_mlp_forward": (None, [dp, i, i, i, dp, i, dp]),
             "or_mlp_grad": (d, [dp, i, i, i, dp, dp, i, dp]),
@@ -262,6 +264,26 @@ def probs(psi, qubits):
     out = np.empty(1 << q.size, dtype=np.float64)
     _load().or_probs(_ptr(a), n, q.size, _ptr(q), _ptr(out))
     return out
+
+
+def sample(psi, qubits, uniforms):
+    """Inverse-CDF samples of measuring qubits[] (all qubits: range(n)), one
+    per uniform in [0, 1) (Sec. II measurement)."""
+    a, n = _state(psi)
+    q = _ints(qubits)
+    u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64))
+    out = np.empty(u.size, dtype=np.uint64)
+    _load().or_sample(_ptr(a), n, q.size, _ptr(q), u.size, _ptr(u), _ptr(out))
+    return out
+
+
+def collapse(psi, qubits, outcome):
+    """(state after the outcome, its probability) (Sec. II collapse)."""
+    a, n = _state(psi)
+    a = a.copy()
+    q = _ints(qubits)
+    p = _load().or_collapse(_ptr(a), n, q.size, _ptr(q), int(outcome))
+    return a, p
 
 
 def fidelity(ref, got):

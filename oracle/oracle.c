@@ -485,6 +485,60 @@ void or_probs(const cplx* psi, int n, int m, const int* qubits, double* out) {
 }
 
 /* ------------------------------------------------------------------ */
+/* Measurement (Sec. II): measuring the qubits[] yields the value r of their
+ * bits with probability P(r), the sum of |alpha_x|^2 over the x whose bits
+ * at qubits[] spell r (all n qubits in order: P(i) = |alpha_i|^2).  Sampling
+ * by the inverse of the cumulative distribution, with the uniforms u[s] in
+ * [0, 1) given: shot s is the smallest r whose cumulative probability
+ * exceeds u[s] times the total; if rounding leaves none, the largest r with
+ * P(r) > 0.  The cumulative sums are compensated. */
+void or_sample(const cplx* psi, int n, int m, const int* qubits, int nshots, const double* u,
+               uint64_t* out) {
+    uint64_t M = (uint64_t)1 << m;
+    double* P = (double*)malloc(M * sizeof(double));
+    double* cum = (double*)malloc(M * sizeof(double));
+    or_probs(psi, n, m, qubits, P);
+    nsum acc = {0.0, 0.0};
+    uint64_t last = 0;
+    for (uint64_t r = 0; r < M; ++r) {
+        nsum_add(&acc, P[r]);
+        cum[r] = nsum_val(&acc);
+        if (P[r] > 0.0) last = r;
+    }
+    double total = cum[M - 1];
+    for (int s = 0; s < nshots; ++s) {
+        double target = u[s] * total;
+        uint64_t r = 0;
+        while (r < M && !(cum[r] > target)) ++r;
+        out[s] = (r < M) ? r : last;
+    }
+    free(P);
+    free(cum);
+}
+
+/* The state after a measurement of qubits[] gave `outcome` (Sec. II's
+ * collapse): amplitudes whose bits at qubits[] differ from the outcome
+ * become 0, the others are divided by sqrt(p), p the outcome's probability
+ * (compensated sum).  Returns p; for p = 0 the state is left unchanged. */
+double or_collapse(cplx* psi, int n, int m, const int* qubits, uint64_t outcome) {
+    uint64_t dim = (uint64_t)1 << n;
+    nsum acc = {0.0, 0.0};
+    for (uint64_t x = 0; x < dim; ++x) {
+        if (extract(x, m, qubits) != outcome) continue;
+        nsum_add(&acc, creal(psi[x]) * creal(psi[x]));
+        nsum_add(&acc, cimag(psi[x]) * cimag(psi[x]));
+    }
+    double p = nsum_val(&acc);
+    if (p == 0.0) return 0.0;
+    double inv = 1.0 / sqrt(p);
+    for (uint64_t x = 0; x < dim; ++x) {
+        if (extract(x, m, qubits) != outcome) psi[x] = 0.0;
+        else psi[x] *= inv;
+    }
+    return p;
+}
+
+/* ------------------------------------------------------------------ */
 /* The cost model's network (a multilayer perceptron; not from the paper,
  * which chooses between emulation and simulation by performance models and
  * measured cross-overs, Sec. III-B and Sec. IV-D).  Layout of params:

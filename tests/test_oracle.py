@@ -537,3 +537,62 @@ def test_mul_applied_2_to_the_N_times_is_the_identity():
     for _ in range(1 << N):
         x = oracle.mul(x, qa, qb, qc)
     assert np.array_equal(x, psi)
+
+
+# --- Sec. II measurement: sampling and collapse -------------------------------
+def _exact_state():
+    # probabilities 1/4, 1/4, 1/4, 1/16 x 4, 0: exact in binary
+    return np.array([0.5, 0.5j, -0.5, 0.25, -0.25j, 0.25, 0.25, 0.0], dtype=complex)
+
+
+def test_sample_inverse_cdf_closed_form():
+    psi = _exact_state()
+    # cumulative: 0.25 0.5 0.75 0.8125 0.875 0.9375 1 1
+    u = [0.0, 0.2499, 0.25, 0.5, 0.8125, 0.9, 0.9375, 0.99999]
+    got = oracle.sample(psi, [0, 1, 2], u)
+    assert list(got) == [0, 0, 1, 2, 4, 5, 6, 6]    # index 7 (probability 0) never
+    # marginal of qubit 2: P(0) = 13/16 (x = 0..3), P(1) = 3/16; qubits (2, 0): r = b2 + 2 b0
+    assert list(oracle.sample(psi, [2], [0.7, 0.8125, 0.9])) == [0, 1, 1]
+    # P(r) for (q2, q0): r=0: x in {0,2}: 1/2; r=1: {4,6}: 1/8; r=2: {1,3}: 5/16; r=3: {5,7}: 1/16
+    assert list(oracle.sample(psi, [2, 0], [0.49, 0.5, 0.62, 0.63, 0.95])) == [0, 1, 1, 2, 3]
+
+
+def test_sample_frequencies_match_probabilities():
+    # a statistical property: frequencies of 40000 samples within 5 sigma
+    psi = I.random_state(6, 3)
+    p = np.abs(psi) ** 2
+    u = np.random.default_rng(1).random(40000)
+    s = oracle.sample(psi, list(range(6)), u)
+    f = np.bincount(s.astype(np.int64), minlength=64) / u.size
+    sigma = np.sqrt(p * (1 - p) / u.size)
+    assert np.all(np.abs(f - p) < 5 * sigma + 1e-12)
+
+
+def test_collapse_closed_forms():
+    n = 5
+    ghz = np.zeros(1 << n, complex)
+    ghz[0] = ghz[-1] = 2 ** -0.5
+    post, p = oracle.collapse(ghz, [3], 1)
+    want = np.zeros(1 << n, complex)
+    want[-1] = 1
+    assert abs(p - 0.5) < 1e-15 and np.allclose(post, want, atol=1e-15, rtol=0)
+    # product state |+>|0>|1> (qubits 0, 1, 2): measuring qubit 0 as 1 leaves |1>|0>|1>
+    plus = np.array([1, 1]) / np.sqrt(2)
+    prod = np.kron(np.array([0, 1]), np.kron(np.array([1, 0]), plus)).astype(complex)
+    post, p = oracle.collapse(prod, [0], 1)
+    assert abs(p - 0.5) < 1e-15
+    e = np.zeros(8, complex)
+    e[0b101] = 1
+    assert np.allclose(post, e, atol=1e-15, rtol=0)
+    # an outcome of probability zero leaves the state unchanged
+    post, p = oracle.collapse(prod, [1], 1)
+    assert p == 0 and np.array_equal(post, prod)
+
+
+def test_collapse_renormalises_and_fixes_the_measured_bits():
+    psi = I.random_state(7, 8)
+    post, p = oracle.collapse(psi, [5, 1], 2)        # qubit 5 = 0, qubit 1 = 1
+    assert abs(p - oracle.probs(psi, [5, 1])[2]) < 1e-15
+    assert abs(oracle.norm2(post) - 1) < 1e-14
+    pr = oracle.probs(post, [5, 1])
+    assert abs(pr[2] - 1) < 1e-14 and abs(pr.sum() - 1) < 1e-14
