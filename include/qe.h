@@ -168,6 +168,28 @@ int qe_expectation(qe_state* s, int nterms, const uint64_t* xmask,
  * qubits[] spell r of |alpha_x|^2.  FP64 compensated accumulation. */
 int qe_probs(qe_state* s, int m, const int* qubits, double* out);
 
+/* Measurement (Sec. II: the value r of the measured qubits' bits occurs with
+ * probability P(r) = sum of |alpha_x|^2 over the x whose bits spell r;
+ * Sec. III-D: an emulator draws all the samples it needs from one copy of
+ * the state).
+ *   qe_sample: nshots samples, by the inverse of the cumulative
+ *     distribution with the caller's uniforms[s] in [0, 1) (host, nshots
+ *     values; the caller owns the randomness, so samples are reproducible):
+ *     outcomes[s] (host) is the smallest r whose cumulative probability
+ *     exceeds uniforms[s] times the total, or, when rounding leaves none, the
+ *     largest r with P(r) > 0.  m = 0 measures all n qubits (outcome = basis
+ *     index, qubits ignored); 1 <= m <= 16 measures qubits[] (outcome bit j
+ *     <-> qubits[j]).  Sums are FP64 in a fixed order; the state is not
+ *     changed.  QE_ERR_ARG for m out of range, bad qubits, nshots < 0, NULL
+ *     arrays with nshots > 0 or a uniform outside [0, 1).
+ *   qe_collapse: the state after measuring qubits[] (1 <= m <= n) gave
+ *     `outcome` (bit j <-> qubits[j]): amplitudes whose bits differ become 0,
+ *     the others are divided by sqrt(p), p the outcome's probability (FP64
+ *     sum), which *probability receives (may be NULL).  QE_ERR_ARG, state
+ *     untouched, for bad qubits, outcome >= 2^m or p = 0. */
+int qe_sample(qe_state* s, int m, const int* qubits, int nshots, const double* uniforms, uint64_t* outcomes);
+int qe_collapse(qe_state* s, int m, const int* qubits, uint64_t outcome, double* probability);
+
 /* sum_i |alpha_i|^2 in compensated FP64. */
 int qe_norm2(qe_state* s, double* out);
 
@@ -273,7 +295,11 @@ int qe_batch_free(qe_batch* b);
  *   qe_cost_features: the 16 features of an operation: op (0 gate pass,
  *     1 QFT emulated, 2 QFT simulated, 3 addition emulated, 4 addition
  *     simulated), n, dtype, k (gate width), lo/hi (lowest/highest qubit
- *     touched), m (register size), c (the added constant);
+ *     touched), m (register size), c (the added constant): one-hot op, n/34,
+ *     complex128 flag, k/5, log2 bytes/40, lo/n, hi/n, m/n, popcount(c)/m,
+ *     the gate count of the subroutine's circuit / n^2 (m + m(m-1)/2 for a
+ *     QFT, the sum of m - j over the set bits j of c for an addition), (n-m)/n
+ *     and a constant 1;
  *   qe_cost_model_gradient: loss (mean squared error) and its gradient with
  *     respect to all parameters for the samples X[n][16], targets t[n];
  *   qe_cost_model_train: full-batch Adam for `epochs` steps at rate lr;

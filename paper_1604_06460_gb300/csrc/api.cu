@@ -850,6 +850,31 @@ int qe_probs(qe_state* s, int m, const int* qubits, double* out) {
     QE_API_END
 }
 
+int qe_sample(qe_state* s, int m, const int* qubits, int nshots, const double* uniforms, uint64_t* outcomes) {
+    QE_API_BEGIN
+    check_state(s);
+    if (m < 0 || m > 16 || m > s->n) fail(QE_ERR_ARG, "m must be 0 (all qubits) or in [1, min(16, n)]");
+    if (m > 0) check_qubits(s, m, qubits, nullptr);
+    if (nshots < 0 || (nshots > 0 && (!uniforms || !outcomes))) fail(QE_ERR_ARG, "bad shot arrays");
+    for (int i = 0; i < nshots; ++i)
+        if (!(uniforms[i] >= 0.0 && uniforms[i] < 1.0)) fail(QE_ERR_ARG, "uniforms must lie in [0, 1)");
+    flush(s);
+    sample_shots(s, m, qubits, nshots, uniforms, outcomes);
+    QE_API_END
+}
+
+int qe_collapse(qe_state* s, int m, const int* qubits, uint64_t outcome, double* probability) {
+    QE_API_BEGIN
+    check_state(s);
+    if (m < 1 || m > s->n) fail(QE_ERR_ARG, "m must be in [1, n]");
+    check_qubits(s, m, qubits, nullptr);
+    if (m < 64 && (outcome >> m) != 0) fail(QE_ERR_ARG, "outcome has bits beyond the m measured qubits");
+    flush(s);
+    const double p = collapse(s, m, qubits, outcome);
+    if (probability) *probability = p;
+    QE_API_END
+}
+
 int qe_norm2(qe_state* s, double* out) {
     QE_API_BEGIN
     check_state(s);

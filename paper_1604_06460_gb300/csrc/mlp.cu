@@ -275,7 +275,14 @@ void cost_features(int op, int n, int dtype, int k, int lo, int hi, int m, uint6
     f[10] = (float)(hi / nn);
     f[11] = (float)(m / nn);
     f[12] = m > 0 ? (float)(__builtin_popcountll(c & ((m >= 64) ? ~0ull : ((1ull << m) - 1ull))) / (double)m) : 0.f;
-    f[13] = (float)((double)m * m / (nn * nn));
+    // size of the subroutine's gate circuit: m + m(m-1)/2 gates for a QFT,
+    // m - j multi-controlled NOTs for every set bit j of an added constant
+    double g = 0.0;
+    if (op == kOpQftEmulate || op == kOpQftSimulate) g = m + 0.5 * m * (m - 1);
+    if (op == kOpAddEmulate || op == kOpAddSimulate)
+        for (int j = 0; j < m && j < 64; ++j)
+            if ((c >> j) & 1ull) g += m - j;
+    f[13] = (float)(g / (nn * nn));
     f[14] = (float)((n - m) / nn);
     f[15] = 1.f;
 }

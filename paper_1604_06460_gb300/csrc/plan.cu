@@ -17,17 +17,25 @@ namespace qe {
 namespace {
 constexpr double kBandwidth = 6.7e12;      // bytes/s, device copy bandwidth
 constexpr double kFp32Ops = 3.4e13;        // FP32-pipe instructions/s
-// FP32-pipe instructions per complex element per radix-2 stage of the FFT:
-// about 46 in double-float arithmetic, 5 in FP32.
-double stage_ops(const qe_state* s) { return s->dtype == QE_C128 ? 46.0 : 5.0; }
+constexpr double kFp64Ops = 5.9e11;        // FP64-pipe instructions/s
+// Seconds of arithmetic per complex element per radix-2 FFT stage: about 46
+// FP32-pipe instructions in double-float arithmetic, 5 in FP32, 4.5 FP64
+// instructions in the FP64 mode.
+double stage_time(const qe_state* s) {
+    if (s->dtype == QE_C64) return 5.0 / kFp32Ops;
+    return s->arith == QE_ARITH_FP64 ? 4.5 / kFp64Ops : 46.0 / kFp32Ops;
+}
+// Seconds of arithmetic per amplitude of a dense 1-qubit pass (8 FP64
+// instructions in the FP64 mode; the FP32 pipes keep up with memory otherwise).
+double one_qubit_alu(const qe_state* s) { return c128_f64(s) ? 8.0 / kFp64Ops : 0.0; }
 }  // namespace
 
 double analytic_qft_simulate(const qe_state* s, int m) {
     const double N = std::ldexp(1.0, s->n), B = s->dtype == QE_C128 ? 16.0 : 8.0;
-    const double h_bytes = m * 2.0 * N * B;                       // m Hadamards
+    const double h = m * std::max(2.0 * N * B / kBandwidth, N * one_qubit_alu(s));    // m Hadamards
     const double cr_bytes = 0.5 * m * (m - 1) * 2.0 * (N / 4.0) * B;  // quarter-state phases
     const double rev_bytes = m > 1 ? 2.0 * N * B : 0.0;
-    return (h_bytes + cr_bytes + rev_bytes) / kBandwidth;
+    return h + (cr_bytes + rev_bytes) / kBandwidth;
 }
 
 double analytic_qft_emulate(const qe_state* s, int m) {
@@ -35,7 +43,7 @@ double analytic_qft_emulate(const qe_state* s, int m) {
     const int per_pass = s->dtype == QE_C128 ? 12 : 13;
     const int passes = (m + per_pass - 1) / per_pass + (m > per_pass ? 1 : 0);
     const double mem = passes * 2.0 * N * B / kBandwidth;
-    const double alu = N * m * stage_ops(s) / kFp32Ops;
+    const double alu = N * m * stage_time(s);
     return mem > alu ? mem : alu;
 }
 

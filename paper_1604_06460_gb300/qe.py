@@ -55,6 +55,8 @@ SIGNATURES = {
     "qe_expectation": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
     "qe_probs": (_i, [_vp, _i, _vp, _vp]),
     "qe_norm2": (_i, [_vp, _vp]),
+    "qe_sample": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
+    "qe_collapse": (_i, [_vp, _i, _vp, _u64, _vp]),
     "qe_flush": (_i, [_vp]),
     "qe_sync": (_i, [_vp]),
     "qe_set_policy": (_i, [_vp, _i, _i]),
@@ -257,6 +259,25 @@ class State:
         out = np.empty(1 << q.size, dtype=np.float64)
         _check(load().qe_probs(self._h, q.size, _ptr(q), _ptr(out)))
         return out
+
+    def sample(self, uniforms, qubits=None):
+        """Outcomes for the given uniforms in [0, 1): basis indices (qubits
+        None: all qubits) or the measured qubits' values (qe_sample)."""
+        u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64).reshape(-1))
+        out = np.empty(u.size, dtype=np.uint64)
+        if qubits is None:
+            _check(load().qe_sample(self._h, 0, None, u.size, _ptr(u), _ptr(out)))
+        else:
+            q = _i32(qubits)
+            _check(load().qe_sample(self._h, q.size, _ptr(q), u.size, _ptr(u), _ptr(out)))
+        return out
+
+    def collapse(self, qubits, outcome):
+        """Collapse onto the outcome of measuring qubits; returns its probability."""
+        q = _i32(qubits)
+        p = C.c_double()
+        _check(load().qe_collapse(self._h, q.size, _ptr(q), int(outcome) & ((1 << 64) - 1), C.byref(p)))
+        return p.value
 
     def norm2(self):
         out = C.c_double()
