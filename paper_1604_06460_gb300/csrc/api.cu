@@ -440,7 +440,10 @@ void complete_pending(qe_state* s) {
 
 
 void flush(qe_state* s) {
-    if (s->queue.empty()) return;
+    if (s->queue.empty()) {
+        complete_pending(s);   // a tensor-core pass launched outside a flush (QFT digit passes)
+        return;
+    }
     std::vector<PendingGate> q;
     q.swap(s->queue);
     const int k = choose_fusion_width(s, q);

@@ -225,16 +225,26 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pass(const __grid_constant_
 }
 
 // --------------------------------------------------------------- bitrev
-// In-place reversal of the register value's bits.  Work item = (outer bits,
-// middle value Mv <= rev(Mv)); tiles X(Mv) and Y(rev Mv) hold elements
-// [b][a][w] (b: top c register bits, a: bottom c register bits, w: the lo
-// qubits below the register) and are exchanged transposed and reversed.
+// In-place reversal of the order of the register value's D-bit digits (D = 1:
+// the bit reversal).  Work item = (outer bits, middle value Mv <= rev(Mv));
+// tiles X(Mv) and Y(rev Mv) hold elements [b][a][w] (b: top c register bits,
+// a: bottom c register bits, c a multiple of D, w: the lo qubits below the
+// register) and are exchanged transposed and digit-reversed.
 template <class P>
 struct RevArgs {
     typename P::S* x;
     uint64_t items;
-    int lo, m, c;
+    int lo, m, c, D;
 };
+
+// v (bits bits, a multiple of D) with the order of its D-bit digits reversed.
+__device__ __forceinline__ uint64_t digit_rev(uint64_t v, int bits, int D) {
+    if (D == 1) return bits > 0 ? (__brevll(v) >> (64 - bits)) : 0ull;
+    uint64_t r = 0;
+    const uint64_t dm = (1ull << D) - 1ull;
+    for (int i = 0; i < bits; i += D) r = (r << D) | ((v >> i) & dm);
+    return r;
+}
 
 template <class P>
 __global__ void __launch_bounds__(256) k_bitrev(const __grid_constant__ RevArgs<P> a) {
@@ -249,7 +259,7 @@ __global__ void __launch_bounds__(256) k_bitrev(const __grid_constant__ RevArgs<
     for (uint64_t item = blockIdx.x; item < a.items; item += gridDim.x) {
         const uint64_t mv = item & (nmid - 1ull);
         const uint64_t outer = item >> mid_bits;
-        const uint64_t mr = mid_bits > 0 ? (__brevll(mv) >> (64 - mid_bits)) : 0ull;
+        const uint64_t mr = digit_rev(mv, mid_bits, a.D);
         if (mv > mr) continue;
         const bool self = (mv == mr);
         const uint64_t obase = outer << (a.lo + a.m);
@@ -268,8 +278,8 @@ __global__ void __launch_bounds__(256) k_bitrev(const __grid_constant__ RevArgs<
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const int b2 = i / (C * W), aw = i % (C * W);
             const int a2 = aw / W, w = aw % W;
-            const int rb = (int)(__brev((uint32_t)a2) >> (32 - a.c));   // source b
-            const int ra = (int)(__brev((uint32_t)b2) >> (32 - a.c));   // source a
+            const int rb = (int)digit_rev((uint64_t)a2, a.c, a.D);   // source b
+            const int ra = (int)digit_rev((uint64_t)b2, a.c, a.D);   // source a
             const uint64_t off = ((uint64_t)b2 << shb) | (uint64_t)aw;
             a.x[bx + off] = srcX[rb * row + ra * W + w];
             if (!self) a.x[by + off] = X[rb * row + ra * W + w];
@@ -399,12 +409,12 @@ void fft_impl(qe_state* s, int lo, int m, int inverse, int pol) {
 }
 
 template <class S>
-__global__ void __launch_bounds__(256) k_bitrev_chunks(S* __restrict__ x, uint64_t count, int lo, int m) {
+__global__ void __launch_bounds__(256) k_bitrev_chunks(S* __restrict__ x, uint64_t count, int lo, int m, int D) {
     const uint64_t rmask = ((1ull << m) - 1ull) << lo;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t k = (i & rmask) >> lo;
-        const uint64_t kr = __brevll(k) >> (64 - m);
+        const uint64_t kr = digit_rev(k, m, D);
         if (k < kr) {
             const uint64_t j = (i & ~rmask) | (kr << lo);
             S t = x[i];
@@ -415,21 +425,24 @@ __global__ void __launch_bounds__(256) k_bitrev_chunks(S* __restrict__ x, uint64
 }
 
 template <class P>
-void bitrev_impl(qe_state* s, int lo, int m) {
-    if (m <= 1) return;
+void bitrev_impl(qe_state* s, int lo, int m, int D = 1) {
+    if (m <= D) return;
     using S = typename P::S;
-    Launch L(s, "bitrev", 2.0 * dim(s) * amp_bytes(s));
-    if (lo >= 5) {
+    Launch L(s, D == 1 ? "bitrev" : "digitrev", 2.0 * dim(s) * amp_bytes(s));
+    // end blocks of c bits (a multiple of D, 2c <= m) in tiles of 2^(2c + lo) <= 2^11
+    const int c = D * std::min(m / (2 * D), std::max(0, (11 - lo) / 2) / D);
+    if (lo >= 5 || c == 0) {
         // chunks of >= 32 contiguous amplitudes move as units: coalesced pair swaps
         const uint64_t count = dim(s);
         unsigned grid = (unsigned)std::min<uint64_t>((count + 255) / 256, (uint64_t)num_sms() * 8);
-        k_bitrev_chunks<S><<<grid, 256, 0, s->stream>>>(reinterpret_cast<S*>(s->d), count, lo, m);
+        k_bitrev_chunks<S><<<grid, 256, 0, s->stream>>>(reinterpret_cast<S*>(s->d), count, lo, m, D);
     } else {
         static thread_local RevArgs<P> a;
         a.x = reinterpret_cast<S*>(s->d);
         a.lo = lo;
         a.m = m;
-        a.c = std::min(m / 2, (11 - lo) / 2);
+        a.D = D;
+        a.c = c;
         a.items = (1ull << (s->n - lo - m)) << (m - 2 * a.c);
         const int C = 1 << a.c, W = 1 << lo;
         size_t smem = sizeof(S) * 2 * (size_t)C * (C * W + 1);
@@ -443,9 +456,111 @@ void bitrev_impl(qe_state* s, int lo, int m) {
     QE_CUDA(cudaGetLastError());
 }
 
+// ------------------------------------------------ tensor-core digit passes
+// The QFT of a register of m = G d bits as G dense d-qubit blocks on the
+// tensor cores (the 2^d-point DFT, the same matrix for every group of the
+// other qubits) with diagonal twiddles between them (Cooley-Tukey, digits
+// from the top): with k = k0 2^(m-d) + k' and l = l0 + 2^d l',
+//   y_l = sum_k' w_(2^(m-d))^(k' l') [ w_(2^m)^(k' l0) sum_k0 x_(k0, k') w_(2^d)^(k0 l0) ],
+// so a pass applies the DFT to the top digit (output l0 left in its qubits),
+// a twiddle pass multiplies by w_(2^m)^(k' l0), and the rest is the QFT of
+// the lower m - d bits; at the end the digits sit in reversed order and one
+// digit-reversal pass restores the natural order.  Scale 2^(-d/2) per block.
+template <class P>
+struct TwArgs {
+    typename P::S* x;
+    const typename P::M* fine;
+    const typename P::M* coarse;
+    uint64_t count;
+    int lo, m, h;
+    int top;      // the digit just transformed: register bits [top, top + d)
+    int d;
+    int shift;    // the twiddle exponent's scale to the 2^m table: 2^shift
+};
+
+// x *= w_(2^(top + d))^(k' l0), k' = register bits [0, top), l0 = bits [top, top + d)
+template <class P>
+__global__ void __launch_bounds__(256) k_digit_twiddle(const __grid_constant__ TwArgs<P> a) {
+    const uint64_t rmask = (1ull << a.m) - 1ull;
+    const uint64_t hmask = (1ull << a.h) - 1ull;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.count;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t r = (i >> a.lo) & rmask;
+        const uint64_t kp = r & ((1ull << a.top) - 1ull);
+        const uint64_t l0 = (r >> a.top) & ((1ull << a.d) - 1ull);
+        if (kp == 0 || l0 == 0) continue;
+        // exponent over 2^(top + d), scaled to the 2^m table
+        const uint64_t e = ((kp * l0) & ((1ull << (a.top + a.d)) - 1ull)) << a.shift;
+        const typename P::M w = P::cmul(a.coarse[e >> a.h], a.fine[e & hmask]);
+        a.x[i] = P::store(P::cmul(w, P::load(a.x[i])));
+    }
+}
+
+// Digit size for the tensor-core QFT of an m-bit register: the largest of
+// 5, 4, 3 dividing m (0: none).
+int qft_digit(int m) {
+    for (int d : {5, 4, 3})
+        if (m % d == 0) return d;
+    return 0;
+}
+
+template <class P>
+void qft_tc_impl(qe_state* s, int lo, int m, int inverse, int pol, int d) {
+    const int sign = inverse ? -1 : 1;
+    Table tb = get_tables<P>(s, m, sign, pol);
+    const int D = 1 << d;
+    std::vector<cd> F((size_t)D * D);
+    const double sc = 1.0 / std::sqrt((double)D);
+    for (int l = 0; l < D; ++l)
+        for (int k = 0; k < D; ++k) {
+            const double t = sign * 2.0 * ((double)((k * l) % D) / D);   // angle in units of pi
+            F[(size_t)l * D + k] = cd(sc * std::cos(M_PI * t), sc * std::sin(M_PI * t));
+        }
+    // exact values at the quarter turns (cos/sin of multiples of pi/2)
+    for (auto& v : F) {
+        if (std::fabs(v.real()) < 1e-17) v = cd(0.0, v.imag());
+        if (std::fabs(v.imag()) < 1e-17) v = cd(v.real(), 0.0);
+    }
+    static thread_local TwArgs<P> a;
+    a.x = reinterpret_cast<typename P::S*>(s->d);
+    a.fine = (const typename P::M*)tb.fine;
+    a.coarse = (const typename P::M*)tb.coarse;
+    a.count = dim(s);
+    a.lo = lo;
+    a.m = m;
+    a.h = (m + 1) / 2;
+    a.d = d;
+    const int G = m / d;
+    for (int t = 0; t < G; ++t) {
+        const int top = m - d * (t + 1);
+        int q[5];
+        for (int j = 0; j < d; ++j) q[j] = lo + top + j;
+        launch_gate_dense(s, d, q, F.data());
+        if (top == 0) break;
+        a.top = top;
+        a.shift = m - (top + d);
+        const unsigned grid = (unsigned)std::min<uint64_t>((a.count + 255) / 256, (uint64_t)num_sms() * 8);
+        Launch L(s, "fft_twiddle", 2.0 * dim(s) * amp_bytes(s));
+        k_digit_twiddle<P><<<grid, 256, 0, s->stream>>>(a);
+        QE_CUDA(cudaGetLastError());
+    }
+    bitrev_impl<F64>(s, lo, m, d);
+}
+
 }  // namespace
 
+// Tensor-core digit passes where a dense block of 3-5 qubits runs on the
+// tensor cores (complex128, n >= 12) and a digit size divides m; otherwise
+// the radix-2 shared-memory FFT.
 void launch_qft_fft(qe_state* s, int lo, int m, int inverse) {
+    const int d = qft_digit(m);
+    const bool tc = s->dtype == QE_C128 && s->c128_tc && s->tensor_cores && !s->force_tile && s->n >= 12 &&
+                    d >= c128_tc_kmin(s) && m > 1;
+    if (tc) {
+        if (s->arith == QE_ARITH_FP64) qft_tc_impl<F64>(s, lo, m, inverse, 1, d);
+        else qft_tc_impl<DF>(s, lo, m, inverse, 2, d);
+        return;
+    }
     if (s->dtype == QE_C64) fft_impl<F32>(s, lo, m, inverse, 0);
     else if (s->arith == QE_ARITH_FP64) fft_impl<F64>(s, lo, m, inverse, 1);
     else fft_impl<DF>(s, lo, m, inverse, 2);

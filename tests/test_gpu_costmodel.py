@@ -143,5 +143,9 @@ def test_learned_subroutine_choices_beat_analytic_rule(qe):
     for r in res:
         print(r)
     print("regret:", regret)
-    assert regret["learned"] < regret["analytic"]
+    # measured: the analytic rule emulates every addition, also those whose
+    # constant has only high bits set (one or two multi-controlled-NOT passes
+    # beat the register rotation) and those on registers of a few low qubits
+    # (tiny shared-memory slices); the learned model simulates those
+    assert regret["learned"] < 0.5 * regret["analytic"]
     model.close()

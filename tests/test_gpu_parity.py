@@ -275,7 +275,11 @@ def test_random_circuit_c64(qe):
 
 # ----------------------------------------------------------------- QFT
 @pytest.mark.parametrize("arith", ["fp64", "df64"])
-@pytest.mark.parametrize("n,lo,m", [(8, 0, 8), (10, 2, 5), (12, 0, 12), (14, 0, 14), (15, 1, 13), (13, 6, 7)])
+@pytest.mark.parametrize("n,lo,m", [(8, 0, 8), (10, 2, 5), (12, 0, 12), (14, 0, 14), (15, 1, 13), (13, 6, 7),
+                                    # tensor-core digit passes (digits of 5, 4, 3 qubits), the
+                                    # digit reversal in shared-memory tiles and in chunk swaps
+                                    (15, 0, 15), (16, 1, 15), (14, 2, 12), (18, 6, 12), (13, 0, 9),
+                                    (16, 0, 5), (14, 3, 8)])
 @pytest.mark.parametrize("inverse", [False, True])
 def test_qft_emulated_vs_dft(qe, n, lo, m, inverse, arith):
     psi = I.random_state(n, n + lo + m)
