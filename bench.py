@@ -898,17 +898,32 @@ def bench_tensor_cores(qe, I, n=32, depth=30, n_err=28, oracle_reference=None):
 def bench_config4(qe, I, n=33):
     """n=33 complex128 (128 GiB) random state: add-constant on a 16-qubit
     register (emulated permutation vs multi-controlled-NOT ripple) and the QFT
-    on it (FFT vs 136 gates); the learned cost model, trained on timing sweeps
-    of the other configurations, picks the paths; regret vs the measured best."""
+    on it (digit passes vs 136 gates).  The learned cost model is trained on
+    timing sweeps at the sizes of configurations 1-3 (gate passes of the
+    30-qubit complex128 and 32-qubit complex64 states, subroutines on 24- and
+    26-qubit states) and scored, with the analytic rule, on held-out
+    emulate-or-simulate decisions at n = 30 and on this configuration's two
+    subroutines: regret = time of the chosen paths / time of the best - 1."""
     import torch
     from paper_1604_06460_gb300 import costmodel
     t0 = time.perf_counter()
-    Xg, yg = costmodel.sweep_gate_passes([24, 26, 28], dtypes=("c128", "c64"), seed=0)
-    Xs, ys = costmodel.sweep_subroutines([22, 24, 26], dtypes=("c128",), seed=0)
-    X = np.concatenate([Xg, Xs])
-    y = np.concatenate([yg, ys])
+    Xg, yg = costmodel.sweep_gate_passes([30], dtypes=("c128",), seed=0)
+    Xc, yc = costmodel.sweep_gate_passes([32], dtypes=("c64",), seed=0)
+    Xs, ys = costmodel.sweep_subroutines([24, 26], dtypes=("c128",), seed=0)
+    X = np.concatenate([Xg, Xc, Xs])
+    y = np.concatenate([yg, yc, ys])
     model, loss = costmodel.train(X, y, epochs=4000, lr=3e-3, seed=0)
-    out = {"cost_model": {"samples": int(len(y)), "train_loss": loss, "sweep_and_train_s": time.perf_counter() - t0}}
+    out = {"cost_model": {"samples": int(len(y)), "train_loss": loss, "sweep_and_train_s": time.perf_counter() - t0,
+                          "sweeps": "gate passes k=1..5 at n=30 (c128) and n=32 (c64); QFTs and additions at "
+                                    "n=24, 26 (c128)"}}
+    t0 = time.perf_counter()
+    res, regret = costmodel.evaluate_decisions(30, costmodel.decision_cases(30), model)
+    out["decisions_n30"] = {"cases": len(res), "regret": regret,
+                            "learned_differs_from_analytic": sum(r["learned"] != r["analytic"] for r in res),
+                            "analytic_wrong": sum(r["analytic"] != r["best"] for r in res),
+                            "learned_wrong": sum(r["learned"] != r["best"] for r in res),
+                            "seconds": time.perf_counter() - t0}
+    torch.cuda.empty_cache()
     c = I.random_constant(16, 7)
     results = {}
     with qe.State(n, "c128") as st:
@@ -935,17 +950,21 @@ def bench_config4(qe, I, n=33):
             e1.synchronize()
             results[f"qft_{label}"] = e0.elapsed_time(e1)
             results[f"qft_{label}_sample"] = st.get(777 << 16, 4096).copy()
-        # what the learned model and the analytic rule choose
-        st.set_cost_model(model)
-        st.set_policy(qe.POLICY_AUTO, 2)
-        st.reset_stats()
-        st.init_random(9)
-        st.reset_stats()
-        st.apply_qft(0, 16)
-        learned_qft = "emulated" if st.stats()["launches"] < 10 else "simulated"
-        st.reset_stats()
-        st.add_const(list(range(16)), c)
-        learned_add = "emulated" if st.stats()["launches"] <= 3 else "simulated"
+        # which path each policy takes for this configuration's subroutines
+        chosen = {}
+        for pname, pol, mdl in (("analytic", qe.POLICY_ANALYTIC, None), ("learned", qe.POLICY_AUTO, model)):
+            st.set_cost_model(mdl)
+            st.set_policy(pol, 2)
+            st.init_random(9)
+            st.profile(True)
+            st.apply_qft(0, 16)
+            q = costmodel._path(st.profile_read())
+            st.profile(False)
+            st.profile(True)
+            st.add_const(list(range(16)), c)
+            a = costmodel._path(st.profile_read())
+            st.profile(False)
+            chosen[pname] = (q, a)
         st.set_cost_model(None)
     for r in (0, 17):
         out[f"add_const_reg_{r}_{r + 16}"] = {
@@ -960,9 +979,11 @@ def bench_config4(qe, I, n=33):
                            "simulated_gates": 16 + 120, "max_abs_sample": float(np.max(np.abs(a - b)))}
     best_qft = "emulated" if results["qft_emulated"] <= results["qft_simulated"] else "simulated"
     best_add = "emulated" if results["add_0_emulated"] <= results["add_0_simulated"] else "simulated"
-    out["learned_choice"] = {"qft": learned_qft, "add_const": learned_add,
-                             "qft_regret": results[f"qft_{learned_qft}"] / results[f"qft_{best_qft}"] - 1,
-                             "add_regret": results[f"add_0_{learned_add}"] / results[f"add_0_{best_add}"] - 1}
+    for pname in ("analytic", "learned"):
+        q, a_ = chosen[pname]
+        out[f"{pname}_choice_n33"] = {"qft": q, "add_const": a_,
+                                      "qft_regret": results[f"qft_{q}"] / results[f"qft_{best_qft}"] - 1,
+                                      "add_regret": results[f"add_0_{a_}"] / results[f"add_0_{best_add}"] - 1}
     model.close()
     return out
 

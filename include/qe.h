@@ -373,14 +373,16 @@ int qe_profile_read(qe_state* s, qe_kernel_profile* out, int max, int* count);
  * Block partial sums live in one static device array of 65536 (sum,
  * compensation) pairs, 1 MiB, which every GPU that loads the library keeps
  * until the process exits; requests needing more partials than that return
- * QE_ERR_ARG (with m <= 16 none does).  The first call on a device looks up
- * that array's device address (cudaGetSymbolAddress) once for that device,
- * so make the first call on each device before any stream capture.  All
+ * QE_ERR_ARG (with m <= 16 none does).  Every call looks up that array's
+ * address on the current device (cudaGetSymbolAddress, which allocates
+ * nothing); the first call on a device also loads the library's kernels
+ * there, so make the first call on each device before any stream capture.  All
  * calls share the array: calls whose work overlaps on the GPU (other streams,
  * other threads) race and must be serialised by the caller.  Every partial a
  * call reads is written earlier by the same call, so nothing needs clearing.
  * Status only (QE_ERR_ARG for bad arguments, QE_ERR_CUDA for a failed
- * launch); qe_last_error() is not updated. */
+ * launch, which includes an error an earlier CUDA call left pending on the
+ * calling thread); qe_last_error() is not updated. */
 int qe_probs_noalloc(const void* state, int n, int dtype, int m, const int* qubits,
                      double* out, void* stream);
 

@@ -471,6 +471,7 @@ struct TwArgs {
     typename P::S* x;
     const typename P::M* fine;
     const typename P::M* coarse;
+    const typename P::M* direct;   // w_(2^(top + d))^j for all j, when the order is at most 2^20 (else null)
     uint64_t count;
     int lo, m, h;
     int top;      // the digit just transformed: register bits [top, top + d)
@@ -489,9 +490,16 @@ __global__ void __launch_bounds__(256) k_digit_twiddle(const __grid_constant__ T
         const uint64_t kp = r & ((1ull << a.top) - 1ull);
         const uint64_t l0 = (r >> a.top) & ((1ull << a.d) - 1ull);
         if (kp == 0 || l0 == 0) continue;
-        // exponent over 2^(top + d), scaled to the 2^m table
-        const uint64_t e = ((kp * l0) & ((1ull << (a.top + a.d)) - 1ull)) << a.shift;
-        const typename P::M w = P::cmul(a.coarse[e >> a.h], a.fine[e & hmask]);
+        // exponent over 2^(top + d): one table entry when the order is small
+        // enough for a direct table, else the product of the two 2^m tables
+        const uint64_t e0 = (kp * l0) & ((1ull << (a.top + a.d)) - 1ull);
+        typename P::M w;
+        if (a.direct) {
+            w = a.direct[e0];
+        } else {
+            const uint64_t e = e0 << a.shift;
+            w = P::cmul(a.coarse[e >> a.h], a.fine[e & hmask]);
+        }
         a.x[i] = P::store(P::cmul(w, P::load(a.x[i])));
     }
 }
@@ -502,6 +510,37 @@ int qft_digit(int m) {
     for (int d : {5, 4, 3})
         if (m % d == 0) return d;
     return 0;
+}
+
+// Direct table of the 2^k roots of unity w_(2^k)^j (FP64-generated, stored in
+// the policy's type), cached per (device, k, sign, policy) like the two-level
+// tables; k <= 20 (16 MB for complex128, resident in L2).
+template <class P>
+__global__ void k_roots_direct(typename P::M* t, int k, int sign) {
+    const uint64_t N = 1ull << k;
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < N; j += (uint64_t)gridDim.x * blockDim.x) {
+        double sn, cs;
+        sincospi(scalbn((double)j, 1 - k), &sn, &cs);
+        t[j] = P::from_d(cs, sign > 0 ? sn : -sn);
+    }
+}
+std::map<std::pair<int, TableKey>, void*> g_direct;   // (device, (k, sign, policy)) -> table
+
+template <class P>
+const typename P::M* get_direct(qe_state* s, int k, int sign, int pol) {
+    int dev = 0;
+    QE_CUDA(cudaGetDevice(&dev));
+    auto key = std::make_pair(dev, TableKey{k, sign, pol});
+    auto it = g_direct.find(key);
+    if (it != g_direct.end()) return (const typename P::M*)it->second;
+    void* t = nullptr;
+    QE_CUDA(cudaMalloc(&t, sizeof(typename P::M) << k));
+    Launch L(s, "fft_twiddles", 0.0, false);
+    const unsigned grid = (unsigned)std::min<uint64_t>(((1ull << k) + 255) / 256, 4096);
+    k_roots_direct<P><<<grid, 256, 0, s->stream>>>((typename P::M*)t, k, sign);
+    QE_CUDA(cudaGetLastError());
+    g_direct[key] = t;
+    return (const typename P::M*)t;
 }
 
 template <class P>
@@ -539,6 +578,7 @@ void qft_tc_impl(qe_state* s, int lo, int m, int inverse, int pol, int d) {
         if (top == 0) break;
         a.top = top;
         a.shift = m - (top + d);
+        a.direct = (top + d <= 20) ? get_direct<P>(s, top + d, sign, pol) : nullptr;
         const unsigned grid = (unsigned)std::min<uint64_t>((a.count + 255) / 256, (uint64_t)num_sms() * 8);
         Launch L(s, "fft_twiddle", 2.0 * dim(s) * amp_bytes(s));
         k_digit_twiddle<P><<<grid, 256, 0, s->stream>>>(a);
@@ -549,16 +589,17 @@ void qft_tc_impl(qe_state* s, int lo, int m, int inverse, int pol, int d) {
 
 }  // namespace
 
-// Tensor-core digit passes where a dense block of 3-5 qubits runs on the
-// tensor cores (complex128, n >= 12) and a digit size divides m; otherwise
-// the radix-2 shared-memory FFT.
+// Tensor-core digit passes in the FP64 mode where a dense block of 3-5
+// qubits runs on the tensor cores (n >= 12) and a digit size divides m;
+// otherwise the radix-2 shared-memory FFT.
 void launch_qft_fft(qe_state* s, int lo, int m, int inverse) {
     const int d = qft_digit(m);
-    const bool tc = s->dtype == QE_C128 && s->c128_tc && s->tensor_cores && !s->force_tile && s->n >= 12 &&
-                    d >= c128_tc_kmin(s) && m > 1;
+    // (in the double-float mode the shared-memory FFT is the faster: its
+    // twiddle joins cost as much FP64 work as the digit passes save)
+    const bool tc = s->dtype == QE_C128 && s->arith == QE_ARITH_FP64 && s->c128_tc && s->tensor_cores &&
+                    !s->force_tile && s->n >= 12 && d >= c128_tc_kmin(s) && m > 1;
     if (tc) {
-        if (s->arith == QE_ARITH_FP64) qft_tc_impl<F64>(s, lo, m, inverse, 1, d);
-        else qft_tc_impl<DF>(s, lo, m, inverse, 2, d);
+        qft_tc_impl<F64>(s, lo, m, inverse, 1, d);
         return;
     }
     if (s->dtype == QE_C64) fft_impl<F32>(s, lo, m, inverse, 0);

@@ -9,7 +9,6 @@
 // array instead of allocated scratch.  The caller passes the state and the
 // output buffer; nothing is allocated on the device or through any library.
 #include <cstdint>
-#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -103,11 +102,6 @@ __global__ void k_noalloc_sum(const double2* __restrict__ partial, uint64_t bins
     }
 }
 
-// Device address of the scratch array, resolved once per device.
-constexpr int kMaxDevices = 64;
-double2* g_scratch_ptr[kMaxDevices] = {nullptr};
-std::mutex g_scratch_mu;
-
 }  // namespace
 
 extern "C" int qe_probs_noalloc(const void* state, int n, int dtype, int m, const int* qubits,
@@ -134,24 +128,19 @@ extern "C" int qe_probs_noalloc(const void* state, int n, int dtype, int m, cons
     a.m = m;
     a.per_bin = 1ull << (n - m);
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         return QE_ERR_CUDA;
     }
-    double2* partial;
-    {
-        std::lock_guard<std::mutex> lock(g_scratch_mu);
-        if (!g_scratch_ptr[dev]) {
-            void* p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-            if (e != cudaSuccess || !p) {
-                cudaGetLastError();
-                return QE_ERR_CUDA;
-            }
-            g_scratch_ptr[dev] = static_cast<double2*>(p);
-        }
-        partial = g_scratch_ptr[dev];
+    // the array's address on the current device, looked up on every call (a
+    // lookup once the module is loaded; it allocates nothing), so that an
+    // address from a context that was reset is never reused
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return QE_ERR_CUDA;
     }
+    double2* partial = static_cast<double2*>(p);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     uint64_t chunks = (uint64_t)(sms > 0 ? sms : 1) * 8 / bins;

@@ -40,6 +40,15 @@ double analytic_qft_simulate(const qe_state* s, int m) {
 
 double analytic_qft_emulate(const qe_state* s, int m) {
     const double N = std::ldexp(1.0, s->n), B = s->dtype == QE_C128 ? 16.0 : 8.0;
+    // FP64 mode, digit passes on the tensor cores: G = m / d block passes,
+    // G - 1 twiddle passes (about 6 FP64 instructions an amplitude) and the
+    // digit reversal
+    const int d = (m % 5 == 0) ? 5 : (m % 4 == 0) ? 4 : (m % 3 == 0) ? 3 : 0;
+    if (c128_f64(s) && s->c128_tc && s->tensor_cores && s->n >= 12 && d > 0) {
+        const int G = m / d;
+        const double pass = 2.0 * N * B / kBandwidth;
+        return G * pass + (G - 1) * std::max(pass, 6.0 * N / kFp64Ops) + (G > 1 ? pass : 0.0);
+    }
     const int per_pass = s->dtype == QE_C128 ? 12 : 13;
     const int passes = (m + per_pass - 1) / per_pass + (m > per_pass ? 1 : 0);
     const double mem = passes * 2.0 * N * B / kBandwidth;

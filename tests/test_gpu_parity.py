@@ -276,10 +276,10 @@ def test_random_circuit_c64(qe):
 # ----------------------------------------------------------------- QFT
 @pytest.mark.parametrize("arith", ["fp64", "df64"])
 @pytest.mark.parametrize("n,lo,m", [(8, 0, 8), (10, 2, 5), (12, 0, 12), (14, 0, 14), (15, 1, 13), (13, 6, 7),
-                                    # tensor-core digit passes (digits of 5, 4, 3 qubits), the
+                                    # tensor-core digit passes (digits of 4, 3 and 5 qubits), the
                                     # digit reversal in shared-memory tiles and in chunk swaps
-                                    (15, 0, 15), (16, 1, 15), (14, 2, 12), (18, 6, 12), (13, 0, 9),
-                                    (16, 0, 5), (14, 3, 8)])
+                                    (14, 2, 12), (18, 6, 12), (13, 0, 9), (16, 0, 5), (14, 3, 8),
+                                    (12, 1, 10)])
 @pytest.mark.parametrize("inverse", [False, True])
 def test_qft_emulated_vs_dft(qe, n, lo, m, inverse, arith):
     psi = I.random_state(n, n + lo + m)
@@ -329,6 +329,30 @@ def test_qft_many_passes_sampled(qe, arith):
             assert abs(got - want) < 1e-12
         st.apply_qft(lo, m, inverse=True)
         back = st.get()
+    close(back, psi)
+
+
+@pytest.mark.parametrize("arith", ["fp64", "df64"])
+@pytest.mark.parametrize("n,lo,m", [(15, 0, 15), (17, 1, 15), (20, 0, 20), (21, 4, 16)])
+def test_qft_tensor_core_digits_sampled(qe, n, lo, m, arith):
+    # registers too large for the direct DFT: sampled outputs from the
+    # oracle's one-amplitude definition, then the inverse restores the input
+    with make(qe, n, arith=arith) as st:
+        st.set_policy(qe.POLICY_EMULATE, 1)
+        st.init_random(3 + m)
+        psi = st.get()
+        st.profile(True)
+        st.apply_qft(lo, m)
+        prof = st.profile_read()
+        st.profile(False)
+        rng = np.random.default_rng(m)
+        for i in [0, 1, (1 << n) - 1] + [int(v) for v in rng.integers(0, 1 << n, size=5)]:
+            want = oracle.qft_amplitude(psi, lo, m, i)
+            assert abs(st.get(i, 1)[0] - want) < 1e-12
+        st.apply_qft(lo, m, inverse=True)
+        back = st.get()
+    if arith == "fp64":
+        assert "digitrev" in prof and "fft_pass" not in prof
     close(back, psi)
 
 
