@@ -286,6 +286,42 @@ def collapse(psi, qubits, outcome):
     return a, p
 
 
+def dense_unitary(n, gates):
+    """The 2^n x 2^n matrix of a circuit on n qubits (Sec. III-C): column j is
+    the circuit applied, gate by gate, to the basis state |j>."""
+    U = np.zeros((1 << n, 1 << n), dtype=np.complex128)
+    for j in range(1 << n):
+        e = np.zeros(1 << n, dtype=np.complex128)
+        e[j] = 1.0
+        for g in gates:
+            if getattr(g, "controls", ()):
+                e = apply_controlled(e, list(g.controls), list(g.qubits), g.matrix)
+            else:
+                e = apply_gate(e, list(g.qubits), g.matrix)
+        U[:, j] = e
+    return U
+
+
+def qpe_circuit(psi_sys, n, b, gates):
+    """Coherent phase estimation simulated gate by gate (Sec. III-C): b
+    ancillas at qubits [n, n+b) start in |0>, get Hadamards, ancilla j
+    controls U^(2^j) (the circuit repeated 2^j times, every gate controlled by
+    it), then the inverse QFT on the ancillas.  Returns the (n+b)-qubit
+    state; with an eigenvector of eigenvalue exp(2 pi i k / 2^b) the ancilla
+    register ends in |k>."""
+    psi = np.zeros(1 << (n + b), dtype=np.complex128)
+    psi[: 1 << n] = psi_sys
+    h = np.array([[1, 1], [1, -1]], dtype=np.complex128) / np.sqrt(2)
+    for j in range(b):
+        psi = apply_gate(psi, [n + j], h)
+    for j in range(b):
+        for _ in range(1 << j):
+            for g in gates:
+                ctl = [n + j] + list(getattr(g, "controls", ()))
+                psi = apply_controlled(psi, ctl, list(g.qubits), g.matrix)
+    return qft_dft(psi, n, b, inverse=True)
+
+
 def fidelity(ref, got):
     """|<ref|got>|^2 / (<ref|ref><got|got>) in FP64 (max-abs and fidelity are
     the two error measures every parity test reports)."""

@@ -596,3 +596,35 @@ def test_collapse_renormalises_and_fixes_the_measured_bits():
     assert abs(oracle.norm2(post) - 1) < 1e-14
     pr = oracle.probs(post, [5, 1])
     assert abs(pr[2] - 1) < 1e-14 and abs(pr.sum() - 1) < 1e-14
+
+
+# --- Sec. III-C phase estimation ----------------------------------------------
+def test_dense_unitary_matches_kronecker_products():
+    # single-qubit gates on distinct qubits: U = kron of the factors (numpy),
+    # qubit 0 the rightmost factor (little-endian)
+    rng = np.random.default_rng(5)
+    A, B2 = I.haar_u2(rng), I.haar_u2(rng)
+    gates = [I.single(0, A), I.single(2, B2)]
+    U = oracle.dense_unitary(3, gates)
+    want = np.kron(B2, np.kron(np.eye(2), A))
+    assert np.max(np.abs(U - want)) < 1e-15
+    # a CNOT then: the product of the two matrices (numpy's matmul)
+    cx = oracle.dense_unitary(3, [I.cnot(0, 1)])
+    U2 = oracle.dense_unitary(3, gates + [I.cnot(0, 1)])
+    assert np.max(np.abs(U2 - cx @ U)) < 1e-15
+
+
+def test_qpe_circuit_reads_exact_phases():
+    # U diagonal with eigenvalues exp(2 pi i k / 2^b) on basis states: the
+    # ancilla register ends exactly in |k> (closed form of phase estimation)
+    n, b = 2, 4
+    # phase of basis state x: 2 pi (3 x0 + 5 x1) / 16 via two RZ-like diagonal gates
+    def phase_gate(q, k):
+        return I.Gate((q,), np.diag([1.0, np.exp(2j * np.pi * k / 16)]), (), "p")
+    gates = [phase_gate(0, 3), phase_gate(1, 5)]
+    for x in range(4):
+        e = np.zeros(4, complex)
+        e[x] = 1
+        out = oracle.qpe_circuit(e, n, b, gates)
+        k = (3 * (x & 1) + 5 * (x >> 1)) % 16
+        assert abs(abs(out[(k << n) | x]) - 1) < 1e-12
