@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--fusion-comparison", action="store_true",
                     help="also time the step with fusion up to 2 qubits")
     ap.add_argument("--quick", action="store_true", help="skip e2e, CPU baseline and the comparison")
-    ap.add_argument("--only", default="", choices=["", "batch", "tensor_cores", "config4", "qft"],
+    ap.add_argument("--only", default="", choices=["", "batch", "tensor_cores", "config4", "qft", "qpe"],
                     help="run one secondary configuration alone (sizes from --n) and print its JSON")
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64"], help="state type for --only qft")
     ap.add_argument("--kernel-case", default="", choices=["", *KERNEL_CASES],
@@ -373,6 +373,8 @@ def main():
             res = bench_batch(qe, I)
         elif args.only == "qft":
             res = bench_qft(qe, args.n, args.dtype)
+        elif args.only == "qpe":
+            res = bench_qpe(qe, I)
         elif args.only == "tensor_cores":
             res = bench_tensor_cores(qe, I, n=args.n, n_err=min(args.n, 24))
         else:
@@ -484,7 +486,7 @@ def main():
         pool = ThreadPoolExecutor(max_workers=1)
         ref28 = pool.submit(_config2_oracle, 28, 30, max(1, (os.cpu_count() or 2) - 1))
         for key, fn in (("config0_gate_by_gate", bench_config0), ("batch_config3", bench_batch),
-                        ("config4_and_cost_model", bench_config4),
+                        ("config4_and_cost_model", bench_config4), ("phase_estimation", bench_qpe),
                         ("tensor_core_config2", lambda q, i: bench_tensor_cores(q, i, oracle_reference=ref28))):
             try:
                 line[key] = fn(qe, I)
@@ -892,6 +894,65 @@ def bench_tensor_cores(qe, I, n=32, depth=30, n_err=28, oracle_reference=None):
                                    "reference": "oracle (FP64, gate by gate on the host cores)",
                                    "oracle_s": t_or, "oracle_threads": oracle.max_threads()}
     del ref, got
+    return out
+
+
+def bench_qpe(qe, I, ns=(8, 9, 10, 11, 12)):
+    """Phase estimation, simulated vs emulated (Sec. III-C; Table II's
+    quantities on one GPU): U is one Trotter step of the 1-D transverse-field
+    Ising evolution (G = 4n - 3 gates).  T_apply: the circuit applied once,
+    gate by gate, to an (n+1)-qubit state (the one-ancilla simulation needs
+    2^b - 1 of them); T_build: the dense 2^n x 2^n matrix of U (identity state
+    plus the gates); T_gemm: one FP64 squaring.  The cross-over is the
+    smallest b with (2^b - 1) T_apply >= T_build + (b - 1) T_gemm."""
+    import torch
+    out = {}
+    for n in ns:
+        gates = I.tfim_trotter_step(n)
+        with qe.State(n + 1, "c128") as st:
+            st.set_policy(qe.POLICY_AUTO, 1)
+            st.init_random(1)
+            for g in gates:
+                st.apply(g)
+            st.flush()
+            reps = 20
+            e0, e1 = _events()
+            e0.record(st.stream)
+            for _ in range(reps):
+                for g in gates:
+                    st.apply(g)
+                st.flush()
+            e1.record(st.stream)
+            e1.synchronize()
+            t_apply = e0.elapsed_time(e1) / reps
+        with qe.State(2 * n, "c128") as u, qe.State(2 * n, "c128") as u2:
+            u.set_policy(qe.POLICY_AUTO, 0)
+            torch.cuda.synchronize()
+            e0, e1 = _events()
+            e0.record(u.stream)
+            u.init_identity(n)
+            for g in gates:
+                u.apply(g)
+            u.flush()
+            e1.record(u.stream)
+            e1.synchronize()
+            t_build = e0.elapsed_time(e1)
+            u2.matmul(u, u)
+            torch.cuda.synchronize()
+            e0, e1 = _events()
+            e0.record(u2.stream)
+            u2.matmul(u, u)
+            e1.record(u2.stream)
+            e1.synchronize()
+            t_gemm = e0.elapsed_time(e1)
+        b = 1
+        while (2 ** b - 1) * t_apply < t_build + (b - 1) * t_gemm and b < 64:
+            b += 1
+        out[f"n{n}"] = {"G": len(gates), "apply_U_ms": t_apply, "build_dense_U_ms": t_build, "zgemm_ms": t_gemm,
+                        "zgemm_TFLOPs": 8.0 * 8 ** n / (t_gemm * 1e-3) / 1e12, "crossover_bits": b}
+        torch.cuda.empty_cache()
+    out["note"] = ("Table II of the paper (Xeon, MKL zgemm) gives cross-overs 6, 9, 12, 15, 18 bits for "
+                   "n = 8..12 (context only)")
     return out
 
 

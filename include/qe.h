@@ -168,6 +168,31 @@ int qe_expectation(qe_state* s, int nterms, const uint64_t* xmask,
  * qubits[] spell r of |alpha_x|^2.  FP64 compensated accumulation. */
 int qe_probs(qe_state* s, int m, const int* qubits, double* out);
 
+/* Phase estimation by emulation (Sec. III-C).  A dense 2^k x 2^k complex
+ * matrix is held in a complex128 state of 2k qubits, column-major: entry
+ * (i, j) is amplitude (j << k) | i.
+ *   qe_init_identity: the identity matrix (s has 2 nsys qubits).  Applying a
+ *     circuit's gates to qubits [0, nsys) of it afterwards applies them to
+ *     every column, so the state becomes the circuit's dense matrix U: the
+ *     emulator's O(G 2^(2n)) construction of U.
+ *   qe_matmul: c = a b for three such states of the same width (c distinct
+ *     from a and b), in FP64 (fused multiply-adds): one squaring of the
+ *     repeated squaring U^(2^i) = U^(2^(i-1)) U^(2^(i-1)), O(2^(3k)).
+ *   qe_qpe_emulate: coherent phase estimation on s with the system register
+ *     [0, nsys) and b ancillas [nsys, nsys + b) (nsys + b <= n): Hadamards on
+ *     the ancillas, ancilla j applies U^(2^j) (u holds U, 2 nsys qubits) to
+ *     the system register where it is 1 -- the powers by repeated squaring,
+ *     each applied as one dense product -- then the inverse QFT on the
+ *     ancillas (emulated).  With the ancillas in |0> and an eigenvector of U
+ *     with eigenvalue exp(2 pi i k / 2^b), the ancilla register ends in |k>.
+ *     Allocates two temporary matrices (QE_ERR_OOM if that fails) and uses
+ *     the state's scratch; synchronises the stream.
+ * All three want complex128 states; QE_ERR_ARG for mismatched widths or a
+ * result that would overwrite an input. */
+int qe_init_identity(qe_state* s, int nsys);
+int qe_matmul(qe_state* c, qe_state* a, qe_state* b);
+int qe_qpe_emulate(qe_state* s, int nsys, int b, qe_state* u);
+
 /* Measurement (Sec. II: the value r of the measured qubits' bits occurs with
  * probability P(r) = sum of |alpha_x|^2 over the x whose bits spell r;
  * Sec. III-D: an emulator draws all the samples it needs from one copy of

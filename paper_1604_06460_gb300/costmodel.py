@@ -110,10 +110,15 @@ def decision_cases(n, seed=1):
     return cases
 
 
+# kernels that only the emulated QFT and addition launch (the simulated paths
+# run elementwise 1-2-qubit gates, controlled phases and permutations)
+_EMULATED = {"fft_pass", "fft_twiddle", "digitrev", "gate_tc_k5_c128", "gate_tc_k5_c128_df",
+             "add_slice", "add_cluster", "add_walk"}
+
+
 def _path(prof):
     """'emulated' or 'simulated' from the kernels a call launched."""
-    names = set(prof)
-    return "emulated" if names & {"fft_pass", "add_slice", "add_cluster", "add_walk"} else "simulated"
+    return "emulated" if set(prof) & _EMULATED else "simulated"
 
 
 def evaluate_decisions(n, cases, model, dtype="c128", reps=2):

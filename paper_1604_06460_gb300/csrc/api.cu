@@ -853,6 +853,92 @@ int qe_probs(qe_state* s, int m, const int* qubits, double* out) {
     QE_API_END
 }
 
+int qe_init_identity(qe_state* s, int nsys) {
+    QE_API_BEGIN
+    check_state(s);
+    if (s->dtype != QE_C128) fail(QE_ERR_ARG, "dense matrices are complex128 states");
+    if (nsys < 1 || 2 * nsys != s->n) fail(QE_ERR_ARG, "the state must have 2 nsys qubits");
+    s->queue.clear();
+    launch_init_identity(s, nsys);
+    QE_API_END
+}
+
+static void check_matrix_state(const qe_state* m, int k) {
+    check_state(m);
+    if (m->dtype != QE_C128 || m->n != 2 * k) fail(QE_ERR_ARG, "matrix states must be complex128 of 2k qubits");
+}
+
+int qe_matmul(qe_state* c, qe_state* a, qe_state* b) {
+    QE_API_BEGIN
+    check_state(c);
+    const int k = c->n / 2;
+    if (c->n % 2 || k < 1) fail(QE_ERR_ARG, "matrix states must have an even number of qubits");
+    check_matrix_state(a, k);
+    check_matrix_state(b, k);
+    if (c == a || c == b || c->d == a->d || c->d == b->d) fail(QE_ERR_ARG, "the product may not overwrite a factor");
+    flush(a);
+    flush(b);
+    flush(c);
+    if (a->stream != c->stream) QE_CUDA(cudaStreamSynchronize(a->stream));
+    if (b->stream != c->stream && b->stream != a->stream) QE_CUDA(cudaStreamSynchronize(b->stream));
+    launch_matmul(c, c->d, a->d, b->d, k);
+    QE_API_END
+}
+
+int qe_qpe_emulate(qe_state* s, int nsys, int b, qe_state* u) {
+    QE_API_BEGIN
+    check_state(s);
+    check_matrix_state(u, nsys);
+    if (s->dtype != QE_C128) fail(QE_ERR_ARG, "phase estimation runs on complex128 states");
+    if (b < 1 || nsys < 1 || nsys + b > s->n) fail(QE_ERR_ARG, "need 1 <= b and nsys + b <= n");
+    if (u == s || u->d == s->d) fail(QE_ERR_ARG, "the matrix state may not be the state");
+    flush(u);
+    flush(s);
+    if (u->stream != s->stream) QE_CUDA(cudaStreamSynchronize(u->stream));
+    // Hadamards on the ancillas [nsys, nsys + b)
+    const double r2 = 1.0 / std::sqrt(2.0);
+    const std::vector<cd> H = {r2, r2, r2, -r2};
+    for (int j = 0; j < b; ++j) {
+        const int q = nsys + j;
+        apply_block(s, 1, &q, H, 0);
+    }
+    // ancilla j controls U^(2^j): the powers by repeated squaring in two
+    // temporary matrices
+    const size_t mbytes = (size_t)16 << (2 * nsys);
+    void* tmp[2] = {nullptr, nullptr};
+    if (b > 1) {
+        for (auto& t : tmp) {
+            cudaError_t e = cudaMalloc(&t, mbytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                if (tmp[0]) cudaFree(tmp[0]);
+                fail(QE_ERR_OOM, "no room for the matrix powers");
+            }
+        }
+    }
+    try {
+        const void* cur = u->d;
+        for (int j = 0; j < b; ++j) {
+            launch_dense_controlled(s, cur, nsys, nsys + j);
+            if (j + 1 < b) {
+                void* next = tmp[j & 1];
+                launch_matmul(s, next, cur, cur, nsys);
+                cur = next;
+            }
+        }
+        launch_qft_fft(s, nsys, b, 1);
+        QE_CUDA(cudaStreamSynchronize(s->stream));
+    } catch (...) {
+        cudaStreamSynchronize(s->stream);
+        for (auto t : tmp)
+            if (t) cudaFree(t);
+        throw;
+    }
+    for (auto t : tmp)
+        if (t) cudaFree(t);
+    QE_API_END
+}
+
 int qe_sample(qe_state* s, int m, const int* qubits, int nshots, const double* uniforms, uint64_t* outcomes) {
     QE_API_BEGIN
     check_state(s);

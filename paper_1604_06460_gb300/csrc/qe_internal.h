@@ -156,6 +156,13 @@ void reduce_probs(qe_state* s, int m, const int* qubits, double* out);
 uint64_t probs_partials_needed(const qe_state* s, int m);
 void reduce_probs_device(qe_state* s, int m, const int* qubits, double2* partial, double* dout);
 
+// phase estimation (Sec. III-C): identity matrix in a 2 nsys-qubit state,
+// column-major complex products (FP64), a dense matrix applied to the system
+// register [0, nsys) of the rows whose qubit ctrl is set
+void launch_init_identity(qe_state* s, int nsys);
+void launch_matmul(qe_state* acct, void* c, const void* a, const void* b, int k);
+void launch_dense_controlled(qe_state* s, const void* mat, int nsys, int ctrl);
+
 // measurement (Sec. II): inverse-CDF sampling with caller-given uniforms, and
 // the collapse onto an outcome
 void sample_shots(qe_state* s, int m, const int* qubits, int nshots, const double* u, uint64_t* out);

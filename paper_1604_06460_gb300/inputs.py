@@ -177,3 +177,17 @@ def random_state(n, seed):
 
 def random_constant(m, seed):
     return int(np.random.default_rng(seed).integers(0, 1 << m))
+
+
+def tfim_trotter_step(n, dt=0.1, J=1.0, h=0.7):
+    """One Trotter step of the 1-D transverse-field Ising time evolution as
+    G = 4n - 3 gates: for every bond (i, i+1) a CNOT, RZ(2 J dt) on i+1 and
+    the CNOT again, then RX(2 h dt) on every qubit (the operator of the
+    phase-estimation timings, with G = 29 .. 53 for n = 8 .. 14)."""
+    gates = []
+    for i in range(n - 1):
+        gates += [cnot(i, i + 1), single(i + 1, mat_rz(2 * J * dt), "rz"), cnot(i, i + 1)]
+    c, sn = np.cos(h * dt), np.sin(h * dt)
+    rx = np.array([[c, -1j * sn], [-1j * sn, c]])
+    gates += [single(q, rx, "rx") for q in range(n)]
+    return gates

@@ -56,6 +56,9 @@ SIGNATURES = {
     "qe_probs": (_i, [_vp, _i, _vp, _vp]),
     "qe_norm2": (_i, [_vp, _vp]),
     "qe_sample": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
+    "qe_init_identity": (_i, [_vp, _i]),
+    "qe_matmul": (_i, [_vp, _vp, _vp]),
+    "qe_qpe_emulate": (_i, [_vp, _i, _i, _vp]),
     "qe_collapse": (_i, [_vp, _i, _vp, _u64, _vp]),
     "qe_flush": (_i, [_vp]),
     "qe_sync": (_i, [_vp]),
@@ -271,6 +274,19 @@ class State:
             q = _i32(qubits)
             _check(load().qe_sample(self._h, q.size, _ptr(q), u.size, _ptr(u), _ptr(out)))
         return out
+
+    def init_identity(self, nsys):
+        """The identity matrix of 2^nsys x 2^nsys, column-major (qe_init_identity)."""
+        _check(load().qe_init_identity(self._h, int(nsys)))
+
+    def matmul(self, a, b):
+        """self = a b for matrix states (qe_matmul)."""
+        _check(load().qe_matmul(self._h, a._h, b._h))
+
+    def qpe_emulate(self, nsys, b, u):
+        """Phase estimation with b ancillas above the nsys system qubits, U
+        held in the matrix state u (qe_qpe_emulate)."""
+        _check(load().qe_qpe_emulate(self._h, int(nsys), int(b), u._h))
 
     def collapse(self, qubits, outcome):
         """Collapse onto the outcome of measuring qubits; returns its probability."""

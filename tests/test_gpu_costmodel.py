@@ -113,8 +113,8 @@ def test_learned_subroutine_choice_is_emulation(qe):
         st.apply_qft(0, n)
         launches = st.stats()["launches"]
         got = st.get()
-    # emulation: a few FFT passes instead of n + n(n-1)/2 gate passes
-    assert launches < 10
+    # emulation: a few FFT or digit passes instead of n + n(n-1)/2 gate passes
+    assert launches < 20
     # the result equals the transform computed by the other path
     with qe.State(n, "c128") as st2:
         st2.set(psi)
