@@ -67,11 +67,16 @@ def parse():
 
 # small single-kernel workloads for ncu captures: (dtype, n, what)
 KERNEL_CASES = {
-    "tc128": "complex128 5-qubit block on qubits (3,7,11,15,19) of a 24-qubit state, 3 passes",
+    "tc128": "complex128 5-qubit block on qubits (3,7,11,15,19) of a 24-qubit state, FP64 mode (7 digits), 3 passes",
+    "tc128df": "complex128 5-qubit block on qubits (3,7,11,15,19) of a 24-qubit state, double-float mode (6 digits), "
+               "3 passes",
     "tc64": "complex64 5-qubit block on qubits (3,7,11,15,19) of a 26-qubit state, 3 passes",
     "direct2": "complex128 2-qubit block on qubits (5,17) of a 26-qubit state (fusion width 2), 3 passes",
-    "expect": "TFIM energy of a 26-qubit complex128 state, 2 evaluations",
-    "fft": "emulated 26-qubit QFT of a complex128 state, 2 transforms",
+    "expect": "TFIM energy of a 26-qubit complex128 state, FP64 mode, 2 evaluations",
+    "expectdf": "TFIM energy of a 26-qubit complex128 state, double-float mode, 2 evaluations",
+    "fft": "emulated 25-qubit QFT of a complex128 state, FP64 mode (5-qubit digit passes), 2 transforms",
+    "fftdf": "emulated 26-qubit QFT of a complex128 state, double-float mode (radix-2 shared-memory passes), "
+             "2 transforms",
 }
 
 
@@ -85,8 +90,11 @@ def run_kernel_case(qe, I, which):
         q, r = np.linalg.qr(z)
         return q * (np.diag(r) / abs(np.diag(r)))[None, :]
 
-    if which in ("tc128", "tc64"):
-        with qe.State(24 if which == "tc128" else 26, "c128" if which == "tc128" else "c64") as st:
+    df = which.endswith("df")
+    if which in ("tc128", "tc128df", "tc64"):
+        with qe.State(26 if which == "tc64" else 24, "c64" if which == "tc64" else "c128") as st:
+            if df:
+                st.set_arith(qe.ARITH_DF64)
             st.set_policy(qe.POLICY_AUTO, 5)
             st.init_random(3)
             U = unitary(32)
@@ -101,18 +109,23 @@ def run_kernel_case(qe, I, which):
             for _ in range(3):
                 st.apply_gate([5, 17], U)
                 st.flush()
-    elif which == "expect":
+    elif which in ("expect", "expectdf"):
         with qe.State(26, "c128") as st:
+            if df:
+                st.set_arith(qe.ARITH_DF64)
             st.init_random(2)
             xm, zm, cf = I.tfim_terms(26)
             for _ in range(2):
                 st.expectation(xm, zm, cf)
     else:
-        with qe.State(26, "c128") as st:
+        n = 26 if df else 25
+        with qe.State(n, "c128") as st:
+            if df:
+                st.set_arith(qe.ARITH_DF64)
             st.set_policy(qe.POLICY_EMULATE, 1)
             st.init_random(2)
             for _ in range(2):
-                st.apply_qft(0, 26)
+                st.apply_qft(0, n)
     torch.cuda.synchronize()
     print(json.dumps({"kernel_case": which, "workload": KERNEL_CASES[which]}), flush=True)
 
@@ -296,6 +309,8 @@ def peak_hbm():
 # only these, so an edit elsewhere keeps the counters valid).
 KERNEL_SOURCES = {
     "gate_tc_k5_c128": ["tc_c128.cu", "qe_tc.cuh", "qe_arith.cuh"],
+    "fft_twiddle": ["fft.cu", "qe_arith.cuh"],
+    "digitrev": ["fft.cu", "qe_arith.cuh"],
     "gate_tc_k5": ["tcgen05.cu", "qe_tc.cuh", "qe_arith.cuh"],
     "gate_direct": ["gates.cu", "qe_arith.cuh"],
     "expect": ["reduce.cu", "qe_arith.cuh"],
