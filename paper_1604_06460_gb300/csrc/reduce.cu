@@ -423,10 +423,24 @@ __global__ void __launch_bounds__(kRThreads) k_expect_tile(const __grid_constant
                 if (k >= a.nxt) break;
                 const uint32_t xl = a.xloc[k], below = a.xbelow[k];
                 const uint32_t l = ((i & ~below) << 1) | (i & below);
-                V w = tile[l ^ xl];
-                const V v = tile[l];
-                if (a.xsigned[k] && ((__popc(l & a.xzl[k]) ^ (xflip >> k)) & 1u)) w = vneg(w);
-                corr_acc(xacc[k], w, v, a.ximag[k] != 0);
+                const bool flip = a.xsigned[k] && ((__popc(l & a.xzl[k]) ^ (xflip >> k)) & 1u);
+                if constexpr (NAT) {
+                    // Re or Im of conj(w) v as w.x p + w.y q, the operands
+                    // chosen and signed with integer selects, so that the FP64
+                    // pipe runs exactly two fused multiply-adds per pair
+                    const double2 w = tile[l ^ xl], v = tile[l];
+                    const bool im = a.ximag[k] != 0;
+                    const unsigned long long sgn = flip ? 0x8000000000000000ull : 0ull;
+                    const unsigned long long vx = __double_as_longlong(v.x), vy = __double_as_longlong(v.y);
+                    const double p = __longlong_as_double((im ? vy : vx) ^ sgn);
+                    const double q = __longlong_as_double((im ? (vx ^ 0x8000000000000000ull) : vy) ^ sgn);
+                    xacc[k].s = __fma_rn(w.x, p, __fma_rn(w.y, q, xacc[k].s));
+                } else {
+                    V w = tile[l ^ xl];
+                    const V v = tile[l];
+                    if (flip) w = vneg(w);
+                    corr_acc(xacc[k], w, v, a.ximag[k] != 0);
+                }
             }
         }
         __syncthreads();
