@@ -13,6 +13,7 @@
 // FP64 (53-bit significands) instead, with the same FP64 compensated
 // combination of the block partials.
 #include <algorithm>
+#include <cstdlib>
 #include <type_traits>
 #include <vector>
 
@@ -24,6 +25,15 @@ namespace qe {
 namespace {
 
 constexpr int kRThreads = 256;
+
+// Expectation kernel choice (a test and measurement switch, read per call):
+// QE_EXPECT_TILE=1 keeps every expectation on the pair-indexed tile kernel,
+// =2 takes the register-round kernel whenever the terms fit it; otherwise it
+// is taken when it needs no more launches.
+int expect_kernel_switch() {
+    const char* e = std::getenv("QE_EXPECT_TILE");
+    return (e && (e[0] == '1' || e[0] == '2')) ? e[0] - '0' : 0;
+}
 
 // ------------------------------------------------ compensated accumulators
 struct Acc {
@@ -477,6 +487,310 @@ __global__ void __launch_bounds__(kRThreads) k_expect_tile(const __grid_constant
     if (tid == 0) a.partial[blockIdx.x] = make_double2(s, c);
 }
 
+// ------------------------------------- expectation by register rounds
+// Tiles of 2^12 amplitudes (the chunk bits [0, L) plus 12 - L high qubits),
+// 512 threads, eight amplitudes a thread at a time.  The tile's local bits
+// form four triples {0,1,2}, {3,4,5}, {6,7,8}, {9,10,11}; in round r a thread
+// holds the eight amplitudes that differ only in triple r (its other nine
+// local bits come from the thread index), so a term whose X/Y bits lie in
+// triple r pairs two of those registers: no index arithmetic and one shared
+// load per amplitude and round.  Z-only masks are counted in round 0 from
+// per-mask parity bytes (bit j: the parity of amplitude j), summed bytewise.
+// All X/Y terms of a launch share one weight, so one accumulator serves them.
+// Shared tiles are XOR-swizzled so that every round's loads are free of bank
+// conflicts; three tile buffers keep two tiles in flight (cp.async).
+constexpr int kT2 = 12, kThr2 = 512, kXT2 = 24, kNB2 = 3;
+
+template <class S>
+struct RoundArgs {
+    const S* x;
+    uint64_t ntiles;
+    int L, kh;
+    uint8_t hq[8];            // local bit L + j <-> qubit hq[j]
+    uint8_t hq_sorted[8];     // the same qubits ascending (tile base)
+    int nzg, nz;
+    int zg_end[kZW];          // group g: Z masks [zg_end[g - 1], zg_end[g])
+    double zw[kZW];
+    uint32_t zl[kZT];         // tile-local bits of Z mask m
+    uint64_t zo[kZT];         // its bits outside the tile
+    uint8_t zpz[kZT];         // bit j: parity of j & (its bits in triple 0)
+    int rb[5];                // round r: X/Y terms [rb[r], rb[r + 1])
+    int nxt;
+    uint32_t xw[kXT2];        // bits 0-2: X bits in the round's triple; 3-10: bit j = parity of j & the
+                              // term's Z bits in the triple; 11: Im part; 12: negated (i^ny); 13: has a
+                              // Z part (a sign per pair)
+    uint32_t xzl[kXT2];       // the term's Z bits at tile-local positions
+    uint64_t xzo[kXT2];       // and outside the tile
+    double wx;                // 2 x the common coefficient of the X/Y terms
+    double2* partial;
+};
+
+template <int EB>
+__device__ __forceinline__ uint32_t swz(uint32_t l) {
+    if constexpr (EB == 16) return l ^ ((l >> 3) & 7u);
+    else return l ^ ((l >> 4) & 7u) ^ ((l >> 3) & 8u);
+}
+
+// tile-local index of a thread's amplitude 0 in round r (triple r zero)
+__device__ __forceinline__ uint32_t round_base(uint32_t tid, int r) {
+    const int s = 3 * r;
+    return (tid & ((1u << s) - 1u)) | ((tid >> s) << (s + 3));
+}
+
+// acc += (-1)^neg Re (IM = false) or Im (IM = true) of conj(w) v; SIGNED =
+// false: no per-pair sign (neg is ignored).  FP64: the sign enters as an
+// integer XOR of the operands' sign bits, so the FP64 pipe runs exactly two
+// fused multiply-adds per pair.
+template <bool IM, bool SIGNED>
+__device__ __forceinline__ void pair_acc(AccD& acc, const double2& w, const double2& v, uint32_t neg) {
+    double p = IM ? v.y : v.x, q = IM ? v.x : v.y;
+    double wy = w.y;
+    if constexpr (SIGNED) {
+        const long long sgn = (long long)neg << 63;
+        p = __longlong_as_double(__double_as_longlong(p) ^ sgn);
+        q = __longlong_as_double(__double_as_longlong(q) ^ sgn);
+    }
+    if constexpr (IM) acc.s = __fma_rn(w.x, p, __fma_rn(-wy, q, acc.s));
+    else acc.s = __fma_rn(w.x, p, __fma_rn(wy, q, acc.s));
+}
+template <bool IM, bool SIGNED, class V>
+__device__ __forceinline__ void pair_acc(Acc& acc, const V& w, const V& v, uint32_t neg) {
+    if constexpr (SIGNED) corr_acc(acc, neg ? vneg(w) : w, v, IM);
+    else corr_acc(acc, w, v, IM);
+}
+
+// the four pairs (j, j ^ XT) with the lowest bit of XT clear in j
+template <int XT, bool IM, bool SIGNED, class V, class A>
+__device__ __forceinline__ void round_pairs(const V (&v)[8], uint32_t zp, uint32_t f, A& acc) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        if (j & (XT & -XT)) continue;
+        pair_acc<IM, SIGNED>(acc, v[j ^ XT], v[j], f ^ ((zp >> j) & 1u));
+    }
+}
+
+// One term: XT, Im and whether it carries a Z part select the code path
+// (uniform across the block); in FP64 a term without Z part has one sign for
+// all its pairs and accumulates into xacc or, negated, into xneg (the
+// float-pair paths sign each pair with selects).
+template <int XT, class V, class A>
+__device__ __forceinline__ void round_term(const V (&v)[8], uint32_t zp, uint32_t f, bool im, bool signed_term,
+                                           A& xacc, A& xneg) {
+    if constexpr (!std::is_same<A, AccD>::value) {
+        if (im) round_pairs<XT, true, true>(v, zp, f, xacc);
+        else round_pairs<XT, false, true>(v, zp, f, xacc);
+        return;
+    }
+    if (signed_term) {
+        if (im) round_pairs<XT, true, true>(v, zp, f, xacc);
+        else round_pairs<XT, false, true>(v, zp, f, xacc);
+    } else if (f) {
+        if (im) round_pairs<XT, true, false>(v, 0u, 0u, xneg);
+        else round_pairs<XT, false, false>(v, 0u, 0u, xneg);
+    } else {
+        if (im) round_pairs<XT, true, false>(v, 0u, 0u, xacc);
+        else round_pairs<XT, false, false>(v, 0u, 0u, xacc);
+    }
+}
+
+template <class S, bool NAT>
+__global__ void __launch_bounds__(kThr2, 1) k_expect_rounds(const __grid_constant__ RoundArgs<S> a) {
+    using V = std::conditional_t<NAT, S, decltype(rview(S{}))>;
+    using A = std::conditional_t<NAT, AccD, Acc>;
+    using W = std::conditional_t<NAT, double, float>;
+    constexpr int EB = (int)sizeof(S);
+    constexpr uint32_t Tn = 1u << kT2;
+    static_assert(sizeof(V) == sizeof(S), "tiles are converted in place");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* const tiles = reinterpret_cast<V*>(smem_raw);
+    __shared__ Acc sh[32];
+    __shared__ double shd[32];
+    __shared__ uint64_t offA[64];
+    __shared__ uint64_t spread[256];          // byte j of spread[p] = bit j of p
+    __shared__ W s_cnt[kZW][kZT + 1];         // group g, o odd masks: (masks of g) - 2 o
+    __shared__ uint64_t s_zbits;              // bit m: outside parity of Z mask m (this tile)
+    __shared__ uint32_t s_xbits;              // bit k: outside parity of term k's Z bits
+    const uint32_t tid = threadIdx.x;
+    if (tid < 64) {
+        uint64_t o = 0;
+        for (int j = 0; j < a.kh; ++j)
+            if ((tid >> j) & 1u) o |= 1ull << a.hq[j];
+        offA[tid] = o;
+    }
+    if (tid < 256) {
+        uint64_t sp = 0;
+        for (int j = 0; j < 8; ++j) sp |= (uint64_t)((tid >> j) & 1u) << (8 * j);
+        spread[tid] = sp;
+    }
+    for (uint32_t i = tid; i < (uint32_t)(kZW * (kZT + 1)); i += blockDim.x) {
+        const int g = (int)i / (kZT + 1), o = (int)i % (kZT + 1);
+        const int ng = g < a.nzg ? a.zg_end[g] - (g ? a.zg_end[g - 1] : 0) : 0;
+        s_cnt[g][o] = (W)(ng - 2 * o);
+    }
+    // parities of the thread's part of each mask (fixed for the launch)
+    uint64_t tz = 0;
+    {
+        const uint32_t lt0 = round_base(tid, 0);
+        for (int m = 0; m < a.nz; ++m) tz |= (uint64_t)(__popc(lt0 & a.zl[m]) & 1) << m;
+    }
+    uint32_t tx = 0;
+    for (int r = 0; r < 4; ++r) {
+        const uint32_t lt = round_base(tid, r);
+        for (int k = a.rb[r]; k < a.rb[r + 1]; ++k) tx |= (uint32_t)(__popc(lt & a.xzl[k]) & 1) << k;
+    }
+    A zacc[kZW], xacc, xneg;
+#pragma unroll
+    for (int g = 0; g < kZW; ++g) acc_zero(zacc[g]);
+    acc_zero(xacc);
+    acc_zero(xneg);
+    __syncthreads();
+    const uint32_t lowmask = (1u << a.L) - 1u;
+    auto load = [&](uint64_t t, V* buf) {
+        const uint64_t b = insert_zero_bits(t << a.L, a.hq_sorted, a.kh);
+#pragma unroll
+        for (int i = 0; i < (int)(Tn / kThr2); ++i) {
+            const uint32_t l = tid + (uint32_t)i * kThr2;
+            async_copy<EB>(buf + swz<EB>(l), a.x + (b + (l & lowmask) + offA[l >> a.L]));
+        }
+    };
+    const uint64_t step = gridDim.x;
+#pragma unroll
+    for (int s = 0; s < kNB2 - 1; ++s) {
+        const uint64_t t = blockIdx.x + (uint64_t)s * step;
+        if (t < a.ntiles) load(t, tiles + (size_t)s * Tn);
+        asm volatile("cp.async.commit_group;");
+    }
+    int it = 0;
+    for (uint64_t t = blockIdx.x; t < a.ntiles; t += step, ++it) {
+        V* const tile = tiles + (size_t)(it % kNB2) * Tn;
+        asm volatile("cp.async.wait_group %0;" ::"n"(kNB2 - 2) : "memory");
+        if constexpr (sizeof(S) == 16 && !NAT) {   // complex128: split into double-float in place
+#pragma unroll
+            for (int i = 0; i < (int)(Tn / kThr2); ++i) {
+                const uint32_t p = swz<EB>(tid + (uint32_t)i * kThr2);
+                tile[p] = rview(*reinterpret_cast<const S*>(tile + p));
+            }
+        }
+        if (tid < 32) {   // outside parities of this tile
+            const uint64_t base = insert_zero_bits(t << a.L, a.hq_sorted, a.kh);
+            const int lane = (int)tid;
+            const uint32_t p0 = (lane < a.nz) ? (uint32_t)(__popcll(base & a.zo[lane]) & 1) : 0u;
+            const uint32_t p1 = (lane + 32 < a.nz) ? (uint32_t)(__popcll(base & a.zo[lane + 32]) & 1) : 0u;
+            const uint32_t px = (lane < a.nxt) ? (uint32_t)(__popcll(base & a.xzo[lane]) & 1) : 0u;
+            const uint32_t b0 = __ballot_sync(0xffffffffu, p0), b1 = __ballot_sync(0xffffffffu, p1);
+            const uint32_t xb = __ballot_sync(0xffffffffu, px);
+            if (lane == 0) {
+                s_zbits = ((uint64_t)b1 << 32) | b0;
+                s_xbits = xb;
+            }
+        }
+        __syncthreads();
+        {
+            const uint64_t tn = t + (uint64_t)(kNB2 - 1) * step;
+            if (tn < a.ntiles) load(tn, tiles + (size_t)((it + kNB2 - 1) % kNB2) * Tn);
+            asm volatile("cp.async.commit_group;");
+        }
+        const uint64_t zbits = tz ^ s_zbits;
+        const uint32_t xflip = tx ^ s_xbits;
+#pragma unroll 1
+        for (int r = 0; r < 4; ++r) {
+            const bool zr = (r == 0) && (a.nzg > 0);
+            const int k0 = a.rb[r], k1 = a.rb[r + 1];
+            if (k0 == k1 && !zr) continue;
+            const uint32_t lt = round_base(tid, r);
+            V v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = tile[swz<EB>(lt | ((uint32_t)j << (3 * r)))];
+            if (zr) {
+                uint64_t cnt[kZW];
+                int m = 0;
+#pragma unroll
+                for (int g = 0; g < kZW; ++g) {
+                    cnt[g] = 0;
+                    if (g >= a.nzg) continue;
+                    for (; m < a.zg_end[g]; ++m) {
+                        const uint32_t pat = a.zpz[m] ^ ((uint32_t)((zbits >> m) & 1ull) * 0xFFu);
+                        cnt[g] += spread[pat];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if constexpr (NAT) {
+                        const double pd = abs2d(v[j]);
+#pragma unroll
+                        for (int g = 0; g < kZW; ++g) {
+                            if (g >= a.nzg) break;
+                            zacc[g].s = __fma_rn(pd, s_cnt[g][(cnt[g] >> (8 * j)) & 0xFFu], zacc[g].s);
+                        }
+                    } else {
+                        float ph, pl;
+                        abs2(v[j], ph, pl);
+#pragma unroll
+                        for (int g = 0; g < kZW; ++g) {
+                            if (g >= a.nzg) break;
+                            const float f = s_cnt[g][(cnt[g] >> (8 * j)) & 0xFFu];
+                            const float p = fmul(ph, f);
+                            acc_add(zacc[g], p, __fmaf_rn(pl, f, __fmaf_rn(ph, f, -p)));
+                        }
+                    }
+                }
+            }
+            for (int k = k0; k < k1; ++k) {
+                const uint32_t w = a.xw[k];
+                const uint32_t f = ((xflip >> k) & 1u) ^ ((w >> 12) & 1u);
+                const uint32_t zp = (w >> 3) & 0xFFu;
+                const bool im = ((w >> 11) & 1u) != 0, sg = ((w >> 13) & 1u) != 0;
+                switch (w & 7u) {
+                    case 1: round_term<1>(v, zp, f, im, sg, xacc, xneg); break;
+                    case 2: round_term<2>(v, zp, f, im, sg, xacc, xneg); break;
+                    case 3: round_term<3>(v, zp, f, im, sg, xacc, xneg); break;
+                    case 4: round_term<4>(v, zp, f, im, sg, xacc, xneg); break;
+                    case 5: round_term<5>(v, zp, f, im, sg, xacc, xneg); break;
+                    case 6: round_term<6>(v, zp, f, im, sg, xacc, xneg); break;
+                    default: round_term<7>(v, zp, f, im, sg, xacc, xneg); break;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    double s = 0.0, c = 0.0;
+#pragma unroll
+    for (int g = 0; g < kZW; ++g) {
+        if (g >= a.nzg) break;
+        if constexpr (NAT) {
+            const double r = block_reduce_d(zacc[g].s, shd);
+            if (tid == 0) neumaier(s, c, r * a.zw[g]);
+        } else {
+            Acc r = block_reduce(zacc[g], sh);
+            if (tid == 0) {
+                df d = df_norm(r.s, r.e);
+                neumaier(s, c, df2d(d.h, d.l) * a.zw[g]);
+            }
+        }
+    }
+    if (a.nxt > 0) {
+        if constexpr (NAT) {
+            const double r = block_reduce_d(xacc.s, shd);
+            if (tid == 0) neumaier(s, c, r * a.wx);
+            const double rn = block_reduce_d(xneg.s, shd);
+            if (tid == 0) neumaier(s, c, -rn * a.wx);
+        } else {
+            Acc r = block_reduce(xacc, sh);
+            if (tid == 0) {
+                df d = df_norm(r.s, r.e);
+                neumaier(s, c, df2d(d.h, d.l) * a.wx);
+            }
+            r = block_reduce(xneg, sh);
+            if (tid == 0) {
+                df d = df_norm(r.s, r.e);
+                neumaier(s, c, -df2d(d.h, d.l) * a.wx);
+            }
+        }
+    }
+    if (tid == 0) a.partial[blockIdx.x] = make_double2(s, c);
+}
+
 // Native FP64 variants (baseline policy).
 __global__ void __launch_bounds__(kRThreads) k_probs_partial_f64(const __grid_constant__ ProbArgs<double2> a) {
     __shared__ double shs[32], shc[32];
@@ -637,6 +951,215 @@ __global__ void __launch_bounds__(kRThreads) k_expect_wide(const __grid_constant
     if (threadIdx.x == 0) a.partial[blockIdx.x] = make_double2(s, c);
 }
 
+// Launches of the register-round kernel: layout 0 (qubits [0, 12)) and
+// layouts of six high qubits above the chunk bits [0, 6), two triples each;
+// one launch per layout and common X/Y weight (at most kXT2 terms), the Z-only
+// groups on layout 0.  False when a term does not fit: X/Y bits below qubit
+// 12 outside one triple, three or more high X/Y bits, or both kinds at once.
+struct RoundLaunch {
+    std::vector<int> hq;                                  // high qubits, local order (empty: layout 0)
+    std::vector<std::pair<int, int>> x;                   // (term, round), ascending rounds
+    std::vector<std::pair<int, std::vector<int>>> z;      // (weight group, Z masks)
+    double wx = 0.0;
+};
+
+bool plan_rounds(int n, int nterms, const uint64_t* xm, const double* cf,
+                 const std::vector<std::pair<int, std::vector<int>>>& zchunks, std::vector<RoundLaunch>& out) {
+    out.clear();
+    if (n < kT2) return false;
+    const uint64_t lowq = (1ull << kT2) - 1ull;
+    std::vector<std::pair<int, int>> low;
+    std::vector<int> high;
+    for (int t = 0; t < nterms; ++t) {
+        if (xm[t] == 0) continue;
+        if ((xm[t] & ~lowq) == 0) {
+            int r = -1;
+            for (int q = 0; q < 4; ++q)
+                if ((xm[t] & ~(7ull << (3 * q))) == 0) r = q;
+            if (r < 0) return false;
+            low.push_back({t, r});
+        } else if ((xm[t] & lowq) == 0 && __builtin_popcountll(xm[t]) <= 3) {
+            high.push_back(t);
+        } else {
+            return false;
+        }
+    }
+    // high qubits grouped into triples, each term inside one
+    std::vector<uint64_t> trip;
+    std::vector<int> trip_of(high.size());
+    for (size_t i = 0; i < high.size(); ++i) {
+        const uint64_t q = xm[high[i]];
+        int f = -1;
+        for (size_t j = 0; j < trip.size() && f < 0; ++j)
+            if ((trip[j] & q) == q) f = (int)j;
+        for (size_t j = 0; j < trip.size() && f < 0; ++j)
+            if (__builtin_popcountll(trip[j] | q) <= 3) f = (int)j;
+        if (f < 0) {
+            trip.push_back(0ull);
+            f = (int)trip.size() - 1;
+        }
+        trip[f] |= q;
+        trip_of[i] = f;
+    }
+    struct Lay {
+        std::vector<int> hq;
+        std::vector<std::pair<int, int>> x;
+    };
+    // pair disjoint triples into layouts (triples that share a qubit may not
+    // sit in one layout)
+    std::vector<Lay> lays(1);
+    lays[0].x = low;
+    std::vector<int> lay_of(trip.size(), -1), round_of(trip.size(), 2);
+    for (size_t j = 0; j < trip.size(); ++j) {
+        if (lay_of[j] >= 0) continue;
+        int mate = -1;
+        for (size_t k = j + 1; k < trip.size() && mate < 0; ++k)
+            if (lay_of[k] < 0 && (trip[k] & trip[j]) == 0) mate = (int)k;
+        Lay ly;
+        int pad = 6;   // fill short triples with qubits of [6, 12), never high-term qubits
+        for (int h = 0; h < 2; ++h) {
+            const uint64_t tq = h == 0 ? trip[j] : (mate >= 0 ? trip[mate] : 0ull);
+            int c = 0;
+            for (int q = 0; q < n; ++q)
+                if ((tq >> q) & 1ull) {
+                    ly.hq.push_back(q);
+                    ++c;
+                }
+            for (; c < 3; ++c) ly.hq.push_back(pad++);
+        }
+        lay_of[j] = (int)lays.size();
+        if (mate >= 0) {
+            lay_of[mate] = (int)lays.size();
+            round_of[mate] = 3;
+        }
+        lays.push_back(ly);
+    }
+    for (size_t i = 0; i < high.size(); ++i) lays[lay_of[trip_of[i]]].x.push_back({high[i], round_of[trip_of[i]]});
+    size_t zi = 0;
+    for (size_t li = 0; li < lays.size(); ++li) {
+        std::vector<double> ws;
+        for (const auto& tr : lays[li].x)
+            if (std::find(ws.begin(), ws.end(), 2.0 * cf[tr.first]) == ws.end()) ws.push_back(2.0 * cf[tr.first]);
+        std::vector<RoundLaunch> mine;
+        for (double w : ws) {
+            std::vector<std::pair<int, int>> xs;
+            for (const auto& tr : lays[li].x)
+                if (2.0 * cf[tr.first] == w) xs.push_back(tr);
+            std::stable_sort(xs.begin(), xs.end(),
+                             [](const std::pair<int, int>& p, const std::pair<int, int>& q) { return p.second < q.second; });
+            for (size_t i = 0; i < xs.size(); i += kXT2) {
+                RoundLaunch R;
+                R.hq = lays[li].hq;
+                R.wx = w;
+                R.x.assign(xs.begin() + i, xs.begin() + std::min(xs.size(), i + kXT2));
+                mine.push_back(R);
+            }
+        }
+        if (li == 0) {
+            size_t k = 0;
+            while (zi < zchunks.size()) {
+                if (k == mine.size()) mine.push_back(RoundLaunch{});
+                RoundLaunch& R = mine[k++];
+                int masks = 0;
+                while (zi < zchunks.size() && (int)R.z.size() < kZW &&
+                       masks + (int)zchunks[zi].second.size() <= kZT) {
+                    masks += (int)zchunks[zi].second.size();
+                    R.z.push_back(zchunks[zi++]);
+                }
+            }
+        }
+        for (auto& R : mine) out.push_back(std::move(R));
+    }
+    return true;
+}
+
+template <class S, bool NAT>
+double expect_rounds(qe_state* s, const std::vector<RoundLaunch>& rl, const uint64_t* xm, const uint64_t* zm,
+                     const std::vector<double>& wv) {
+    using V = std::conditional_t<NAT, S, decltype(rview(S{}))>;
+    const int n = s->n;
+    const size_t smem = (size_t)kNB2 * (sizeof(V) << kT2);
+    QE_CUDA(cudaFuncSetAttribute(k_expect_rounds<S, NAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    QE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_expect_rounds<S, NAT>, kThr2, smem));
+    const uint64_t ntiles = 1ull << (n - kT2);
+    const unsigned grid = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)num_sms() * std::max(occ, 1));
+    char* scr = (char*)ensure_scratch(s, rl.size() * grid * sizeof(double2) + 64);
+    double2* partial = (double2*)scr;
+    double* dout = (double*)(scr + rl.size() * grid * sizeof(double2));
+    auto pattern = [](uint32_t bits3) {   // bit j: parity of j & bits3
+        uint32_t p = 0;
+        for (uint32_t j = 0; j < 8; ++j) p |= (uint32_t)(__builtin_popcount(j & bits3) & 1) << j;
+        return p;
+    };
+    static thread_local RoundArgs<S> a;
+    for (size_t i = 0; i < rl.size(); ++i) {
+        const RoundLaunch& R = rl[i];
+        a = RoundArgs<S>{};
+        a.x = reinterpret_cast<const S*>(s->d);
+        a.ntiles = ntiles;
+        a.kh = (int)R.hq.size();
+        a.L = kT2 - a.kh;
+        std::vector<int> so(R.hq);
+        std::sort(so.begin(), so.end());
+        for (int j = 0; j < a.kh; ++j) {
+            a.hq[j] = (uint8_t)R.hq[j];
+            a.hq_sorted[j] = (uint8_t)so[j];
+        }
+        uint64_t inside = (1ull << a.L) - 1ull;
+        for (int q : R.hq) inside |= 1ull << q;
+        auto to_local = [&](uint64_t m) {
+            uint32_t loc = (uint32_t)(m & ((1ull << a.L) - 1ull));
+            for (int h = 0; h < a.kh; ++h)
+                if ((m >> R.hq[h]) & 1ull) loc |= 1u << (a.L + h);
+            return loc;
+        };
+        a.nzg = (int)R.z.size();
+        int k = 0;
+        for (int g = 0; g < a.nzg; ++g) {
+            a.zw[g] = wv[R.z[g].first];
+            for (int t : R.z[g].second) {
+                a.zl[k] = to_local(zm[t]);
+                a.zo[k] = zm[t] & ~inside;
+                a.zpz[k] = (uint8_t)pattern(a.zl[k] & 7u);
+                ++k;
+            }
+            a.zg_end[g] = k;
+        }
+        a.nz = k;
+        a.nxt = (int)R.x.size();
+        int per[4] = {0, 0, 0, 0};
+        for (const auto& tr : R.x) ++per[tr.second];
+        a.rb[0] = 0;
+        for (int r = 0; r < 4; ++r) a.rb[r + 1] = a.rb[r] + per[r];
+        for (int j = 0; j < a.nxt; ++j) {
+            const int t = R.x[j].first, r = R.x[j].second;
+            const uint32_t xl = to_local(xm[t]), zl = to_local(zm[t]);
+            const uint32_t xt = (xl >> (3 * r)) & 7u;
+            if (xt == 0 || (xl & ~(7u << (3 * r))) != 0) fail(QE_ERR_STATE, "expectation term outside its round");
+            const int ny = __builtin_popcountll(xm[t] & zm[t]) & 3;
+            a.xw[j] = xt | (pattern((zl >> (3 * r)) & 7u) << 3) | ((uint32_t)(ny & 1) << 11) |
+                      ((uint32_t)(ny == 1 || ny == 2) << 12) | ((uint32_t)(zm[t] != 0) << 13);
+            a.xzl[j] = zl;
+            a.xzo[j] = zm[t] & ~inside;
+        }
+        a.wx = R.wx;
+        a.partial = partial + i * grid;
+        Launch L(s, "expect_rounds", (double)dim(s) * amp_bytes(s));
+        k_expect_rounds<S, NAT><<<grid, kThr2, smem, s->stream>>>(a);
+        QE_CUDA(cudaGetLastError());
+    }
+    {
+        Launch L(s, "sum_partials", 0.0, false);
+        k_sum_partials<<<1, kSumThreads, 0, s->stream>>>(partial, 1, (uint64_t)rl.size() * grid, nullptr, dout);
+        QE_CUDA(cudaGetLastError());
+    }
+    double out = 0.0;
+    QE_CUDA(cudaMemcpyAsync(&out, dout, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    QE_CUDA(cudaStreamSynchronize(s->stream));
+    return out;
+}
+
 template <class S, bool NAT>
 double expect_impl(qe_state* s, int nterms, const uint64_t* xm, const uint64_t* zm, const double* cf) {
     const int n = s->n;
@@ -728,6 +1251,16 @@ double expect_impl(qe_state* s, int nterms, const uint64_t* xm, const uint64_t* 
     }
     const int nwide = (int)((wide.size() + kXT - 1) / kXT);
     if (plans.empty() && nwide == 0) return 0.0;
+    // the register-round kernel when every term fits it, in no more
+    // launches, for the float-pair and complex64 paths (their per-pair cost
+    // is instruction issue, which it cuts by a third); the native FP64 path
+    // is bound by the FP64 pipe either way and measured no faster with it
+    if (const int sw = expect_kernel_switch(); sw != 1 && (sw == 2 || !NAT)) {
+        std::vector<RoundLaunch> rl;
+        if (plan_rounds(n, nterms, xm, cf, zchunks, rl) && !rl.empty() &&
+            (sw == 2 || rl.size() <= plans.size() + (size_t)nwide))
+            return expect_rounds<S, NAT>(s, rl, xm, zm, wv);
+    }
     uint64_t max_grid = (uint64_t)num_sms() * 8;
     std::vector<unsigned> grids(plans.size());
     for (size_t i = 0; i < plans.size(); ++i) {

@@ -422,6 +422,102 @@ def test_tfim_expectation(qe, dtype, arith):
     assert abs(e - ref) < (1e-12 if dtype == "c128" else 1e-5)
 
 
+def _rounds_terms(n, seed, nweights=1):
+    """Terms the register-round kernel takes: X/Y bits below qubit 12 inside
+    one of the triples {0,1,2} .. {9,10,11} (every 3-bit pattern), one to
+    three high X/Y bits, Z parts inside the triple, elsewhere in the tile and
+    outside it; Z-only masks in several weight groups, some entirely outside
+    the tile."""
+    rng = np.random.default_rng(seed)
+    xm, zm, cf = [], [], []
+    wx = [0.35, -1.25][:nweights]
+    for r in range(4):
+        for pat in range(1, 8):
+            xm.append(pat << (3 * r))
+            zm.append(int(rng.integers(0, 1 << n)) if pat % 2 else 0)
+            cf.append(wx[(r + pat) % nweights])
+    for q in range(12, n):
+        xm.append(1 << q); zm.append(0); cf.append(wx[q % nweights])
+    high = [q for q in range(12, n)]
+    for _ in range(6 if high else 0):
+        k = int(rng.integers(1, 4))
+        qs = rng.choice(high, size=k, replace=False)
+        xm.append(int(sum(1 << int(q) for q in qs)))
+        zm.append(int(rng.integers(0, 1 << n)))
+        cf.append(wx[0])
+    for i in range(n - 1):
+        xm.append(0); zm.append((1 << i) | (1 << (i + 1))); cf.append(1.0)
+    for _ in range(10):
+        xm.append(0); zm.append(int(rng.integers(1, 1 << n))); cf.append(-0.5)
+    if n > 12:
+        xm.append(0); zm.append(((1 << (n - 12)) - 1) << 12); cf.append(0.25)   # outside the 12-qubit tile only
+    xm.append(0); zm.append(0b101); cf.append(2.0)                            # triple 0 only
+    return np.array(xm, dtype=np.uint64), np.array(zm, dtype=np.uint64), np.array(cf)
+
+
+@pytest.mark.parametrize("dtype,arith,tol", [("c128", "fp64", 1e-12), ("c128", "df64", 1e-12), ("c64", None, 2e-5)])
+@pytest.mark.parametrize("n,nweights", [(12, 1), (15, 2), (20, 1)])
+def test_expectation_register_rounds(qe, dtype, arith, tol, n, nweights):
+    # the register-round kernel forced on (QE_EXPECT_TILE=2) and off (=1):
+    # both against the oracle, and the forced run must have used it
+    import os
+    xm, zm, cf = _rounds_terms(n, 60 + n, nweights)
+    psi = I.random_state(n, 70 + n)
+    ref = oracle.expectation(psi, xm, zm, cf)
+    got = {}
+    for sw in ("2", "1"):
+        os.environ["QE_EXPECT_TILE"] = sw
+        try:
+            with make(qe, n, dtype, psi=psi, arith=arith) as st:
+                st.profile(True)
+                got[sw] = st.expectation(xm, zm, cf)
+                prof = st.profile_read()
+        finally:
+            os.environ.pop("QE_EXPECT_TILE", None)
+        assert ("expect_rounds" in prof) == (sw == "2"), prof
+    bound = tol if dtype == "c128" else tol * float(np.sum(np.abs(cf)))
+    for sw, e in got.items():
+        assert abs(e - ref) < bound, (sw, e, ref)
+
+
+@pytest.mark.parametrize("dtype,arith", [("c128", "fp64"), ("c128", "df64"), ("c64", None)])
+def test_expectation_rounds_chosen_for_tfim(qe, dtype, arith):
+    # TFIM at n = 24: the float-pair and complex64 paths take 3 launches of
+    # the register-round kernel (qubits [0, 12), then two layouts of six high
+    # qubits) instead of 4 tile ones; the FP64 path keeps the tile kernel;
+    # closed forms on |0..0> and |+..+>
+    n = 24
+    xm, zm, cf = I.tfim_terms(n)
+    with make(qe, n, dtype, arith=arith) as st:
+        st.profile(True)
+        e0 = st.expectation(xm, zm, cf)
+        prof = st.profile_read()
+        if arith == "fp64":
+            assert "expect_rounds" not in prof and prof["expect_tile"][0] == 4, prof
+        else:
+            assert prof["expect_rounds"][0] == 3 and "expect_tile" not in prof, prof
+        for q in range(n):
+            st.apply_gate([q], I.mat_h())
+        e1 = st.expectation(xm, zm, cf)
+    tol = 1e-12 if dtype == "c128" else 1e-5 * n
+    assert abs(e0 - (n - 1)) < tol
+    assert abs(e1 - 0.7 * n) < 10 * tol
+
+
+def test_expectation_rounds_not_chosen_when_terms_do_not_fit(qe):
+    # an X/Y mask across two triples (qubits 2 and 3) goes to the tile kernel
+    n = 14
+    xm, zm, cf = I.tfim_terms(n)
+    xm = np.append(xm, np.uint64(0b1100)); zm = np.append(zm, np.uint64(0)); cf = np.append(cf, 0.3)
+    psi = I.random_state(n, 3)
+    with make(qe, n, psi=psi) as st:
+        st.profile(True)
+        e = st.expectation(xm, zm, cf)
+        prof = st.profile_read()
+    assert "expect_rounds" not in prof and "expect_tile" in prof
+    assert abs(e - oracle.expectation(psi, xm, zm, cf)) < 1e-12
+
+
 def test_tfim_closed_forms(qe):
     n = 11
     xm, zm, cf = I.tfim_terms(n)
