@@ -19,9 +19,11 @@
 //     high qubits; a final read-only low pass adds the X terms of the low
 //     qubits.  Each pass is split into items of a few tiles.
 // An item may start only when every item of the circuit's earlier passes has
-// finished: CTAs wait on a per-circuit completion counter.  Items are queued
-// pass-major across circuits, so the dependencies of any claimed item were
-// claimed earlier by running CTAs; waits are bounded and report a timeout.
+// finished: CTAs wait on a per-circuit completion counter.  Large circuits
+// are queued in waves of at most 64 MiB of state (half the L2 cache),
+// pass-major inside a wave, with the small circuits spread between the
+// passes; the dependencies of any claimed item were claimed earlier by
+// running CTAs; waits are bounded and report a timeout.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -410,6 +412,10 @@ void upload_matrices(qe_batch* b, std::vector<uint64_t>& u_off) {
     QE_CUDA(cudaMemcpy(b->U, h.data(), h.size() * sizeof(typename P::M), cudaMemcpyHostToDevice));
 }
 
+// States of the large circuits of one wave: together at most this many bytes
+// (half the 129 MB L2 cache).
+constexpr uint64_t kWaveBytes = 64ull << 20;
+
 template <class P>
 void build_plan(qe_batch* b) {
     const int T = b->plan.T;
@@ -435,7 +441,7 @@ void build_plan(qe_batch* b) {
             large.push_back(c);
         }
     }
-    // large circuits largest first, then pass-major across circuits
+    // large circuits largest first
     std::stable_sort(large.begin(), large.end(), [&](int x, int y) { return circ[x].n > circ[y].n; });
     const int P_ = 2 * b->layers + 1;
     std::vector<std::vector<int>> per_pass_count(b->count, std::vector<int>(P_, 0));
@@ -449,38 +455,63 @@ void build_plan(qe_batch* b) {
         cc.nslots = 2 * nper;   // last high pass + energy low pass
         slots += cc.nslots;
     }
-    for (int p = 0; p < P_; ++p) {
-        for (int c : large) {
-            const Circ& cc = circ[c];
-            const uint32_t tiles = 1u << (cc.n - T);
-            const uint32_t per = (uint32_t)std::max(1, b->plan.tiles_per_item);
-            const int nper = (int)((tiles + per - 1) / per);
-            for (int j = 0; j < nper; ++j) {
-                Item it{};
-                it.circuit = c;
-                it.kind = (p == P_ - 1) ? 3 : (p % 2 == 0 ? 1 : 2);
-                it.layer = p / 2;
-                it.tile0 = j * per;
-                it.tile1 = std::min(tiles, (uint32_t)(j + 1) * per);
-                it.dep = (uint32_t)(p * nper);
-                it.last_energy = (p == P_ - 2) ? 1 : 0;
-                it.slot = (p == P_ - 2) ? cc.slot0 + j : (p == P_ - 1) ? cc.slot0 + nper + j : -1;
-                items.push_back(it);
-            }
+    auto push_pass = [&](int c, int p) {
+        const Circ& cc = circ[c];
+        const uint32_t tiles = 1u << (cc.n - T);
+        const uint32_t per = (uint32_t)std::max(1, b->plan.tiles_per_item);
+        const int nper = (int)((tiles + per - 1) / per);
+        for (int j = 0; j < nper; ++j) {
+            Item it{};
+            it.circuit = c;
+            it.kind = (p == P_ - 1) ? 3 : (p % 2 == 0 ? 1 : 2);
+            it.layer = p / 2;
+            it.tile0 = j * per;
+            it.tile1 = std::min(tiles, (uint32_t)(j + 1) * per);
+            it.dep = (uint32_t)(p * nper);
+            it.last_energy = (p == P_ - 2) ? 1 : 0;
+            it.slot = (p == P_ - 2) ? cc.slot0 + j : (p == P_ - 1) ? cc.slot0 + nper + j : -1;
+            items.push_back(it);
         }
-    }
-    // small circuits last (largest first), each one item without dependencies
-    std::vector<int> small;
-    for (int c = 0; c < b->count; ++c)
-        if (circ[c].n <= T) small.push_back(c);
-    std::stable_sort(small.begin(), small.end(), [&](int x, int y) { return circ[x].n > circ[y].n; });
-    for (int c : small) {
+    };
+    auto push_small = [&](int c) {
         Item it{};
         it.circuit = c;
         it.kind = 0;
         it.slot = -1;
         items.push_back(it);
+    };
+    // small circuits (largest first): one item each, without dependencies
+    std::vector<int> small;
+    for (int c = 0; c < b->count; ++c)
+        if (circ[c].n <= T) small.push_back(c);
+    std::stable_sort(small.begin(), small.end(), [&](int x, int y) { return circ[x].n > circ[y].n; });
+    // Large circuits go in waves whose states together fit in the L2 cache,
+    // pass-major inside a wave, so that a circuit's passes find its state in
+    // L2 instead of HBM; the small circuits' items are spread evenly between
+    // the passes, where they occupy CTAs that would otherwise wait for a
+    // pass to finish.  Every item's dependencies (its circuit's earlier
+    // passes) come earlier in this order, so the claimed items never wait on
+    // unclaimed ones.
+    std::vector<std::vector<int>> waves;
+    uint64_t in_wave = 0;
+    for (int c : large) {
+        const uint64_t bytes = (1ull << circ[c].n) * sizeof(typename P::S);
+        if (waves.empty() || in_wave + bytes > kWaveBytes) {
+            waves.emplace_back();
+            in_wave = 0;
+        }
+        waves.back().push_back(c);
+        in_wave += bytes;
     }
+    const size_t gaps = waves.size() * (size_t)P_;
+    size_t si = 0, gap = 0;
+    for (const auto& w : waves)
+        for (int p = 0; p < P_; ++p) {
+            for (int c : w) push_pass(c, p);
+            const size_t upto = small.size() * (++gap) / gaps;
+            for (; si < upto; ++si) push_small(small[si]);
+        }
+    for (; si < small.size(); ++si) push_small(small[si]);
     b->nitems = (int)items.size();
     // device buffers
     const size_t need_states = state_off * sizeof(typename P::S);
