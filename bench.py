@@ -936,8 +936,10 @@ def bench_qpe(qe, I, ns=(8, 9, 10, 11, 12)):
     Ising evolution (G = 4n - 3 gates).  T_apply: the circuit applied once,
     gate by gate, to an (n+1)-qubit state (the one-ancilla simulation needs
     2^b - 1 of them); T_build: the dense 2^n x 2^n matrix of U (identity state
-    plus the gates); T_gemm: one FP64 squaring.  The cross-over is the
-    smallest b with (2^b - 1) T_apply >= T_build + (b - 1) T_gemm."""
+    plus the gates); T_gemm: one squaring, on the tensor cores (exact digit
+    products, 128-bit sums) and with the FP64 kernel (QE_GEMM_F64=1).  The
+    cross-over is the smallest b with (2^b - 1) T_apply >= T_build + (b - 1)
+    T_gemm."""
     import torch
     out = {}
     for n in ns:
@@ -970,19 +972,34 @@ def bench_qpe(qe, I, ns=(8, 9, 10, 11, 12)):
             e1.record(u.stream)
             e1.synchronize()
             t_build = e0.elapsed_time(e1)
-            u2.matmul(u, u)
-            torch.cuda.synchronize()
-            e0, e1 = _events()
-            e0.record(u2.stream)
-            u2.matmul(u, u)
-            e1.record(u2.stream)
-            e1.synchronize()
-            t_gemm = e0.elapsed_time(e1)
-        b = 1
-        while (2 ** b - 1) * t_apply < t_build + (b - 1) * t_gemm and b < 64:
-            b += 1
-        out[f"n{n}"] = {"G": len(gates), "apply_U_ms": t_apply, "build_dense_U_ms": t_build, "zgemm_ms": t_gemm,
-                        "zgemm_TFLOPs": 8.0 * 8 ** n / (t_gemm * 1e-3) / 1e12, "crossover_bits": b}
+            gemm = {}
+            for label in ("tensor_cores", "fp64"):
+                if label == "fp64":
+                    os.environ["QE_GEMM_F64"] = "1"
+                try:
+                    u2.matmul(u, u)
+                    torch.cuda.synchronize()
+                    e0, e1 = _events()
+                    e0.record(u2.stream)
+                    u2.matmul(u, u)
+                    e1.record(u2.stream)
+                    e1.synchronize()
+                    gemm[label] = (e0.elapsed_time(e1), u2.get())
+                finally:
+                    os.environ.pop("QE_GEMM_F64", None)
+        t_gemm, t_f64 = gemm["tensor_cores"][0], gemm["fp64"][0]
+        diff = float(np.max(np.abs(gemm["tensor_cores"][1] - gemm["fp64"][1])))
+
+        def crossover(tg):
+            b = 1
+            while (2 ** b - 1) * t_apply < t_build + (b - 1) * tg and b < 64:
+                b += 1
+            return b
+        out[f"n{n}"] = {"G": len(gates), "apply_U_ms": t_apply, "build_dense_U_ms": t_build,
+                        "zgemm_ms": t_gemm, "zgemm_TFLOPs": 8.0 * 8 ** n / (t_gemm * 1e-3) / 1e12,
+                        "zgemm_fp64_ms": t_f64, "zgemm_fp64_TFLOPs": 8.0 * 8 ** n / (t_f64 * 1e-3) / 1e12,
+                        "tensor_core_vs_fp64_max_abs": diff,
+                        "crossover_bits": crossover(t_gemm), "crossover_bits_fp64_gemm": crossover(t_f64)}
         torch.cuda.empty_cache()
     out["note"] = ("Table II of the paper (Xeon, MKL zgemm) gives cross-overs 6, 9, 12, 15, 18 bits for "
                    "n = 8..12 (context only)")

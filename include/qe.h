@@ -176,8 +176,16 @@ int qe_probs(qe_state* s, int m, const int* qubits, double* out);
  *     every column, so the state becomes the circuit's dense matrix U: the
  *     emulator's O(G 2^(2n)) construction of U.
  *   qe_matmul: c = a b for three such states of the same width (c distinct
- *     from a and b), in FP64 (fused multiply-adds): one squaring of the
- *     repeated squaring U^(2^i) = U^(2^(i-1)) U^(2^(i-1)), O(2^(3k)).
+ *     from a and b): one squaring of the repeated squaring
+ *     U^(2^i) = U^(2^(i-1)) U^(2^(i-1)), O(2^(3k)).  For k >= 6 on the
+ *     tensor cores: every input rounded once to 56 bits of its row's (a's
+ *     rows) or column's (b's columns) largest magnitude, exact digit
+ *     products, exact 128-bit sums, one rounding to FP64 (each element within
+ *     2^k rowmax colmax 2^-51 of the exact product; rows or columns below
+ *     2^-920 flush to zero); the workspace (about 0.9 x the three matrices'
+ *     bytes) is kept with c.  For k < 6, or with the environment variable
+ *     QE_GEMM_F64=1, FP64 fused multiply-adds.  Synchronises c's stream;
+ *     QE_ERR_TIMEOUT if a tensor-core wait ran out (bounded waits).
  *   qe_qpe_emulate: coherent phase estimation on s with the system register
  *     [0, nsys) and b ancillas [nsys, nsys + b) (nsys + b <= n): Hadamards on
  *     the ancillas, ancilla j applies U^(2^j) (u holds U, 2 nsys qubits) to
@@ -185,6 +193,8 @@ int qe_probs(qe_state* s, int m, const int* qubits, double* out);
  *     each applied as one dense product -- then the inverse QFT on the
  *     ancillas (emulated).  With the ancillas in |0> and an eigenvector of U
  *     with eigenvalue exp(2 pi i k / 2^b), the ancilla register ends in |k>.
+ *     The squarings are qe_matmul's (tensor cores for nsys >= 6, workspace
+ *     kept with s); the controlled products use FP64 fused multiply-adds.
  *     Allocates two temporary matrices (QE_ERR_OOM if that fails) and uses
  *     the state's scratch; synchronises the stream.
  * All three want complex128 states; QE_ERR_ARG for mismatched widths or a

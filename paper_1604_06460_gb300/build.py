@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", f"-I{INCLUDE}"]
 SOURCES = ["api.cu", "plan.cu", "state.cu", "gates.cu", "fft.cu", "perm.cu", "reduce.cu", "batch.cu", "mlp.cu", "tcgen05.cu",
-           "tc_c128.cu", "arith.cu", "sample.cu", "qpe.cu",
+           "tc_c128.cu", "oz_gemm.cu", "arith.cu", "sample.cu", "qpe.cu",
            "noalloc.cu"]
 
 

@@ -670,6 +670,7 @@ int qe_free_state(qe_state* s) {
     cudaStreamSynchronize(s->stream);
     if (s->owned && s->d) cudaFree(s->d);
     if (s->scratch) cudaFree(s->scratch);
+    if (s->oz_ws) cudaFree(s->oz_ws);
     if (s->status_host) cudaFreeHost(s->status_host);
     profile_clear(s);
     for (auto e : s->event_pool) cudaEventDestroy(e);

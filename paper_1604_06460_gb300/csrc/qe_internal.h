@@ -61,6 +61,9 @@ struct qe_state {
     // device scratch for reductions, grown on demand
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
+    // digit planes of the tensor-core matrix product, grown on demand
+    void* oz_ws = nullptr;
+    size_t oz_ws_bytes = 0;
     // pinned host mirror of small results
     double* host_result = nullptr;
     qe::Stats stats;
@@ -100,6 +103,17 @@ inline bool c128_f64(const qe_state* s) { return s->dtype == QE_C128 && s->arith
 inline int c128_tc_kmin(const qe_state*) { return 3; }
 int num_sms();
 void* ensure_scratch(qe_state* s, size_t bytes);
+// the tensor-core matrix product's workspace (at least `bytes`; the state's
+// stream is synchronised before an old one is freed)
+void* ensure_oz_workspace(qe_state* s, size_t bytes);
+// complex matrix products on the tensor cores (7-digit splitting, exact
+// 128-bit sums): C (M x N, row-major, ldc) = A (M x K; logical row r is memory
+// row r with a 1 inserted at a_rowbit when a_rowbit >= 0) B (K x N, row-major);
+// false from the first when the shape is not supported (K a multiple of 32, N
+// of 16) or QE_GEMM_F64=1 asks for the FP64 kernel
+bool oz_gemm_available(int64_t M, int64_t K, int64_t N);
+void oz_zgemm(qe_state* s, double2* C, int64_t ldc, const double2* A, int64_t M, int64_t K, int64_t lda, int a_rowbit,
+              const double2* B, int64_t N, int64_t ldb);
 
 // ---- kernels (each launcher enqueues on s->stream and updates s->stats)
 void launch_init_basis(qe_state* s, uint64_t index);

@@ -126,6 +126,12 @@ void launch_init_identity(qe_state* s, int nsys) {
 // C^T = B^T A^T.  Enqueued on acct's stream, counted in its statistics.
 void launch_matmul(qe_state* acct, void* c, const void* a, const void* b, int k) {
     const int64_t D = 1ll << k;
+    if (acct->tensor_cores && k >= 6 && oz_gemm_available(D, D, D)) {
+        // on the tensor cores: exact digit products, 128-bit sums
+        oz_zgemm(acct, reinterpret_cast<double2*>(c), D, reinterpret_cast<const double2*>(b), D, D, D, -1,
+                 reinterpret_cast<const double2*>(a), D, D);
+        return;
+    }
     GemmArgs g{};
     g.A = reinterpret_cast<const double2*>(b);
     g.B = reinterpret_cast<const double2*>(a);

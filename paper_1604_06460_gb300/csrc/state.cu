@@ -41,6 +41,20 @@ void* ensure_scratch(qe_state* s, size_t bytes) {
     return s->scratch;
 }
 
+void* ensure_oz_workspace(qe_state* s, size_t bytes) {
+    if (s->oz_ws_bytes < bytes) {
+        if (s->oz_ws) {
+            QE_CUDA(cudaStreamSynchronize(s->stream));
+            QE_CUDA(cudaFree(s->oz_ws));
+            s->oz_ws = nullptr;
+            s->oz_ws_bytes = 0;
+        }
+        QE_CUDA(cudaMalloc(&s->oz_ws, bytes));
+        s->oz_ws_bytes = bytes;
+    }
+    return s->oz_ws;
+}
+
 // ---------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
 // 32x32->64-bit products with multipliers 0xD2511F53 / 0xCD9E8D57 and a Weyl

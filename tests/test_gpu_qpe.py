@@ -96,3 +96,112 @@ def test_qpe_reads_exact_eigenphases(qe):
                 p = np.abs(st.get()) ** 2
             k = (3 * (x & 1) + 5 * ((x >> 1) & 1) + 9 * (x >> 2)) % 64
             assert abs(p[(k << nsys) | x] - 1) < 1e-12
+
+
+# ------------------------------------------- tensor-core matrix products
+def matrix_state(qe, k, M):
+    st = qe.State(2 * k, "c128")
+    st.set(np.ascontiguousarray(M.T).reshape(-1))     # column-major storage
+    return st
+
+
+def product(qe, k, A, B, fp64=False):
+    import os
+    if fp64:
+        os.environ["QE_GEMM_F64"] = "1"
+    try:
+        with matrix_state(qe, k, A) as sa, matrix_state(qe, k, B) as sb, qe.State(2 * k, "c128") as sc:
+            sc.profile(True)
+            sc.matmul(sa, sb)
+            prof = sc.profile_read()
+            C = as_matrix(sc, k)
+    finally:
+        os.environ.pop("QE_GEMM_F64", None)
+    return C, prof
+
+
+def long_double_rows(A, B, rows):
+    a = A[rows].astype(np.clongdouble)
+    return a @ B.astype(np.clongdouble)
+
+
+@pytest.mark.parametrize("k", [6, 7, 8, 9])
+def test_matmul_tensor_cores_vs_long_double(qe, k):
+    # Gaussian complex matrices: every element of the tensor-core product
+    # within K rowmax(A) colmax(B) 2^-51 of the long-double product (the
+    # 56-bit splitting bound), and the path must be the tensor cores
+    D = 1 << k
+    rng = np.random.default_rng(10 + k)
+    A = rng.standard_normal((D, D)) + 1j * rng.standard_normal((D, D))
+    B = rng.standard_normal((D, D)) + 1j * rng.standard_normal((D, D))
+    C, prof = product(qe, k, A, B)
+    assert "oz_zgemm" in prof and "zgemm" not in prof, prof
+    C64, prof64 = product(qe, k, A, B, fp64=True)
+    assert "zgemm" in prof64 and "oz_zgemm" not in prof64
+    rows = np.arange(D) if k <= 8 else rng.choice(D, 48, replace=False)
+    ref = long_double_rows(A, B, rows)
+    rowmax = np.max(np.maximum(np.abs(A.real), np.abs(A.imag)), axis=1)[rows][:, None]
+    colmax = np.max(np.maximum(np.abs(B.real), np.abs(B.imag)), axis=0)[None, :]
+    bound = D * rowmax * colmax * 2.0 ** -51
+    err = np.abs(C[rows].astype(np.clongdouble) - ref).astype(float)
+    assert np.all(err <= bound)
+    err64 = np.abs(C64[rows].astype(np.clongdouble) - ref).astype(float)
+    # typical errors of both products are rounding-level
+    assert np.max(err / (rowmax * colmax)) < 64 * 2.0 ** -52
+    assert np.max(err64 / (rowmax * colmax)) < D * 2.0 ** -52
+
+
+def test_matmul_tensor_cores_scales_and_exact_cases(qe):
+    # rows of A and columns of B scaled by 2^-300 .. 2^300: each element keeps
+    # its relative accuracy; identity and permutation products are exact;
+    # a zero row and a zero column give zeros
+    k = 7
+    D = 1 << k
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((D, D)) + 1j * rng.standard_normal((D, D))
+    B = rng.standard_normal((D, D)) + 1j * rng.standard_normal((D, D))
+    er = rng.integers(-300, 300, D)
+    fc = rng.integers(-300, 300, D)
+    As = A * np.ldexp(1.0, er)[:, None]
+    Bs = B * np.ldexp(1.0, fc)[None, :]
+    As[5] = 0
+    Bs[:, 9] = 0
+    C, _ = product(qe, k, As, Bs)
+    ref = long_double_rows(A, B, np.arange(D))
+    got = (C * np.ldexp(1.0, -er)[:, None] * np.ldexp(1.0, -fc)[None, :]).astype(np.clongdouble)
+    rowmax = np.max(np.maximum(np.abs(A.real), np.abs(A.imag)), axis=1)[:, None]
+    colmax = np.max(np.maximum(np.abs(B.real), np.abs(B.imag)), axis=0)[None, :]
+    mask = np.ones((D, D), bool)
+    mask[5, :] = False
+    mask[:, 9] = False
+    err = np.abs(got - ref).astype(float)
+    assert np.all(err[mask] <= (D * rowmax * colmax * 2.0 ** -51)[mask])
+    assert np.all(C[5, :] == 0) and np.all(C[:, 9] == 0)
+    # a permutation (identity) times B: each element is one product, within
+    # colmax(B) 2^-51 of its value (the 56-bit splitting of B's column and one
+    # rounding of Y, each at most 2^(E+F-57))
+    perm = rng.permutation(D)
+    P = np.eye(D)[perm].astype(complex)
+    for Pm, want in ((np.eye(D, dtype=complex), B), (P, B[perm])):
+        Cp, _ = product(qe, k, Pm, B)
+        assert np.all(np.abs(Cp - want) <= colmax * 2.0 ** -51)
+
+
+@pytest.mark.parametrize("nsys,b", [(6, 3), (7, 2)])
+def test_qpe_tensor_core_squaring_vs_oracle(qe, nsys, b):
+    # nsys >= 6: the powers U^(2^j) come from the tensor-core product
+    gates = tfim_step(nsys)
+    psi = I.random_state(nsys, 70 + nsys)
+    ref = oracle.qpe_circuit(psi, nsys, b, gates)
+    n = nsys + b
+    with dense_on_gpu(qe, nsys, gates) as u, qe.State(n, "c128") as st:
+        full = np.zeros(1 << n, complex)
+        full[: 1 << nsys] = psi
+        st.set(full)
+        st.profile(True)
+        st.qpe_emulate(nsys, b, u)
+        prof = st.profile_read()
+        got = st.get()
+    assert "oz_zgemm" in prof
+    assert np.max(np.abs(got - ref)) < 1e-12
+    assert oracle.fidelity(ref, got) > 1 - 1e-10
