@@ -77,6 +77,8 @@ KERNEL_CASES = {
     "fft": "emulated 25-qubit QFT of a complex128 state, FP64 mode (5-qubit digit passes), 2 transforms",
     "fftdf": "emulated 26-qubit QFT of a complex128 state, double-float mode (radix-2 shared-memory passes), "
              "2 transforms",
+    "qpegemm": "one squaring of a 2^10 x 2^10 complex128 matrix on the tensor cores (digit splitting + product), "
+               "2 products",
 }
 
 
@@ -109,6 +111,13 @@ def run_kernel_case(qe, I, which):
             for _ in range(3):
                 st.apply_gate([5, 17], U)
                 st.flush()
+    elif which == "qpegemm":
+        D = 1 << 10
+        z = rng.standard_normal((D, D)) + 1j * rng.standard_normal((D, D))
+        with qe.State(20, "c128") as a, qe.State(20, "c128") as c:
+            a.set(np.ascontiguousarray(z).reshape(-1))
+            for _ in range(2):
+                c.matmul(a, a)
     elif which in ("expect", "expectdf"):
         with qe.State(26, "c128") as st:
             if df:
@@ -308,7 +317,8 @@ def peak_hbm():
 # Source files each profiled kernel is built from (its summary's hash covers
 # only these, so an edit elsewhere keeps the counters valid).
 KERNEL_SOURCES = {
-    "gate_tc_k5_c128": ["tc_c128.cu", "qe_tc.cuh", "qe_arith.cuh"],
+    "gate_tc_k5_c128": ["tc_c128.cu", "qe_oz.cuh", "qe_tc.cuh", "qe_arith.cuh"],
+    "oz_zgemm": ["oz_gemm.cu", "qe_oz.cuh", "qe_tc.cuh"],
     "fft_twiddle": ["fft.cu", "qe_arith.cuh"],
     "digitrev": ["fft.cu", "qe_arith.cuh"],
     "gate_tc_k5": ["tcgen05.cu", "qe_tc.cuh", "qe_arith.cuh"],
