@@ -12,14 +12,18 @@
 // per row over its 2K real values) and of the rows of the right operand's
 // transpose, Bt, whose rows are the real output columns (one scale per
 // complex output column, shared by its real and imaginary rows), as fp16
-// planes [digit][row][k] with k contiguous.  Bt rows are ordered per tile of
-// 16 complex output columns: their 16 real-part rows, then their 16
-// imaginary-part rows.  Rows of A beyond M (up to a multiple of 128) are zero.
+// digits in blocks of one operand tile and K-chunk (A: 128 rows, Bt: 32 rows,
+// x 64 values of K) per digit, each block already in the 128-byte-swizzled
+// K-major layout the MMAs read, so that one bulk copy moves it into shared
+// memory.  Bt rows are ordered per tile of 16 complex output columns: their
+// 16 real-part rows, then their 16 imaginary-part rows.  Rows of A beyond M
+// (up to a multiple of 128) are zero.
 //
 // Product kernel: one CTA per output tile of 128 rows x 16 complex columns,
-// warp-specialised like the gate kernel.  Two load warps copy one K-chunk of
-// the A tile's and the Bt tile's seven digit planes into the 128-byte-swizzled
-// K-major layout (112 + 28 KB, one buffer); one thread issues the 34 digit
+// warp-specialised like the gate kernel.  One thread copies a K-chunk's seven
+// A and seven Bt digit blocks (112 + 28 KB, one buffer) with the bulk-copy
+// engine (cp.async.bulk, completion counted in bytes on an mbarrier); one
+// thread issues the 34 digit
 // pairs with i + j <= 9 as 8 MMAs per K-step (the Bt digit slices stacked
 // along N, as the gate kernel stacks W's) into one of two tensor-memory
 // accumulator sets (8 accumulators x 32 columns each); sixteen recombining
@@ -54,22 +58,34 @@ constexpr uint32_t kASlice = kTM * 128;     // bytes of one digit plane of the A
 constexpr uint32_t kBSlice = kTN * 128;     // bytes of one digit plane of the Bt tile
 constexpr uint32_t kSetCols = 256;          // 8 accumulators x 32 columns
 constexpr int kRecWarps = 16;               // 4 per tensor-memory lane quarter, 8 columns each
-constexpr int kMmaWarp = kRecWarps, kLoadWarp0 = kRecWarps + 1, kLoadWarps = 2;
-constexpr int kThreads = 32 * (kLoadWarp0 + kLoadWarps);   // 608
-constexpr int kRecThreads = 32 * kRecWarps, kLoadThreads = 32 * kLoadWarps;
+constexpr int kMmaWarp = kRecWarps, kLoadWarp = kRecWarps + 1;
+constexpr int kThreads = 32 * (kLoadWarp + 1);   // 576
+constexpr int kRecThreads = 32 * kRecWarps;
+constexpr uint32_t kChunkBytes = kD * (kASlice + kBSlice);   // bulk-copied per K-chunk
 constexpr int kFlushExp = 100;              // biased exponent below which a row is flushed
 constexpr size_t kSmem = 1024 + (size_t)kD * (kASlice + kBSlice);
 static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
 
 // ------------------------------------------------------------- splitting
-// The seven digits of one row's values v[0..Kr) (two at a time, packed as
-// fp16 pairs), written to planes [digit][row][Kr/2 pairs].
-__device__ __forceinline__ void put_pair(uint32_t* dig, size_t plane, size_t idx, double a, double b,
-                                         uint32_t base_s) {
+// Digit blocks: digit i of operand-tile t (of nt) and K-chunk c (of nc) is
+// the block ((i nt + t) nc + c) of `block` bytes; inside it, values k, k + 1
+// (k even) of the tile's row r sit at sw128_chunk(r, (k mod 64) / 8) +
+// 2 (k mod 8) bytes.
+__device__ __forceinline__ size_t block_word(int i, int64_t t, int64_t nt, int64_t c, int64_t nc, uint32_t block,
+                                             int r, int64_t k) {
+    const uint32_t kk = (uint32_t)(k & 63);
+    const size_t base = (((size_t)i * nt + t) * nc + c) * block;
+    return (base + sw128_chunk(r, (int)(kk >> 3)) + 2u * (kk & 7u)) >> 2;
+}
+
+// The seven digits of two consecutive values (packed fp16 pairs) into their
+// blocks (operand row r of tile t, values k, k + 1).
+__device__ __forceinline__ void put_pair(uint32_t* dig, int64_t t, int64_t nt, int64_t nc, uint32_t block, int r,
+                                         int64_t k, double a, double b, uint32_t base_s) {
     uint32_t w[kD];
     digit_pairs<kD>(split_z<kD>(a, base_s), split_z<kD>(b, base_s), w);
 #pragma unroll
-    for (int i = 0; i < kD; ++i) dig[i * plane + idx] = w[i];
+    for (int i = 0; i < kD; ++i) dig[block_word(i, t, nt, k >> 6, nc, block, r, k)] = w[i];
 }
 
 __device__ __forceinline__ uint32_t biased_exp(double v) { return ((uint32_t)__double2hiint(v) << 1) >> 21; }
@@ -96,12 +112,12 @@ __global__ void __launch_bounds__(256) k_split_a(const double2* __restrict__ src
                                                  int64_t Mp) {
     __shared__ uint32_t sh[32];
     const int64_t r = blockIdx.x;
-    const int64_t Kr = 2 * K, pairs = K;   // pairs of consecutive reals
-    const size_t plane = (size_t)Mp * (size_t)pairs;
-    uint32_t* out = dig + (size_t)r * pairs;
+    const int64_t pairs = K;   // pairs of consecutive reals of the 2K
+    const int64_t nt = Mp / kTM, nc = 2 * K / kKC, t = r / kTM;
+    const int rl = (int)(r % kTM);
     if (r >= M) {
         for (int64_t p = threadIdx.x; p < pairs; p += blockDim.x)
-            for (int i = 0; i < kD; ++i) out[i * plane + p] = 0u;   // fp16 zeros
+            for (int i = 0; i < kD; ++i) dig[block_word(i, t, nt, (2 * p) >> 6, nc, kASlice, rl, 2 * p)] = 0u;
         if (threadIdx.x == 0) escale[r] = 0;
         return;
     }
@@ -117,10 +133,9 @@ __global__ void __launch_bounds__(256) k_split_a(const double2* __restrict__ src
         const int64_t k = 2 * p;   // reals k, k + 1 of [Re | Im]
         const double2 u = row[k % K], w = row[(k + 1) % K];
         const bool im = k >= K;
-        put_pair(out, plane, (size_t)p, im ? u.y : u.x, im ? w.y : w.x, base_s);
+        put_pair(dig, t, nt, nc, kASlice, rl, k, im ? u.y : u.x, im ? w.y : w.x, base_s);
     }
     if (threadIdx.x == 0) escale[r] = (int)em - 1021;
-    (void)Kr;
 }
 
 // One CTA per tile of 16 complex columns c of B (K x N, row-major): the Bt
@@ -150,8 +165,7 @@ __global__ void __launch_bounds__(256) k_split_b(const double2* __restrict__ src
         fscale[32 * blockIdx.x + 16 + tid] = (int)m - 1021;
     }
     __syncthreads();
-    const int64_t pairs = K;   // per Bt row: 2K reals
-    const size_t plane = (size_t)Nr * (size_t)pairs;
+    const int64_t nt = Nr / kTN, nc = 2 * K / kKC;
     const int q = tid & 15;    // pair within a 32-value segment
     for (int64_t k0 = 0; k0 < K; k0 += 32) {
         for (int e = tid; e < 32 * 16; e += 256) blk[e >> 4][e & 15] = src[(k0 + (e >> 4)) * ldb + c0 + (e & 15)];
@@ -169,7 +183,7 @@ __global__ void __launch_bounds__(256) k_split_b(const double2* __restrict__ src
                 b = hf ? w.x : w.y;
             }
             const int64_t pos = (hf ? K : 0) + k0 + 2 * q;
-            put_pair(dig, plane, (size_t)(32 * blockIdx.x + rho) * pairs + pos / 2, a, b, base[cl]);
+            put_pair(dig, blockIdx.x, nt, nc, kBSlice, rho, pos, a, b, base[cl]);
         }
         __syncthreads();
     }
@@ -177,8 +191,8 @@ __global__ void __launch_bounds__(256) k_split_b(const double2* __restrict__ src
 
 // ---------------------------------------------------------------- product
 struct GemmOzArgs {
-    const uint16_t* adig;   // [kD][Mp][Kr]
-    const uint16_t* bdig;   // [kD][Nr][Kr]
+    const uint16_t* adig;   // digit blocks of A (kD x Mp/128 x Kr/64 blocks of 16 KB)
+    const uint16_t* bdig;   // digit blocks of Bt (kD x Nr/32 x Kr/64 blocks of 4 KB)
     const int* ea;          // [Mp]
     const int* fb;          // [Nr]
     double2* C;             // row-major, C[r * ldc + c]
@@ -188,6 +202,19 @@ struct GemmOzArgs {
 };
 
 enum GBar { kOpReady, kOpFree, kFull0, kFull1, kFree0, kFree1, kDrain, kGBars };
+
+// The executing thread's arrival on the mbarrier, announcing `bytes` of
+// asynchronous copies that complete on it.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// from global to this CTA's shared memory, completion counted on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+                 : "memory");
+}
 
 __device__ __forceinline__ double i128_to_double(long long hi, unsigned long long lo) {
     if ((hi == 0 && (long long)lo >= 0) || (hi == -1 && (long long)lo < 0)) return __ll2double_rn((long long)lo);
@@ -205,7 +232,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_zgemm(const __grid_constant_
     const int64_t row0 = (int64_t)blockIdx.y * kTM, brow0 = (int64_t)blockIdx.x * kTN;
     const int nchunks = (int)(a.Kr / kKC);
     if (tid == 0) {
-        const uint32_t counts[kGBars] = {kLoadThreads, 1, 1, 1, kRecThreads, kRecThreads, 1};
+        const uint32_t counts[kGBars] = {1, 1, 1, 1, kRecThreads, kRecThreads, 1};
         for (int b = 0; b < kGBars; ++b) mbar_init_count(&bars[b], counts[b]);
         abort_flag = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -240,9 +267,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_zgemm(const __grid_constant_
                     ok = wait_or_abort(smem_u32(&bars[set ? kFree1 : kFree0]), (uint32_t)((c >> 1) - 1) & 1u,
                                        a.spin_limit, &abort_flag);
                 if (!ok) break;
-                // the operands were written by cp.async (generic proxy) and are
-                // read by the tensor cores (async proxy)
-                asm volatile("fence.proxy.async.shared::cta;");
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t dset = tmem + (uint32_t)set * kSetCols;
 #pragma unroll
@@ -265,25 +289,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_zgemm(const __grid_constant_
             if (!tc::mbar_wait(smem_u32(&bars[kDrain]), 0u, a.spin_limit)) atomicExch(a.status, 1u);
         }
         __syncwarp();
-    } else if (warp >= kLoadWarp0) {
+    } else if (warp == kLoadWarp) {
         // ------------------------------------------------------- loads
-        const int t = tid - kLoadWarp0 * 32;
-        const uint32_t dA = smem_u32(sA), dB = smem_u32(sB);
-        for (int c = 0; c < nchunks; ++c) {
-            if (c > 0 && !wait(kOpFree, (uint32_t)(c - 1) & 1u)) break;
-            const int64_t k0 = (int64_t)c * kKC;
-            for (int e = t; e < kD * kTM * 8; e += kLoadThreads) {
-                const int i = e / (kTM * 8), r = (e / 8) % kTM, ch = e % 8;
-                cp_async16(dA + (uint32_t)i * kASlice + sw128_chunk(r, ch),
-                           a.adig + ((size_t)i * a.Mp + row0 + r) * a.Kr + k0 + ch * 8);
+        // one thread: per K-chunk, once the previous chunk's MMAs are done,
+        // the byte count on the ready barrier and 14 bulk copies
+        if (lane == 0) {
+            const int64_t ntA = a.Mp / kTM, ntB = a.Nr / kTN;
+            const char* ga = reinterpret_cast<const char*>(a.adig);
+            const char* gb = reinterpret_cast<const char*>(a.bdig);
+            for (int c = 0; c < nchunks; ++c) {
+                if (c > 0 && !wait_or_abort(smem_u32(&bars[kOpFree]), (uint32_t)(c - 1) & 1u, a.spin_limit, &abort_flag)) {
+                    atomicExch(a.status, 1u);
+                    break;
+                }
+                mbar_expect_tx(&bars[kOpReady], kChunkBytes);
+#pragma unroll 1
+                for (int i = 0; i < kD; ++i) {
+                    bulk_g2s(smem_u32(sA) + (uint32_t)i * kASlice,
+                             ga + (((size_t)i * ntA + blockIdx.y) * nchunks + c) * kASlice, kASlice, &bars[kOpReady]);
+                    bulk_g2s(smem_u32(sB) + (uint32_t)i * kBSlice,
+                             gb + (((size_t)i * ntB + blockIdx.x) * nchunks + c) * kBSlice, kBSlice, &bars[kOpReady]);
+                }
             }
-            for (int e = t; e < kD * kTN * 8; e += kLoadThreads) {
-                const int j = e / (kTN * 8), r = (e / 8) % kTN, ch = e % 8;
-                cp_async16(dB + sw128_chunk(j * kTN + r, ch), a.bdig + ((size_t)j * a.Nr + brow0 + r) * a.Kr + k0 + ch * 8);
-            }
-            cp_async_arrive(&bars[kOpReady]);
         }
-        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncwarp();
     } else {
         // --------------------------------------------- recombination
         // thread <-> (row 32 q + lane, Bt columns [8 u, 8 u + 8) of the tile)
