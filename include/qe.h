@@ -194,7 +194,9 @@ int qe_probs(qe_state* s, int m, const int* qubits, double* out);
  *     ancillas (emulated).  With the ancillas in |0> and an eigenvector of U
  *     with eigenvalue exp(2 pi i k / 2^b), the ancilla register ends in |k>.
  *     The squarings are qe_matmul's (tensor cores for nsys >= 6, workspace
- *     kept with s); the controlled products use FP64 fused multiply-adds.
+ *     kept with s); the controlled products run on the tensor cores too when
+ *     nsys >= 6 and the rows they act on (2^(n - nsys - 1)) number at least
+ *     128, else with FP64 fused multiply-adds.
  *     Allocates two temporary matrices (QE_ERR_OOM if that fails) and uses
  *     the state's scratch; synchronises the stream.
  * All three want complex128 states; QE_ERR_ARG for mismatched widths or a

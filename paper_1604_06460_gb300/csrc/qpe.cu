@@ -144,20 +144,27 @@ void launch_matmul(qe_state* acct, void* c, const void* a, const void* b, int k)
 
 // The rows of s (system register [0, nsys)) whose qubit ctrl is set times
 // M^T: psi_row <- M psi_row.  M is held column-major in mat (2 nsys qubits),
-// i.e. mat's amplitudes read row-major are M^T.
+// i.e. mat's amplitudes read row-major are M^T.  On the tensor cores from 128
+// rows and nsys >= 6, else FP64 fused multiply-adds.
 void launch_dense_controlled(qe_state* s, const void* mat, int nsys, int ctrl) {
     const int64_t D = 1ll << nsys;
     const uint64_t rows = 1ull << (s->n - nsys - 1);
     double2* scr = reinterpret_cast<double2*>(ensure_scratch(s, (size_t)(rows << nsys) * sizeof(double2)));
-    GemmArgs g{};
-    g.A = reinterpret_cast<const double2*>(s->d);
-    g.B = reinterpret_cast<const double2*>(mat);
-    g.C = scr;
-    g.M = (int64_t)rows;
-    g.N = g.K = D;
-    g.lda = g.ldb = g.ldc = D;
-    g.a_rowbit = ctrl - nsys;
-    gemm(s, g, "zgemm_controlled");
+    if (s->tensor_cores && nsys >= 6 && rows >= 128 && oz_gemm_available((int64_t)rows, D, D)) {
+        // on the tensor cores (rows padded to 128 inside the product)
+        oz_zgemm(s, scr, D, reinterpret_cast<const double2*>(s->d), (int64_t)rows, D, D, ctrl - nsys,
+                 reinterpret_cast<const double2*>(mat), D, D);
+    } else {
+        GemmArgs g{};
+        g.A = reinterpret_cast<const double2*>(s->d);
+        g.B = reinterpret_cast<const double2*>(mat);
+        g.C = scr;
+        g.M = (int64_t)rows;
+        g.N = g.K = D;
+        g.lda = g.ldb = g.ldc = D;
+        g.a_rowbit = ctrl - nsys;
+        gemm(s, g, "zgemm_controlled");
+    }
     const uint64_t total = rows << nsys;
     const unsigned grid = (unsigned)std::min<uint64_t>((total + 255) / 256, (uint64_t)num_sms() * 8);
     Launch L(s, "copy_rows", 2.0 * (double)total * 16.0, false);

@@ -205,3 +205,24 @@ def test_qpe_tensor_core_squaring_vs_oracle(qe, nsys, b):
     assert "oz_zgemm" in prof
     assert np.max(np.abs(got - ref)) < 1e-12
     assert oracle.fidelity(ref, got) > 1 - 1e-10
+
+
+def test_qpe_tensor_core_controlled_powers_vs_oracle(qe):
+    # 2^7 = 128 rows per controlled power (nsys = 6, b = 8): the controlled
+    # products run on the tensor cores too
+    nsys, b = 6, 8
+    gates = tfim_step(nsys)
+    psi = I.random_state(nsys, 91)
+    ref = oracle.qpe_circuit(psi, nsys, b, gates)
+    n = nsys + b
+    with dense_on_gpu(qe, nsys, gates) as u, qe.State(n, "c128") as st:
+        full = np.zeros(1 << n, complex)
+        full[: 1 << nsys] = psi
+        st.set(full)
+        st.profile(True)
+        st.qpe_emulate(nsys, b, u)
+        prof = st.profile_read()
+        got = st.get()
+    assert prof["oz_zgemm"][0] == 2 * b - 1 and "zgemm_controlled" not in prof, prof
+    assert np.max(np.abs(got - ref)) < 1e-12
+    assert oracle.fidelity(ref, got) > 1 - 1e-10
