@@ -12,24 +12,26 @@
 // per row over its 2K real values) and of the rows of the right operand's
 // transpose, Bt, whose rows are the real output columns (one scale per
 // complex output column, shared by its real and imaginary rows), as fp16
-// digits in blocks of one operand tile and K-chunk (A: 128 rows, Bt: 32 rows,
-// x 64 values of K) per digit, each block already in the 128-byte-swizzled
+// digits in blocks of one operand tile and K-stage (A: 128 rows, Bt: 32 rows,
+// x 32 values of K) per digit, each block already in the 64-byte-swizzled
 // K-major layout the MMAs read, so that one bulk copy moves it into shared
 // memory.  Bt rows are ordered per tile of 16 complex output columns: their
 // 16 real-part rows, then their 16 imaginary-part rows.  Rows of A beyond M
 // (up to a multiple of 128) are zero.
 //
 // Product kernel: one CTA per output tile of 128 rows x 16 complex columns,
-// warp-specialised like the gate kernel.  One thread copies a K-chunk's seven
-// A and seven Bt digit blocks (112 + 28 KB, one buffer) with the bulk-copy
-// engine (cp.async.bulk, completion counted in bytes on an mbarrier); one
-// thread issues the 34 digit
+// warp-specialised like the gate kernel.  One thread copies each K-stage's
+// (32 values) seven A and seven Bt digit blocks (56 + 14 KB, two stage
+// buffers, 64-byte swizzle) with the bulk-copy engine (cp.async.bulk,
+// completion counted in bytes on the buffer's mbarrier), so the copy of a
+// stage overlaps the MMAs of the previous one; one thread issues the 34 digit
 // pairs with i + j <= 9 as 8 MMAs per K-step (the Bt digit slices stacked
 // along N, as the gate kernel stacks W's) into one of two tensor-memory
-// accumulator sets (8 accumulators x 32 columns each); sixteen recombining
-// warps turn a finished set into each output's integer Y of the chunk (as in
-// the gate kernel) and add it to a 128-bit sum.  The two sets let the
-// recombination of chunk c overlap the loads and MMAs of chunk c + 1.
+// accumulator sets (8 accumulators x 32 columns each; a set sums one chunk of
+// 64 values, two stages, exactly); sixteen recombining warps turn a finished
+// set into each output's integer Y of the chunk (as in the gate kernel) and
+// add it to a 128-bit sum.  The two sets let the recombination of chunk c
+// overlap the loads and MMAs of chunk c + 1.
 //
 // Accuracy.  Each input is rounded once to 56 bits of its row's (column's)
 // scale; within a chunk the digit products and Y are exact up to the dropped
@@ -53,29 +55,50 @@ using namespace oz;
 constexpr int kD = 7;
 constexpr int kTM = 128;                    // output rows per tile (MMA M)
 constexpr int kTN = 32;                     // Bt rows per tile (16 complex output columns)
-constexpr int kKC = 64;                     // real K per chunk: one 128-byte fp16 operand row
-constexpr uint32_t kASlice = kTM * 128;     // bytes of one digit plane of the A tile
-constexpr uint32_t kBSlice = kTN * 128;     // bytes of one digit plane of the Bt tile
+constexpr int kKC = 64;                     // real K per accumulator set (exact FP32 sums)
+constexpr int kKS = 32;                     // real K per operand stage: one 64-byte fp16 row
+constexpr uint32_t kASlice = kTM * 64;      // bytes of one digit plane of the A tile (one stage)
+constexpr uint32_t kBSlice = kTN * 64;      // bytes of one digit plane of the Bt tile (one stage)
 constexpr uint32_t kSetCols = 256;          // 8 accumulators x 32 columns
 constexpr int kRecWarps = 16;               // 4 per tensor-memory lane quarter, 8 columns each
 constexpr int kMmaWarp = kRecWarps, kLoadWarp = kRecWarps + 1;
 constexpr int kThreads = 32 * (kLoadWarp + 1);   // 576
 constexpr int kRecThreads = 32 * kRecWarps;
-constexpr uint32_t kChunkBytes = kD * (kASlice + kBSlice);   // bulk-copied per K-chunk
+constexpr uint32_t kStageBytes = kD * (kASlice + kBSlice);   // bulk-copied per stage (70 KB)
 constexpr int kFlushExp = 100;              // biased exponent below which a row is flushed
-constexpr size_t kSmem = 1024 + (size_t)kD * (kASlice + kBSlice);
+constexpr size_t kSmem = 1024 + 2 * (size_t)kStageBytes;      // two stage buffers
 static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
 
 // ------------------------------------------------------------- splitting
-// Digit blocks: digit i of operand-tile t (of nt) and K-chunk c (of nc) is
-// the block ((i nt + t) nc + c) of `block` bytes; inside it, values k, k + 1
-// (k even) of the tile's row r sit at sw128_chunk(r, (k mod 64) / 8) +
-// 2 (k mod 8) bytes.
+// Byte offset of the 16-byte chunk `ch` (8 fp16 along K) of row r in a
+// K-major operand with 64-byte rows, 64-byte swizzle (the chunk index XOR
+// bits 1-2 of the row within its 8-row, 512-byte group).
+__device__ __forceinline__ uint32_t sw64_chunk(int r, int ch) {
+    return (uint32_t)(r >> 3) * 512u + (uint32_t)(r & 7) * 64u + (uint32_t)((ch ^ ((r >> 1) & 3)) * 16);
+}
+
+// Shared-memory matrix descriptor for a K-major operand in the 64-byte swizzle
+// layout: start >> 4, leading offset (unused) 16 bytes, stride between 8-row
+// groups 512 bytes, descriptor version 1, layout SWIZZLE_64B (4).
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)(16u >> 4) << 16;
+    d |= (uint64_t)(512u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
+    return d;
+}
+
+// Digit blocks: digit i of operand-tile t (of nt) and K-stage c (of nc, 32
+// values each) is the block ((i nt + t) nc + c) of `block` bytes; inside it,
+// values k, k + 1 (k even) of the tile's row r sit at
+// sw64_chunk(r, (k mod 32) / 8) + 2 (k mod 8) bytes.
 __device__ __forceinline__ size_t block_word(int i, int64_t t, int64_t nt, int64_t c, int64_t nc, uint32_t block,
                                              int r, int64_t k) {
-    const uint32_t kk = (uint32_t)(k & 63);
+    const uint32_t kk = (uint32_t)(k & 31);
     const size_t base = (((size_t)i * nt + t) * nc + c) * block;
-    return (base + sw128_chunk(r, (int)(kk >> 3)) + 2u * (kk & 7u)) >> 2;
+    return (base + sw64_chunk(r, (int)(kk >> 3)) + 2u * (kk & 7u)) >> 2;
 }
 
 // The seven digits of two consecutive values (packed fp16 pairs) into their
@@ -85,7 +108,7 @@ __device__ __forceinline__ void put_pair(uint32_t* dig, int64_t t, int64_t nt, i
     uint32_t w[kD];
     digit_pairs<kD>(split_z<kD>(a, base_s), split_z<kD>(b, base_s), w);
 #pragma unroll
-    for (int i = 0; i < kD; ++i) dig[block_word(i, t, nt, k >> 6, nc, block, r, k)] = w[i];
+    for (int i = 0; i < kD; ++i) dig[block_word(i, t, nt, k >> 5, nc, block, r, k)] = w[i];
 }
 
 __device__ __forceinline__ uint32_t biased_exp(double v) { return ((uint32_t)__double2hiint(v) << 1) >> 21; }
@@ -113,11 +136,11 @@ __global__ void __launch_bounds__(256) k_split_a(const double2* __restrict__ src
     __shared__ uint32_t sh[32];
     const int64_t r = blockIdx.x;
     const int64_t pairs = K;   // pairs of consecutive reals of the 2K
-    const int64_t nt = Mp / kTM, nc = 2 * K / kKC, t = r / kTM;
+    const int64_t nt = Mp / kTM, nc = 2 * K / kKS, t = r / kTM;
     const int rl = (int)(r % kTM);
     if (r >= M) {
         for (int64_t p = threadIdx.x; p < pairs; p += blockDim.x)
-            for (int i = 0; i < kD; ++i) dig[block_word(i, t, nt, (2 * p) >> 6, nc, kASlice, rl, 2 * p)] = 0u;
+            for (int i = 0; i < kD; ++i) dig[block_word(i, t, nt, (2 * p) >> 5, nc, kASlice, rl, 2 * p)] = 0u;
         if (threadIdx.x == 0) escale[r] = 0;
         return;
     }
@@ -165,7 +188,7 @@ __global__ void __launch_bounds__(256) k_split_b(const double2* __restrict__ src
         fscale[32 * blockIdx.x + 16 + tid] = (int)m - 1021;
     }
     __syncthreads();
-    const int64_t nt = Nr / kTN, nc = 2 * K / kKC;
+    const int64_t nt = Nr / kTN, nc = 2 * K / kKS;
     const int q = tid & 15;    // pair within a 32-value segment
     for (int64_t k0 = 0; k0 < K; k0 += 32) {
         for (int e = tid; e < 32 * 16; e += 256) blk[e >> 4][e & 15] = src[(k0 + (e >> 4)) * ldb + c0 + (e & 15)];
@@ -201,7 +224,7 @@ struct GemmOzArgs {
     long long spin_limit;
 };
 
-enum GBar { kOpReady, kOpFree, kFull0, kFull1, kFree0, kFree1, kDrain, kGBars };
+enum GBar { kReady0, kReady1, kOpFree0, kOpFree1, kFull0, kFull1, kFree0, kFree1, kDrain, kGBars };
 
 // The executing thread's arrival on the mbarrier, announcing `bytes` of
 // asynchronous copies that complete on it.
@@ -224,15 +247,17 @@ __device__ __forceinline__ double i128_to_double(long long hi, unsigned long lon
 __global__ void __launch_bounds__(kThreads, 1) k_oz_zgemm(const __grid_constant__ GemmOzArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    unsigned char* sA = base;                    // 7 digit planes of the A tile
-    unsigned char* sB = sA + kD * kASlice;       // 7 digit planes of the Bt tile, stacked
+    // stage buffer b (0, 1): 7 digit planes of the A tile, then the 7 of the
+    // Bt tile stacked (row j * 32 + r of the stacked operand)
+    auto stageA = [&](int b) { return base + (size_t)b * kStageBytes; };
+    auto stageB = [&](int b) { return base + (size_t)b * kStageBytes + kD * kASlice; };
     __shared__ __align__(8) uint64_t bars[kGBars];
     __shared__ uint32_t tmem_base, abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t row0 = (int64_t)blockIdx.y * kTM, brow0 = (int64_t)blockIdx.x * kTN;
-    const int nchunks = (int)(a.Kr / kKC);
+    const int nchunks = (int)(a.Kr / kKC), nstages = (int)(a.Kr / kKS);
     if (tid == 0) {
-        const uint32_t counts[kGBars] = {1, 1, 1, 1, kRecThreads, kRecThreads, 1};
+        const uint32_t counts[kGBars] = {1, 1, 1, 1, 1, 1, kRecThreads, kRecThreads, 1};
         for (int b = 0; b < kGBars; ++b) mbar_init_count(&bars[b], counts[b]);
         abort_flag = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -256,21 +281,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_zgemm(const __grid_constant_
     };
     if (warp == kMmaWarp) {
         // ---------------------------------------------------- MMA issuer
+        // stage s (32 values of K) from buffer s & 1 into set (s >> 1) & 1;
+        // a set holds one chunk of 64 values (two stages), then is recombined
         if (lane == 0) {
             constexpr MmaTable<kD> tab;
-            const uint64_t da0 = tc::sdesc_sw128(smem_u32(sA)), db0 = tc::sdesc_sw128(smem_u32(sB));
             bool ok = true;
-            for (int c = 0; c < nchunks && ok; ++c) {
-                const int set = c & 1;
-                ok = wait_or_abort(smem_u32(&bars[kOpReady]), (uint32_t)c & 1u, a.spin_limit, &abort_flag);
-                if (ok && c >= 2)
+            for (int st = 0; st < nstages && ok; ++st) {
+                const int buf = st & 1, c = st >> 1, set = c & 1;
+                ok = wait_or_abort(smem_u32(&bars[buf ? kReady1 : kReady0]), (uint32_t)(st >> 1) & 1u, a.spin_limit,
+                                   &abort_flag);
+                if (ok && (st & 1) == 0 && c >= 2)
                     ok = wait_or_abort(smem_u32(&bars[set ? kFree1 : kFree0]), (uint32_t)((c >> 1) - 1) & 1u,
                                        a.spin_limit, &abort_flag);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t dset = tmem + (uint32_t)set * kSetCols;
+                const uint64_t da0 = sdesc_sw64(smem_u32(stageA(buf))), db0 = sdesc_sw64(smem_u32(stageB(buf)));
 #pragma unroll
-                for (int ks = 0; ks < kKC / 16; ++ks) {
+                for (int ks = 0; ks < kKS / 16; ++ks) {
 #pragma unroll
                     for (int m = 0; m <= kD; ++m) {
                         const int i = tab.i[m], j0 = tab.j0[m], j1 = tab.j1[m];
@@ -278,11 +306,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_zgemm(const __grid_constant_
                         const uint64_t da = da0 + (((uint32_t)(i - 1) * kASlice + 32u * ks) >> 4);
                         const uint64_t db = db0 + (((uint32_t)(j0 - 1) * kBSlice + 32u * ks) >> 4);
                         mma_f16(dset + (uint32_t)(i + j0 - 2) * kTN, da, db, tc::idesc(0u, nn, kTM),
-                                (ks > 0 || m > 1) ? 1u : 0u);
+                                ((st & 1) || ks > 0 || m > 1) ? 1u : 0u);
                     }
                 }
-                tc::mma_commit(&bars[set ? kFull1 : kFull0]);
-                tc::mma_commit(&bars[kOpFree]);
+                tc::mma_commit(&bars[buf ? kOpFree1 : kOpFree0]);
+                if (st & 1) tc::mma_commit(&bars[set ? kFull1 : kFull0]);
             }
             if (!ok) atomicExch(a.status, 1u);
             tc::mma_commit(&bars[kDrain]);
@@ -291,24 +319,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_zgemm(const __grid_constant_
         __syncwarp();
     } else if (warp == kLoadWarp) {
         // ------------------------------------------------------- loads
-        // one thread: per K-chunk, once the previous chunk's MMAs are done,
-        // the byte count on the ready barrier and 14 bulk copies
+        // one thread: stage s into buffer s & 1 once that buffer's previous
+        // stage (s - 2) has been consumed by its MMAs: the byte count on the
+        // buffer's ready barrier and 14 bulk copies
         if (lane == 0) {
             const int64_t ntA = a.Mp / kTM, ntB = a.Nr / kTN;
             const char* ga = reinterpret_cast<const char*>(a.adig);
             const char* gb = reinterpret_cast<const char*>(a.bdig);
-            for (int c = 0; c < nchunks; ++c) {
-                if (c > 0 && !wait_or_abort(smem_u32(&bars[kOpFree]), (uint32_t)(c - 1) & 1u, a.spin_limit, &abort_flag)) {
+            for (int st = 0; st < nstages; ++st) {
+                const int buf = st & 1;
+                if (st >= 2 && !wait_or_abort(smem_u32(&bars[buf ? kOpFree1 : kOpFree0]), (uint32_t)((st >> 1) - 1) & 1u,
+                                              a.spin_limit, &abort_flag)) {
                     atomicExch(a.status, 1u);
                     break;
                 }
-                mbar_expect_tx(&bars[kOpReady], kChunkBytes);
+                uint64_t* rb = &bars[buf ? kReady1 : kReady0];
+                mbar_expect_tx(rb, kStageBytes);
 #pragma unroll 1
                 for (int i = 0; i < kD; ++i) {
-                    bulk_g2s(smem_u32(sA) + (uint32_t)i * kASlice,
-                             ga + (((size_t)i * ntA + blockIdx.y) * nchunks + c) * kASlice, kASlice, &bars[kOpReady]);
-                    bulk_g2s(smem_u32(sB) + (uint32_t)i * kBSlice,
-                             gb + (((size_t)i * ntB + blockIdx.x) * nchunks + c) * kBSlice, kBSlice, &bars[kOpReady]);
+                    bulk_g2s(smem_u32(stageA(buf)) + (uint32_t)i * kASlice,
+                             ga + (((size_t)i * ntA + blockIdx.y) * nstages + st) * kASlice, kASlice, rb);
+                    bulk_g2s(smem_u32(stageB(buf)) + (uint32_t)i * kBSlice,
+                             gb + (((size_t)i * ntB + blockIdx.x) * nstages + st) * kBSlice, kBSlice, rb);
                 }
             }
         }
