@@ -317,6 +317,12 @@ int qe_batch_create(int count, const int* nqubits, int layers, const double* ang
 int qe_batch_run(qe_batch* b, double* energies);
 int qe_batch_tune(qe_batch* b, int reps, int* tile_bits, int* tiles_per_item, int* threads);
 int qe_batch_set_plan(qe_batch* b, int tile_bits, int tiles_per_item, int threads);
+/* Arithmetic of a complex128 batch: QE_ARITH_DF64 (the default; double-float
+ * gates on the FP32 pipes and float-pair energy sums) or QE_ARITH_FP64
+ * (native FP64 gates and FP64 energy sums; the FP64 pipe bounds it).  Rebuilds
+ * the work queue and graph with the current plan; complex64 batches ignore
+ * it.  QE_ERR_ARG for another value. */
+int qe_batch_set_arith(qe_batch* b, int arith);
 int qe_batch_info(const qe_batch* b, double* hbm_bytes, int* items);
 int qe_batch_free(qe_batch* b);
 

@@ -1122,6 +1122,14 @@ int qe_batch_set_plan(qe_batch* b, int tile_bits, int tiles_per_item, int thread
     QE_API_END
 }
 
+int qe_batch_set_arith(qe_batch* b, int arith) {
+    QE_API_BEGIN
+    check_batch(b);
+    if (arith != QE_ARITH_FP64 && arith != QE_ARITH_DF64) fail(QE_ERR_ARG, "arith must be QE_ARITH_FP64 or QE_ARITH_DF64");
+    batch_set_arith(b, arith);
+    QE_API_END
+}
+
 int qe_batch_tune(qe_batch* b, int reps, int* tile_bits, int* tiles_per_item, int* threads) {
     QE_API_BEGIN
     check_batch(b);

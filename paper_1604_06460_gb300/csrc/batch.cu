@@ -222,6 +222,52 @@ __device__ double block_sum(float s, float e, double* sh) {
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
     return tot;
 }
+// ... of FP64 values; result valid in thread 0
+__device__ double block_sum_d(double d, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = d;
+    __syncthreads();
+    double tot = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
+    return tot;
+}
+
+// Energy sums of one CTA: float pairs (s, e) with exact products for the
+// FP32 and double-float policies, plain FP64 fused multiply-adds for FP64.
+template <class P>
+struct EAcc {
+    float zs = 0.f, ze = 0.f, xs = 0.f, xe = 0.f;
+    // z += |v|^2 f (f a small integer), x += Re(conj(w) v)
+    __device__ __forceinline__ void add_z(const typename P::V& v, float f) {
+        float h, l;
+        sq(v, h, l);
+        const float p = fmul(h, f);
+        const float pe = __fmaf_rn(h, f, -p);
+        acc2(zs, ze, p, __fmaf_rn(l, f, pe));
+    }
+    __device__ __forceinline__ void add_x(const typename P::V& w, const typename P::V& v) {
+        float h, l;
+        re_dot(w, v, h, l);
+        acc2(xs, xe, h, l);
+    }
+    __device__ double z_total(double* sh) { return block_sum(zs, ze, sh); }
+    __device__ double x_total(double* sh) { return block_sum(xs, xe, sh); }
+};
+template <>
+struct EAcc<F64> {
+    double z = 0.0, x = 0.0;
+    __device__ __forceinline__ void add_z(const double2& v, float f) {
+        z = __fma_rn(__fma_rn(v.x, v.x, __dmul_rn(v.y, v.y)), (double)f, z);
+    }
+    __device__ __forceinline__ void add_x(const double2& w, const double2& v) {
+        x = __fma_rn(w.x, v.x, __fma_rn(w.y, v.y, x));
+    }
+    __device__ double z_total(double* sh) { return block_sum_d(z, sh); }
+    __device__ double x_total(double* sh) { return block_sum_d(x, sh); }
+};
+
 
 template <class P>
 __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ BatchArgs<P> a) {
@@ -262,7 +308,7 @@ __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ BatchArgs
         __syncthreads();
         if (!s_ok) continue;
         const typename P::M* U = a.U + cc.u_off;
-        float zs = 0.f, ze = 0.f, xs = 0.f, xe = 0.f;
+        EAcc<P> acc;
         if (it.kind == 0) {
             // ------------------------------------------------ small circuit
             const uint32_t N = 1u << n;
@@ -277,20 +323,12 @@ __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ BatchArgs
             }
             const uint32_t zmask = (n > 1) ? ((1u << (n - 1)) - 1u) : 0u;
             for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
-                float h, l;
-                sq(tile[pad16(i)], h, l);
-                const float f = (float)((n - 1) - 2 * __popc((i ^ (i >> 1)) & zmask));
-                float p = fmul(h, f);
-                float pe = __fmaf_rn(h, f, -p);
-                acc2(zs, ze, p, __fmaf_rn(l, f, pe));
+                acc.add_z(tile[pad16(i)], (float)((n - 1) - 2 * __popc((i ^ (i >> 1)) & zmask)));
                 for (int q = 0; q < n; ++q)
-                    if (!((i >> q) & 1u)) {
-                        re_dot(tile[pad16(i | (1u << q))], tile[pad16(i)], h, l);
-                        acc2(xs, xe, h, l);
-                    }
+                    if (!((i >> q) & 1u)) acc.add_x(tile[pad16(i | (1u << q))], tile[pad16(i)]);
             }
-            const double z = block_sum(zs, ze, shred);
-            const double x = block_sum(xs, xe, shred);
+            const double z = acc.z_total(shred);
+            const double x = acc.x_total(shred);
             if (threadIdx.x == 0) a.energies[it.circuit] = z + 2.0 * a.hx * x;
             __syncthreads();
             continue;
@@ -327,37 +365,25 @@ __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ BatchArgs
             if (it.kind == 2 && it.last_energy) {
                 for (uint32_t l = threadIdx.x; l < TN; l += blockDim.x) {
                     const uint64_t x = gidx(l);
-                    float h, lo;
-                    sq(tile[pad16(l)], h, lo);
-                    const float f = (float)((n - 1) - 2 * __popcll((x ^ (x >> 1)) & zmask));
-                    float p = fmul(h, f);
-                    float pe = __fmaf_rn(h, f, -p);
-                    acc2(zs, ze, p, __fmaf_rn(lo, f, pe));
+                    acc.add_z(tile[pad16(l)], (float)((n - 1) - 2 * __popcll((x ^ (x >> 1)) & zmask)));
                     for (int q = T; q < n; ++q) {
                         const int b = L + (q - T);
-                        if (!((l >> b) & 1u)) {
-                            re_dot(tile[pad16(l | (1u << b))], tile[pad16(l)], h, lo);
-                            acc2(xs, xe, h, lo);
-                        }
+                        if (!((l >> b) & 1u)) acc.add_x(tile[pad16(l | (1u << b))], tile[pad16(l)]);
                     }
                 }
             }
             if (it.kind == 3) {
                 for (uint32_t l = threadIdx.x; l < TN; l += blockDim.x)
                     for (int q = 0; q < T; ++q)
-                        if (!((l >> q) & 1u)) {
-                            float h, lo;
-                            re_dot(tile[pad16(l | (1u << q))], tile[pad16(l)], h, lo);
-                            acc2(xs, xe, h, lo);
-                        }
+                        if (!((l >> q) & 1u)) acc.add_x(tile[pad16(l | (1u << q))], tile[pad16(l)]);
             } else {
                 for (uint32_t l = threadIdx.x; l < TN; l += blockDim.x) st[gidx(l)] = P::store(tile[pad16(l)]);
             }
             __syncthreads();
         }
         if (it.slot >= 0) {
-            const double z = block_sum(zs, ze, shred);
-            const double x = block_sum(xs, xe, shred);
+            const double z = acc.z_total(shred);
+            const double x = acc.x_total(shred);
             if (threadIdx.x == 0) a.partials[it.slot] = make_double2(z, x);
         }
         // publish completion; the CTA that completes the circuit sums its energy
@@ -586,6 +612,9 @@ void prepare(qe_batch* b) {
     if (b->dtype == QE_C64) {
         build_plan<F32>(b);
         capture<F32>(b);
+    } else if (b->arith == QE_ARITH_FP64) {
+        build_plan<F64>(b);
+        capture<F64>(b);
     } else {
         build_plan<DF>(b);
         capture<DF>(b);
@@ -609,6 +638,11 @@ void batch_run(qe_batch* b, double* out) {
     b->launches += 1;
     if (*b->host_status != 0) fail(QE_ERR_TIMEOUT, "a batch work item waited too long for its dependencies");
     if (out) std::copy(b->host_energies, b->host_energies + b->count, out);
+}
+
+void batch_set_arith(qe_batch* b, int arith) {
+    b->arith = arith;
+    prepare(b);
 }
 
 void batch_set_plan(qe_batch* b, int T, int tiles_per_item, int threads) {

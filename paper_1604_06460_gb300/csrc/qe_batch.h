@@ -18,6 +18,7 @@ struct BatchPlan {
 
 struct qe_batch {
     int count = 0, layers = 0, dtype = QE_C128;
+    int arith = QE_ARITH_DF64;   // complex128 arithmetic (qe_batch_set_arith)
     double hx = 0.7;
     cudaStream_t stream = nullptr;
     std::vector<int> n;

@@ -154,6 +154,7 @@ void launch_div(qe_state* s, int N, const int* qa, const int* qb, const int* qc)
 void batch_create(qe_batch* b);
 void batch_run(qe_batch* b, double* energies);
 void batch_set_plan(qe_batch* b, int T, int tiles_per_item, int threads);
+void batch_set_arith(qe_batch* b, int arith);
 void batch_destroy(qe_batch* b);
 
 // planner

@@ -74,6 +74,7 @@ SIGNATURES = {
     "qe_batch_run": (_i, [_vp, _vp]),
     "qe_batch_tune": (_i, [_vp, _i, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)]),
     "qe_batch_set_plan": (_i, [_vp, _i, _i, _i]),
+    "qe_batch_set_arith": (_i, [_vp, _i]),
     "qe_batch_info": (_i, [_vp, C.POINTER(C.c_double), C.POINTER(_i)]),
     "qe_batch_free": (_i, [_vp]),
     "qe_cost_model_create": (_i, [_i, _i, _u64, C.POINTER(_vp)]),
@@ -389,6 +390,10 @@ class Batch:
 
     def set_plan(self, tile_bits, tiles_per_item, threads):
         _check(load().qe_batch_set_plan(self._h, int(tile_bits), int(tiles_per_item), int(threads)))
+
+    def set_arith(self, arith):
+        """ARITH_DF64 (default) or ARITH_FP64 for complex128 batches."""
+        _check(load().qe_batch_set_arith(self._h, int(arith)))
 
     def info(self):
         b, i = C.c_double(), C.c_int()

@@ -89,3 +89,30 @@ def test_batch_hbm_circuits_at_benchmark_sizes(qe, dtype, tol):
         xm, zm, cf = I.tfim_terms(int(ns[i]), hx)
         ref = oracle.expectation(psi, xm, zm, cf)
         assert abs(e[i] - ref) < tol * max(1.0, abs(ref)), (i, ns[i], e[i], ref)
+
+
+@pytest.mark.parametrize("plan", [None, (8, 3, 256), (9, 16, 128)])
+def test_batch_fp64_energies_vs_oracle(qe, plan):
+    # native FP64 gates and FP64 energy sums: shared-memory circuits and
+    # circuits forced into HBM by small tiles, at FP64 rounding against the
+    # oracle; switching back to double-float rebuilds the queue and agrees
+    layers, hx = 3, 0.7
+    ns = [1, 2, 3, 5, 7, 9, 11, 4, 6, 8, 10, 13, 14]
+    angles = batch_inputs(ns, layers, 300)
+    with qe.Batch(ns, angles, hx, "c128") as b:
+        if plan is not None:
+            b.set_plan(*plan)
+        b.set_arith(qe.ARITH_FP64)
+        e64 = b.run()
+        b.set_arith(qe.ARITH_DF64)
+        edf = b.run()
+        with pytest.raises(qe.QEError):
+            b.set_arith(7)
+    ref = np.array([oracle_energy(n, layers, 300 + i, hx) for i, n in enumerate(ns)])
+    assert np.max(np.abs(e64 - ref)) < 64 * n_terms_bound(ns)
+    assert np.max(np.abs(edf - ref)) < 1e-11
+
+
+def n_terms_bound(ns):
+    # FP64 rounding: a few units of 2^-53 per term of the energy
+    return 2.0 ** -53 * 2 * max(ns)
