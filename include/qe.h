@@ -50,7 +50,7 @@ typedef enum {
     QE_ERR_CUDA = -3,         /* a CUDA call failed; see qe_last_error() */
     QE_ERR_TIMEOUT = -4,      /* a bounded device wait gave up */
     QE_ERR_STATE = -5,        /* handle unusable (freed, failed earlier) */
-    QE_ERR_UNSUPPORTED = -6   /* valid request this build does not implement */
+    QE_ERR_UNSUPPORTED = -6   /* a valid request the library does not implement */
 } qe_status;
 
 /* Planner policy for subroutines that can be emulated or simulated. */
