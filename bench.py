@@ -79,6 +79,12 @@ KERNEL_CASES = {
              "2 transforms",
     "qpegemm": "one squaring of a 2^10 x 2^10 complex128 matrix on the tensor cores (digit splitting + product), "
                "2 products",
+    "addc": "emulated add-constant on qubits [0,16) of a 26-qubit complex128 state (cluster shared-memory "
+            "slices), 2 additions",
+    "mul": "emulated multiplication c += a b of 8-qubit registers (index = a b c) of a 26-qubit complex128 "
+           "state (planes in shared memory), 2 multiplications",
+    "batch": "512 ansatz circuits, n ~ U{10..20}, 8 layers, TFIM energy each, complex128 double-float, "
+             "default plan, 2 runs",
 }
 
 
@@ -111,6 +117,26 @@ def run_kernel_case(qe, I, which):
             for _ in range(3):
                 st.apply_gate([5, 17], U)
                 st.flush()
+    elif which == "addc":
+        with qe.State(26, "c128") as st:
+            st.set_policy(qe.POLICY_EMULATE, 1)
+            st.init_random(2)
+            for _ in range(2):
+                st.add_const(list(range(16)), 40503)
+            st.flush()
+    elif which == "mul":
+        with qe.State(26, "c128") as st:
+            st.set_policy(qe.POLICY_EMULATE, 1)
+            st.init_random(2)
+            for _ in range(2):
+                st.mul(list(range(16, 24)), list(range(8, 16)), list(range(8)))
+            st.flush()
+    elif which == "batch":
+        ns = I.batch_sizes(512, 10, 20, 3)
+        angles = [I.ansatz_angles(int(nq), 8, 300000 + i) for i, nq in enumerate(ns)]
+        with qe.Batch(ns, angles, 0.7, "c128") as b:
+            for _ in range(2):
+                b.run()
     elif which == "qpegemm":
         D = 1 << 10
         z = rng.standard_normal((D, D)) + 1j * rng.standard_normal((D, D))
@@ -319,6 +345,9 @@ def peak_hbm():
 KERNEL_SOURCES = {
     "gate_tc_k5_c128": ["tc_c128.cu", "qe_oz.cuh", "qe_tc.cuh", "qe_arith.cuh"],
     "oz_zgemm": ["oz_gemm.cu", "qe_oz.cuh", "qe_tc.cuh"],
+    "add": ["perm.cu", "qe_arith.cuh"],
+    "arith": ["arith.cu", "qe_arith.cuh"],
+    "batch": ["batch.cu", "qe_batch.h", "qe_arith.cuh"],
     "fft_twiddle": ["fft.cu", "qe_arith.cuh"],
     "digitrev": ["fft.cu", "qe_arith.cuh"],
     "gate_tc_k5": ["tcgen05.cu", "qe_tc.cuh", "qe_arith.cuh"],
