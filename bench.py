@@ -79,8 +79,8 @@ KERNEL_CASES = {
              "2 transforms",
     "qpegemm": "one squaring of a 2^10 x 2^10 complex128 matrix on the tensor cores (digit splitting + product), "
                "2 products",
-    "addc": "emulated add-constant on qubits [0,16) of a 26-qubit complex128 state (cluster shared-memory "
-            "slices), 2 additions",
+    "addc": "emulated add-constant on qubits [0,16) of a 26-qubit complex128 state (1 MiB slices, eight CTAs "
+            "each, bulk copies), 2 additions",
     "mul": "emulated multiplication c += a b of 8-qubit registers (index = a b c) of a 26-qubit complex128 "
            "state (planes in shared memory), 2 multiplications",
     "batch": "512 ansatz circuits, n ~ U{10..20}, 8 layers, TFIM energy each, complex128 double-float, "

@@ -226,19 +226,6 @@ struct GemmOzArgs {
 
 enum GBar { kReady0, kReady1, kOpFree0, kOpFree1, kFull0, kFull1, kFree0, kFree1, kDrain, kGBars };
 
-// The executing thread's arrival on the mbarrier, announcing `bytes` of
-// asynchronous copies that complete on it.
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
-}
-// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
-// from global to this CTA's shared memory, completion counted on the mbarrier.
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* mbar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(smem_u32(mbar))
-                 : "memory");
-}
-
 __device__ __forceinline__ double i128_to_double(long long hi, unsigned long long lo) {
     if ((hi == 0 && (long long)lo >= 0) || (hi == -1 && (long long)lo < 0)) return __ll2double_rn((long long)lo);
     return __fma_rn((double)hi, 18446744073709551616.0, __ull2double_rn(lo));

@@ -6,12 +6,18 @@
 //
 // For a fixed assignment of the non-register qubits (a "column") the map is a
 // rotation by c of 2^m entries, which splits into g = gcd(c, 2^m) cycles of
-// length 2^m / g.  Three in-place strategies:
-//   slice   - register [lo, lo+m) whose slice of 2^(lo+m) contiguous
-//             amplitudes fits one CTA's shared memory: load, write rotated;
-//   cluster - slices up to 8x larger: eight CTAs of a thread-block cluster
-//             each stage 1/8 of the slice and read the rotated source from
-//             the owner's shared memory (distributed shared memory);
+// length 2^m / g.  In-place strategies:
+//   bulk    - register [lo, lo+m), lo < 5, whose slice of 2^(lo+m) contiguous
+//             amplitudes fits one CTA's (or a cluster of eight CTAs')
+//             shared memory, with 16-byte-aligned rotation runs: each CTA
+//             bulk-copies its contiguous part of the slice in, waits at the
+//             cluster barrier until every part is held, and bulk-copies it
+//             back out at its rotated place (one or two contiguous runs);
+//   slice   - the same slices when the runs are not 16-byte aligned
+//             (complex64 with an odd shift): load, write rotated;
+//   cluster - slices up to 8x larger in that case: eight CTAs of a
+//             thread-block cluster each stage 1/8 of the slice and read the
+//             rotated source from the owner's shared memory;
 //   walk    - otherwise every thread follows one cycle of one column,
 //             prefetching several positions ahead (coalesced when the
 //             lowest non-register qubits vary across the warp).
@@ -21,6 +27,7 @@
 
 #include "qe_arith.cuh"
 #include "qe_internal.h"
+#include "qe_oz.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -157,6 +164,55 @@ __global__ void __launch_bounds__(512) k_add_cluster(S* __restrict__ x, int Sbit
     cl.sync();
 }
 
+// Status of the bulk path: set when a wait for a CTA's incoming copy ran out.
+__device__ uint32_t g_add_status;
+
+// One CTA (nblk = 1) or one cluster of nblk CTAs per slice of 2^S amplitudes;
+// CTA `rank` holds the contiguous part [rank E, rank E + E), E = 2^S / nblk,
+// and writes it back rotated by `shift` within the slice.
+template <class S>
+__global__ void __launch_bounds__(32) k_add_bulk(S* __restrict__ x, int Sbits, uint32_t shift, long long limit) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t abort_flag;
+    cg::cluster_group cl = cg::this_cluster();
+    const uint32_t nblk = cl.num_blocks(), rank = cl.block_rank();
+    const uint32_t total = 1u << Sbits, E = total / nblk, mask = total - 1u;
+    S* const base = x + ((uint64_t)(blockIdx.x / nblk) << Sbits);
+    const uint32_t sm = oz::smem_u32(smem_raw);
+    constexpr uint32_t kPiece = 16384;
+    if (threadIdx.x == 0) {
+        oz::mbar_init_count(&bar, 1);
+        abort_flag = 0u;
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    __syncwarp();
+    if (threadIdx.x == 0) {
+        const uint32_t bytes = E * (uint32_t)sizeof(S);
+        oz::mbar_expect_tx(&bar, bytes);
+        const char* src = reinterpret_cast<const char*>(base + (uint64_t)rank * E);
+        for (uint32_t off = 0; off < bytes; off += kPiece)
+            oz::bulk_g2s(sm + off, src + off, min(kPiece, bytes - off), &bar);
+    }
+    const bool ok = oz::wait_or_abort(oz::smem_u32(&bar), 0u, limit, &abort_flag);
+    // every CTA of the cluster holds its part before any part is written back
+    cl.sync();
+    if (threadIdx.x == 0 && ok) {
+        const uint32_t d0 = (rank * E + shift) & mask;
+        const uint32_t first = min(E, total - d0);
+        char* dst0 = reinterpret_cast<char*>(base + d0);
+        for (uint32_t off = 0; off < first * (uint32_t)sizeof(S); off += kPiece)
+            oz::bulk_s2g(dst0 + off, sm + off, min(kPiece, first * (uint32_t)sizeof(S) - off));
+        const uint32_t rest = (E - first) * (uint32_t)sizeof(S), rest0 = first * (uint32_t)sizeof(S);
+        char* dst1 = reinterpret_cast<char*>(base);
+        for (uint32_t off = 0; off < rest; off += kPiece)
+            oz::bulk_s2g(dst1 + off, sm + rest0 + off, min(kPiece, rest - off));
+        oz::bulk_commit();
+        oz::bulk_wait_all();
+    }
+    if (!ok && threadIdx.x == 0) atomicExch(&g_add_status, 1u);
+}
+
 template <class S>
 void add_impl(qe_state* s, int m, const int* qubits, uint64_t c) {
     const uint64_t mmask = (m >= 64) ? ~0ull : ((1ull << m) - 1ull);
@@ -170,6 +226,43 @@ void add_impl(qe_state* s, int m, const int* qubits, uint64_t c) {
     const int cap_bits = (sizeof(S) >= 16) ? 12 : 13;      // 64 KB per CTA
     const int ccap_bits = (sizeof(S) >= 16) ? 13 : 14;     // 128 KB per CTA, 8 per cluster
     S* x = reinterpret_cast<S*>(s->d);
+    // bulk: parts of <= 128 KB per CTA (one CTA, or a cluster of eight), and
+    // rotation runs on 16-byte boundaries
+    const int bulk_bits = (sizeof(S) >= 16) ? 13 : 14;
+    const uint64_t shift = c << lo;
+    const int nblk = (contiguous && Sbits >= 3 && Sbits <= bulk_bits) ? 1 : 8;
+    const bool use_bulk = contiguous && lo < 5 && Sbits >= 4 && Sbits <= bulk_bits + 3 &&
+                          ((shift * sizeof(S)) % 16 == 0) && ((((uint64_t)sizeof(S) << Sbits) / nblk) % 16 == 0);
+    if (use_bulk) {
+        Launch L(s, nblk == 1 ? "add_bulk" : "add_bulk_cluster", 2.0 * dim(s) * amp_bytes(s));
+        const uint64_t nslices = 1ull << (n - Sbits);
+        const size_t smem = (sizeof(S) << Sbits) / nblk;
+        QE_CUDA(cudaFuncSetAttribute(k_add_bulk<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        void* st_addr = nullptr;
+        QE_CUDA(cudaGetSymbolAddress(&st_addr, g_add_status));
+        QE_CUDA(cudaMemsetAsync(st_addr, 0, sizeof(uint32_t), s->stream));
+        cudaLaunchConfig_t cfg = {};
+        if (nslices * nblk > 0x7FFFFFFFull) fail(QE_ERR_UNSUPPORTED, "too many slices for one launch");
+        cfg.gridDim = dim3((unsigned)(nslices * nblk));
+        cfg.blockDim = dim3(32);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)nblk;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const long long limit = 1ll << 20;   // polls of up to 1 us each
+        QE_CUDA(cudaLaunchKernelEx(&cfg, k_add_bulk<S>, x, Sbits, (uint32_t)shift, limit));
+        QE_CUDA(cudaGetLastError());
+        uint32_t st = 0;
+        QE_CUDA(cudaMemcpyAsync(&st, st_addr, sizeof(uint32_t), cudaMemcpyDeviceToHost, s->stream));
+        QE_CUDA(cudaStreamSynchronize(s->stream));
+        if (st != 0) fail(QE_ERR_TIMEOUT, "an add-constant copy wait ran out");
+        return;
+    }
     const bool use_slice = contiguous && lo < 5 && Sbits <= cap_bits;
     const bool use_cluster = !use_slice && contiguous && lo < 5 && Sbits <= ccap_bits + 3 && Sbits >= 3;
     Launch L(s, use_slice ? "add_slice" : use_cluster ? "add_cluster" : "add_walk",

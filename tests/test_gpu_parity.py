@@ -387,6 +387,23 @@ def test_add_const_bit_exact(qe, n, qubits, c):
     assert np.array_equal(got, oracle.add_const(psi, qubits, c))
 
 
+@pytest.mark.parametrize("n,qubits,c", [
+    (12, list(range(0, 8)), 77),          # odd shift: 8-byte runs, shared-memory slice
+    (12, list(range(0, 8)), 78),          # even shift: bulk copies, one CTA
+    (18, list(range(0, 17)), 4097),       # odd shift, cluster through shared memory
+    (18, list(range(0, 17)), 4098),       # even shift, bulk copies, cluster of eight
+    (15, list(range(1, 13)), 5),          # lo = 1: the shift 10 is even
+])
+def test_add_const_c64_paths_bit_exact(qe, n, qubits, c):
+    psi = I.random_state(n, c).astype(np.complex64)
+    with make(qe, n, "c64", psi=psi) as st:
+        st.set_policy(qe.POLICY_EMULATE, 1)
+        st.add_const(qubits, c)
+        got = st.get()
+    want = oracle.add_const(psi.astype(np.complex128), qubits, c).astype(np.complex64)
+    assert np.array_equal(got, want)
+
+
 def test_add_const_simulated_bit_exact(qe):
     n, qubits, c = 12, list(range(2, 10)), 173
     psi = I.random_state(n, 5)
