@@ -72,8 +72,7 @@ KERNEL_CASES = {
                "3 passes",
     "tc64": "complex64 5-qubit block on qubits (3,7,11,15,19) of a 26-qubit state, 3 passes",
     "direct2": "complex128 2-qubit block on qubits (5,17) of a 26-qubit state (fusion width 2), 3 passes",
-    "expect": "TFIM energy of a 26-qubit complex128 state, FP64 mode, 2 evaluations",
-    "expectdf": "TFIM energy of a 26-qubit complex128 state, double-float mode, 2 evaluations",
+    "expect": "TFIM energy of a 26-qubit complex128 state (fixed-point register rounds), 2 evaluations",
     "fft": "emulated 25-qubit QFT of a complex128 state, FP64 mode (5-qubit digit passes), 2 transforms",
     "fftdf": "emulated 26-qubit QFT of a complex128 state, double-float mode (radix-2 shared-memory passes), "
              "2 transforms",
@@ -144,7 +143,7 @@ def run_kernel_case(qe, I, which):
             a.set(np.ascontiguousarray(z).reshape(-1))
             for _ in range(2):
                 c.matmul(a, a)
-    elif which in ("expect", "expectdf"):
+    elif which == "expect":
         with qe.State(26, "c128") as st:
             if df:
                 st.set_arith(qe.ARITH_DF64)
@@ -352,7 +351,7 @@ KERNEL_SOURCES = {
     "digitrev": ["fft.cu", "qe_arith.cuh"],
     "gate_tc_k5": ["tcgen05.cu", "qe_tc.cuh", "qe_arith.cuh"],
     "gate_direct": ["gates.cu", "qe_arith.cuh"],
-    "expect": ["reduce.cu", "qe_arith.cuh"],
+    "expect_fx": ["reduce.cu", "qe_oz.cuh", "qe_tc.cuh", "qe_arith.cuh"],
     "fft": ["fft.cu", "qe_arith.cuh"],
 }
 

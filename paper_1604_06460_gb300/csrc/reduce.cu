@@ -9,9 +9,12 @@
 // writes one FP64 pair (sum, Neumaier compensation) per block; a final
 // single-block kernel adds the block partials in FP64 with Neumaier's
 // compensation in a fixed order, so results are deterministic.
-// In the FP64 mode (complex128) the products and per-thread sums are native
-// FP64 (53-bit significands) instead, with the same FP64 compensated
-// combination of the block partials.
+// In the FP64 mode (complex128) the products and per-thread sums of the
+// probability and pair-indexed expectation kernels are native FP64 (53-bit
+// significands) instead, with the same FP64 compensated combination of the
+// block partials.  Expectation values of complex128 states whose terms fit
+// the register rounds are computed in exact fixed point instead, in either
+// mode (k_expect_fx).
 #include <algorithm>
 #include <cstdlib>
 #include <type_traits>
@@ -19,6 +22,7 @@
 
 #include "qe_arith.cuh"
 #include "qe_internal.h"
+#include "qe_oz.cuh"
 
 namespace qe {
 
@@ -152,12 +156,6 @@ struct AccD {
     double s;
 };
 __device__ __forceinline__ double abs2d(const double2& v) { return __fma_rn(v.x, v.x, __dmul_rn(v.y, v.y)); }
-__device__ __forceinline__ double2 vneg(const double2& v) { return make_double2(-v.x, -v.y); }
-// acc += Re (im = false) or Im (im = true) of conj(w) v
-__device__ __forceinline__ void corr_acc(AccD& a, const double2& w, const double2& v, bool im) {
-    if (!im) a.s = __fma_rn(w.x, v.x, __fma_rn(w.y, v.y, a.s));
-    else a.s = __fma_rn(w.x, v.y, __fma_rn(-w.y, v.x, a.s));
-}
 __device__ __forceinline__ double block_reduce_d(double a, double* sh) {
     for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -523,6 +521,14 @@ struct RoundArgs {
     uint64_t xzo[kXT2];       // and outside the tile
     double wx;                // 2 x the common coefficient of the X/Y terms
     double2* partial;
+    // fixed-point kernel: per weight group, the Z masks (bit m) inside the
+    // tile, wholly outside it, and with bits on both sides
+    uint64_t zin[kZW], zout[kZW], zmix[kZW];
+    uint8_t xtb[4][9];        // round r: its terms with X/Y bits x (in the triple) are [xtb[r][x], xtb[r][x + 1])
+    uint8_t xplain[4][8];     // round r: how many X strings without Z bits have the pattern x (not in the lists)
+    int rmask;                // bit r: round r has X/Y terms
+    uint32_t* status;         // raised when a copy wait ran out
+    long long spin_limit;
 };
 
 template <int EB>
@@ -537,22 +543,8 @@ __device__ __forceinline__ uint32_t round_base(uint32_t tid, int r) {
     return (tid & ((1u << s) - 1u)) | ((tid >> s) << (s + 3));
 }
 
-// acc += (-1)^neg Re (IM = false) or Im (IM = true) of conj(w) v; SIGNED =
-// false: no per-pair sign (neg is ignored).  FP64: the sign enters as an
-// integer XOR of the operands' sign bits, so the FP64 pipe runs exactly two
-// fused multiply-adds per pair.
-template <bool IM, bool SIGNED>
-__device__ __forceinline__ void pair_acc(AccD& acc, const double2& w, const double2& v, uint32_t neg) {
-    double p = IM ? v.y : v.x, q = IM ? v.x : v.y;
-    double wy = w.y;
-    if constexpr (SIGNED) {
-        const long long sgn = (long long)neg << 63;
-        p = __longlong_as_double(__double_as_longlong(p) ^ sgn);
-        q = __longlong_as_double(__double_as_longlong(q) ^ sgn);
-    }
-    if constexpr (IM) acc.s = __fma_rn(w.x, p, __fma_rn(-wy, q, acc.s));
-    else acc.s = __fma_rn(w.x, p, __fma_rn(wy, q, acc.s));
-}
+// acc += (-1)^neg Re (IM = false) or Im (IM = true) of conj(w) v (float
+// pairs); SIGNED = false: no per-pair sign (neg is ignored)
 template <bool IM, bool SIGNED, class V>
 __device__ __forceinline__ void pair_acc(Acc& acc, const V& w, const V& v, uint32_t neg) {
     if constexpr (SIGNED) corr_acc(acc, neg ? vneg(w) : w, v, IM);
@@ -569,42 +561,26 @@ __device__ __forceinline__ void round_pairs(const V (&v)[8], uint32_t zp, uint32
     }
 }
 
-// One term: XT, Im and whether it carries a Z part select the code path
-// (uniform across the block); in FP64 a term without Z part has one sign for
-// all its pairs and accumulates into xacc or, negated, into xneg (the
-// float-pair paths sign each pair with selects).
+// One term: XT and Im select the code path (uniform across the block); each
+// pair is signed with selects.
 template <int XT, class V, class A>
-__device__ __forceinline__ void round_term(const V (&v)[8], uint32_t zp, uint32_t f, bool im, bool signed_term,
-                                           A& xacc, A& xneg) {
-    if constexpr (!std::is_same<A, AccD>::value) {
-        if (im) round_pairs<XT, true, true>(v, zp, f, xacc);
-        else round_pairs<XT, false, true>(v, zp, f, xacc);
-        return;
-    }
-    if (signed_term) {
-        if (im) round_pairs<XT, true, true>(v, zp, f, xacc);
-        else round_pairs<XT, false, true>(v, zp, f, xacc);
-    } else if (f) {
-        if (im) round_pairs<XT, true, false>(v, 0u, 0u, xneg);
-        else round_pairs<XT, false, false>(v, 0u, 0u, xneg);
-    } else {
-        if (im) round_pairs<XT, true, false>(v, 0u, 0u, xacc);
-        else round_pairs<XT, false, false>(v, 0u, 0u, xacc);
-    }
+__device__ __forceinline__ void round_term(const V (&v)[8], uint32_t zp, uint32_t f, bool im, A& xacc) {
+    if (im) round_pairs<XT, true, true>(v, zp, f, xacc);
+    else round_pairs<XT, false, true>(v, zp, f, xacc);
 }
 
-template <class S, bool NAT>
+// complex64 (complex128 states take k_expect_fx)
+template <class S>
 __global__ void __launch_bounds__(kThr2, 1) k_expect_rounds(const __grid_constant__ RoundArgs<S> a) {
-    using V = std::conditional_t<NAT, S, decltype(rview(S{}))>;
-    using A = std::conditional_t<NAT, AccD, Acc>;
-    using W = std::conditional_t<NAT, double, float>;
+    static_assert(sizeof(S) == 8, "complex64 tiles");
+    using V = S;
+    using A = Acc;
+    using W = float;
     constexpr int EB = (int)sizeof(S);
     constexpr uint32_t Tn = 1u << kT2;
-    static_assert(sizeof(V) == sizeof(S), "tiles are converted in place");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* const tiles = reinterpret_cast<V*>(smem_raw);
     __shared__ Acc sh[32];
-    __shared__ double shd[32];
     __shared__ uint64_t offA[64];
     __shared__ uint64_t spread[256];          // byte j of spread[p] = bit j of p
     __shared__ W s_cnt[kZW][kZT + 1];         // group g, o odd masks: (masks of g) - 2 o
@@ -638,11 +614,10 @@ __global__ void __launch_bounds__(kThr2, 1) k_expect_rounds(const __grid_constan
         const uint32_t lt = round_base(tid, r);
         for (int k = a.rb[r]; k < a.rb[r + 1]; ++k) tx |= (uint32_t)(__popc(lt & a.xzl[k]) & 1) << k;
     }
-    A zacc[kZW], xacc, xneg;
+    A zacc[kZW], xacc;
 #pragma unroll
     for (int g = 0; g < kZW; ++g) acc_zero(zacc[g]);
     acc_zero(xacc);
-    acc_zero(xneg);
     __syncthreads();
     const uint32_t lowmask = (1u << a.L) - 1u;
     auto load = [&](uint64_t t, V* buf) {
@@ -664,13 +639,6 @@ __global__ void __launch_bounds__(kThr2, 1) k_expect_rounds(const __grid_constan
     for (uint64_t t = blockIdx.x; t < a.ntiles; t += step, ++it) {
         V* const tile = tiles + (size_t)(it % kNB2) * Tn;
         asm volatile("cp.async.wait_group %0;" ::"n"(kNB2 - 2) : "memory");
-        if constexpr (sizeof(S) == 16 && !NAT) {   // complex128: split into double-float in place
-#pragma unroll
-            for (int i = 0; i < (int)(Tn / kThr2); ++i) {
-                const uint32_t p = swz<EB>(tid + (uint32_t)i * kThr2);
-                tile[p] = rview(*reinterpret_cast<const S*>(tile + p));
-            }
-        }
         if (tid < 32) {   // outside parities of this tile
             const uint64_t base = insert_zero_bits(t << a.L, a.hq_sorted, a.kh);
             const int lane = (int)tid;
@@ -715,23 +683,14 @@ __global__ void __launch_bounds__(kThr2, 1) k_expect_rounds(const __grid_constan
                 }
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    if constexpr (NAT) {
-                        const double pd = abs2d(v[j]);
+                    float ph, pl;
+                    abs2(v[j], ph, pl);
 #pragma unroll
-                        for (int g = 0; g < kZW; ++g) {
-                            if (g >= a.nzg) break;
-                            zacc[g].s = __fma_rn(pd, s_cnt[g][(cnt[g] >> (8 * j)) & 0xFFu], zacc[g].s);
-                        }
-                    } else {
-                        float ph, pl;
-                        abs2(v[j], ph, pl);
-#pragma unroll
-                        for (int g = 0; g < kZW; ++g) {
-                            if (g >= a.nzg) break;
-                            const float f = s_cnt[g][(cnt[g] >> (8 * j)) & 0xFFu];
-                            const float p = fmul(ph, f);
-                            acc_add(zacc[g], p, __fmaf_rn(pl, f, __fmaf_rn(ph, f, -p)));
-                        }
+                    for (int g = 0; g < kZW; ++g) {
+                        if (g >= a.nzg) break;
+                        const float f = s_cnt[g][(cnt[g] >> (8 * j)) & 0xFFu];
+                        const float p = fmul(ph, f);
+                        acc_add(zacc[g], p, __fmaf_rn(pl, f, __fmaf_rn(ph, f, -p)));
                     }
                 }
             }
@@ -739,15 +698,15 @@ __global__ void __launch_bounds__(kThr2, 1) k_expect_rounds(const __grid_constan
                 const uint32_t w = a.xw[k];
                 const uint32_t f = ((xflip >> k) & 1u) ^ ((w >> 12) & 1u);
                 const uint32_t zp = (w >> 3) & 0xFFu;
-                const bool im = ((w >> 11) & 1u) != 0, sg = ((w >> 13) & 1u) != 0;
+                const bool im = ((w >> 11) & 1u) != 0;
                 switch (w & 7u) {
-                    case 1: round_term<1>(v, zp, f, im, sg, xacc, xneg); break;
-                    case 2: round_term<2>(v, zp, f, im, sg, xacc, xneg); break;
-                    case 3: round_term<3>(v, zp, f, im, sg, xacc, xneg); break;
-                    case 4: round_term<4>(v, zp, f, im, sg, xacc, xneg); break;
-                    case 5: round_term<5>(v, zp, f, im, sg, xacc, xneg); break;
-                    case 6: round_term<6>(v, zp, f, im, sg, xacc, xneg); break;
-                    default: round_term<7>(v, zp, f, im, sg, xacc, xneg); break;
+                    case 1: round_term<1>(v, zp, f, im, xacc); break;
+                    case 2: round_term<2>(v, zp, f, im, xacc); break;
+                    case 3: round_term<3>(v, zp, f, im, xacc); break;
+                    case 4: round_term<4>(v, zp, f, im, xacc); break;
+                    case 5: round_term<5>(v, zp, f, im, xacc); break;
+                    case 6: round_term<6>(v, zp, f, im, xacc); break;
+                    default: round_term<7>(v, zp, f, im, xacc); break;
                 }
             }
         }
@@ -758,42 +717,409 @@ __global__ void __launch_bounds__(kThr2, 1) k_expect_rounds(const __grid_constan
 #pragma unroll
     for (int g = 0; g < kZW; ++g) {
         if (g >= a.nzg) break;
-        if constexpr (NAT) {
-            const double r = block_reduce_d(zacc[g].s, shd);
-            if (tid == 0) neumaier(s, c, r * a.zw[g]);
-        } else {
-            Acc r = block_reduce(zacc[g], sh);
-            if (tid == 0) {
-                df d = df_norm(r.s, r.e);
-                neumaier(s, c, df2d(d.h, d.l) * a.zw[g]);
-            }
+        Acc r = block_reduce(zacc[g], sh);
+        if (tid == 0) {
+            df d = df_norm(r.s, r.e);
+            neumaier(s, c, df2d(d.h, d.l) * a.zw[g]);
         }
     }
     if (a.nxt > 0) {
-        if constexpr (NAT) {
-            const double r = block_reduce_d(xacc.s, shd);
-            if (tid == 0) neumaier(s, c, r * a.wx);
-            const double rn = block_reduce_d(xneg.s, shd);
-            if (tid == 0) neumaier(s, c, -rn * a.wx);
-        } else {
-            Acc r = block_reduce(xacc, sh);
-            if (tid == 0) {
-                df d = df_norm(r.s, r.e);
-                neumaier(s, c, df2d(d.h, d.l) * a.wx);
-            }
-            r = block_reduce(xneg, sh);
-            if (tid == 0) {
-                df d = df_norm(r.s, r.e);
-                neumaier(s, c, -df2d(d.h, d.l) * a.wx);
+        Acc r = block_reduce(xacc, sh);
+        if (tid == 0) {
+            df d = df_norm(r.s, r.e);
+            neumaier(s, c, df2d(d.h, d.l) * a.wx);
+        }
+    }
+    if (tid == 0) a.partial[blockIdx.x] = make_double2(s, c);
+}
+
+// ------------------------ expectation by register rounds in fixed point
+// complex128 (both arithmetic modes): the round schedule of k_expect_rounds
+// on integers.  Each tile arrives by bulk copies (one per contiguous run of
+// the layout, or 16 KB pieces) on an mbarrier, three buffers deep, unswizzled:
+// round 0's loads, whose eight amplitudes per thread are adjacent, go in a
+// rotated order (amplitude j ^ (tid & 7) first), and the loads of rounds 1-3
+// are conflict-free as they stand.
+//
+// Fixed point.  With E the largest biased exponent of the tile's components,
+// component v becomes the integer q = v 2^(1076 - E), truncated toward zero
+// (|q| < 2^54; the largest component keeps its 53 significant bits, the
+// others lose at most half a unit of the 53-bit grid 2^(E - 1075)).  A tile
+// whose largest component is below 2^-959 is taken as zero (the products of
+// such values underflow FP64 as well).  q is held as two limbs q = h 2^28 + l,
+// |h| < 2^26, |l| < 2^28, so the product of two components is three
+// 32 x 32 -> 64-bit integer multiply-adds: h h' at unit 2^56 and h l' + l h'
+// at unit 2^28 are summed exactly in int64 accumulators (two independent
+// chains each, positive and negative terms apart); the dropped l l' is below
+// 2^-52 of the largest product.  A launch has at most 24 X/Y terms, so a
+// thread's tile sums stay below 2^62.6.  At the end of a tile they are folded
+// into one int64 at unit 2^56 (truncating less than one unit), summed exactly
+// over four lanes, and one lane in four adds the tile's value, scaled by
+// 2^(2 E - 2152), to its FP64 sum.  Z-only masks weigh |q|^2 (at unit 2^56,
+// truncated the same way) by the integer count of even minus odd parities:
+// masks inside the tile are counted once per launch, masks wholly outside it
+// once per tile by a population count, and only masks with bits on both
+// sides per amplitude.  The products thus run on the integer pipes, whose
+// multiply-add rate is many times the FP64 pipe's.
+struct Fx {
+    int xh, xl, yh, yl;   // Re q = xh 2^28 + xl, Im q = yh 2^28 + yl
+};
+constexpr uint32_t kFxFlush = 64;   // tiles whose largest biased exponent is below this: zero
+
+__device__ __forceinline__ uint32_t fx_exp(double v) { return ((uint32_t)__double2hiint(v) >> 20) & 0x7FFu; }
+
+// the limbs of q = trunc(v 2^(1076 - emx)), emx >= the exponent of v (and
+// emx >= 64, so zero and subnormal v give d = 63 and q = 0)
+__device__ __forceinline__ void fx_limbs(double v, uint32_t emx, int& h, int& l) {
+    const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
+    const uint64_t m2 = ((((uint64_t)((hi & 0xFFFFFu) | 0x100000u)) << 32) | lo) << 1;   // 2 m, below 2^54
+    const uint32_t d = min(emx - ((hi >> 20) & 0x7FFu), 63u);
+    const uint64_t q2 = m2 >> d;
+    const int s = (int)hi >> 31;
+    h = ((int)(q2 >> 28) ^ s) - s;
+    l = ((int)((uint32_t)q2 & 0xFFFFFFFu) ^ s) - s;
+}
+
+// X/Y accumulators: two chains at unit 2^56 (H) and two at unit 2^28 (M)
+struct FxAcc {
+    long long h0, h1, m0, m1;
+};
+
+// acc += (-1)^neg Re (IM = false) or Im (IM = true) of conj(w) v
+template <bool IM, bool SIGNED>
+__device__ __forceinline__ void pair_fx(FxAcc& a, Fx w, const Fx& v, uint32_t neg) {
+    if constexpr (SIGNED) {
+        const int m = -(int)neg;
+        w.xh = (w.xh ^ m) - m;
+        w.xl = (w.xl ^ m) - m;
+        w.yh = (w.yh ^ m) - m;
+        w.yl = (w.yl ^ m) - m;
+    }
+    // C products (not inline PTX): each compiles to one 32 x 32 + 64 multiply-add
+    if constexpr (!IM) {   // w.x v.x + w.y v.y
+        a.h0 += (long long)w.xh * v.xh;
+        a.h1 += (long long)w.yh * v.yh;
+        a.m0 += (long long)w.xh * v.xl;
+        a.m0 += (long long)w.xl * v.xh;
+        a.m1 += (long long)w.yh * v.yl;
+        a.m1 += (long long)w.yl * v.yh;
+    } else {               // w.x v.y - w.y v.x
+        a.h0 += (long long)w.xh * v.yh;
+        a.h1 -= (long long)w.yh * v.xh;
+        a.m0 += (long long)w.xh * v.yl;
+        a.m0 += (long long)w.xl * v.yh;
+        a.m1 -= (long long)w.yh * v.xl;
+        a.m1 -= (long long)w.yl * v.xh;
+    }
+}
+
+template <int XT, bool IM, bool SIGNED>
+__device__ __forceinline__ void round_pairs_fx(const Fx (&v)[8], uint32_t zp, uint32_t f, FxAcc& a) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        if (j & (XT & -XT)) continue;
+        pair_fx<IM, SIGNED>(a, v[j ^ XT], v[j], f ^ ((zp >> j) & 1u));
+    }
+}
+
+// one term: pairs signed by the Z parity (zp = 0 without a Z part) and the
+// thread's sign f, unless no pair of the warp is negated
+template <int XT>
+__device__ __forceinline__ void round_term_fx(const Fx (&v)[8], uint32_t zp, uint32_t f, bool im, bool signed_term,
+                                              FxAcc& acc) {
+    if (signed_term || __any_sync(0xffffffffu, f != 0u)) {
+        const uint32_t z = signed_term ? zp : 0u;
+        if (im) round_pairs_fx<XT, true, true>(v, z, f, acc);
+        else round_pairs_fx<XT, false, true>(v, z, f, acc);
+    } else {
+        if (im) round_pairs_fx<XT, true, false>(v, 0u, 0u, acc);
+        else round_pairs_fx<XT, false, false>(v, 0u, 0u, acc);
+    }
+}
+
+// the terms of round r whose X/Y bits in the triple are XT (sorted so on the
+// host: one code block per pattern, no indirect branch)
+template <int XT>
+__device__ __forceinline__ void round_xt(const RoundArgs<double2>& a, int r, uint32_t rot, uint32_t xflip,
+                                         const Fx (&v)[8], FxAcc& acc) {
+#pragma unroll 1
+    for (int k = a.xtb[r][XT]; k < a.xtb[r][XT + 1]; ++k) {
+        const uint32_t w = a.xw[k];
+        uint32_t f = ((xflip >> k) & 1u) ^ ((w >> 12) & 1u);
+        const uint32_t zp = (w >> 3) & 0xFFu;
+        const bool im = ((w >> 11) & 1u) != 0, sg = ((w >> 13) & 1u) != 0;
+        if (r == 0) {
+            // register i holds amplitude i ^ rot.  A pair (i, i ^ XT), i
+            // without XT's lowest bit, is the amplitude pair (j, j ^ XT) with
+            // j = i ^ rot, or with the roles of its two members swapped when
+            // rot has that bit (Im changes sign); its Z parity is that of i,
+            // flipped by the parity of rot (of rot ^ XT when swapped) with
+            // the term's Z bits
+            const uint32_t swp = (rot & (uint32_t)(XT & -XT)) != 0u;
+            f ^= im ? swp : 0u;
+            if (sg) f ^= ((zp >> rot) ^ (swp ? (zp >> XT) : 0u)) & 1u;
+        }
+        round_term_fx<XT>(v, zp, f, im, sg, acc);
+    }
+}
+
+// X strings without Z bits (in any round order: the pairs are symmetric
+// under the rotation of round 0): Re conj(w) v, one sign
+template <int XT>
+__device__ __forceinline__ void round_plain(const RoundArgs<double2>& a, int r, const Fx (&v)[8], FxAcc& acc) {
+#pragma unroll 1
+    for (int c = a.xplain[r][XT]; c > 0; --c) round_pairs_fx<XT, false, false>(v, 0u, 0u, acc);
+}
+
+// 2^(x - 1023) for a biased exponent x >= 1 (infinity above 2046)
+__device__ __forceinline__ double fx_pow2(uint32_t x) { return __hiloint2double((int)(min(x, 2047u) << 20), 0); }
+
+__global__ void __launch_bounds__(kThr2, 1) k_expect_fx(const __grid_constant__ RoundArgs<double2> a) {
+    constexpr uint32_t Tn = 1u << kT2;
+    constexpr uint64_t kOnes = 0x0101010101010101ull;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* const tiles = reinterpret_cast<double2*>(smem_raw);
+    __shared__ __align__(8) uint64_t full[kNB2];
+    __shared__ double shd[32];
+    __shared__ uint64_t offA[64];
+    __shared__ uint64_t spread[256];          // byte j of spread[p] = bit j of p
+    // per tile, two slots (a warp may start the next tile while others finish this one)
+    __shared__ uint64_t s_zbits[2];           // bit m: outside parity of Z mask m
+    __shared__ uint32_t s_xbits[2];           // bit k: outside parity of term k's Z bits
+    __shared__ __align__(16) uint32_t s_wmax[2][kThr2 / 32];   // largest exponent of each warp's amplitudes
+    __shared__ uint32_t abort_flag;
+    __shared__ uint64_t s_cnt_in[kZW][kThr2];   // per thread: odd parities of the masks inside the tile
+    const uint32_t tid = threadIdx.x, lane = tid & 31u;
+    if (tid < 64) {
+        uint64_t o = 0;
+        for (int j = 0; j < a.kh; ++j)
+            if ((tid >> j) & 1u) o |= 1ull << a.hq[j];
+        offA[tid] = o;
+    }
+    if (tid < 256) {
+        uint64_t sp = 0;
+        for (int j = 0; j < 8; ++j) sp |= (uint64_t)((tid >> j) & 1u) << (8 * j);
+        spread[tid] = sp;
+    }
+    if (tid == 0) {
+        for (int b = 0; b < kNB2; ++b) oz::mbar_init_count(&full[b], 1);
+        abort_flag = 0u;
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    // parities of the thread's part of each mask (fixed for the launch)
+    const uint32_t l0 = round_base(tid, 0);
+    uint64_t tz = 0;
+    for (int m = 0; m < a.nz; ++m) tz |= (uint64_t)(__popc(l0 & a.zl[m]) & 1) << m;
+    uint32_t tx = 0;
+    for (int r = 0; r < 4; ++r) {
+        const uint32_t lt = round_base(tid, r);
+        for (int k = a.rb[r]; k < a.rb[r + 1]; ++k) tx |= (uint32_t)(__popc(lt & a.xzl[k]) & 1) << k;
+    }
+    __syncthreads();
+    // the counts of the masks inside the tile (odd parities per amplitude, one byte each)
+    for (int g = 0; g < a.nzg; ++g) {
+        uint64_t ci = 0;
+        for (uint64_t bits = a.zin[g]; bits; bits &= bits - 1) {
+            const int m = __ffsll((long long)bits) - 1;
+            ci += spread[a.zpz[m] ^ ((uint32_t)((tz >> m) & 1ull) * 0xFFu)];
+        }
+        s_cnt_in[g][tid] = ci;
+    }
+    FxAcc acc{0, 0, 0, 0};
+    double xs = 0.0, zs = 0.0;   // X/Y sum (common weight applied at the end); weighted Z sum
+    const bool later_rounds = (a.rmask & 0xE) != 0;
+    // tile copies: piece p of a tile by thread p (512 / npieces); the bytes
+    // of a buffer's next tile are announced by thread 0 before the barrier
+    // that precedes the copies, which follow a generic-proxy fence of every
+    // thread (the buffer's previous contents were read and written by them)
+    const uint32_t npieces = max(4u, 1u << a.kh), pamps = Tn / npieces;
+    const uint32_t istride = kThr2 / npieces;
+    const bool issuer = tid % istride == 0u;
+    const uint32_t lp = (tid / istride) * pamps;   // the piece's first tile-local amplitude
+    const uint32_t lowmask = (1u << a.L) - 1u;
+    const uint64_t step = gridDim.x;
+    auto issue = [&](uint64_t t, int b) {
+        const uint64_t base = insert_zero_bits(t << a.L, a.hq_sorted, a.kh);
+        oz::bulk_g2s(oz::smem_u32(tiles + (size_t)b * Tn + lp), a.x + (base + (lp & lowmask) + offA[lp >> a.L]),
+                     pamps * 16u, &full[b]);
+    };
+    if (tid == 0)
+        for (int b = 0; b < kNB2 - 1; ++b)
+            if (blockIdx.x + (uint64_t)b * step < a.ntiles) oz::mbar_expect_tx(&full[b], Tn * 16u);
+    __syncthreads();
+    if (issuer)
+        for (int b = 0; b < kNB2 - 1; ++b) {
+            const uint64_t t = blockIdx.x + (uint64_t)b * step;
+            if (t < a.ntiles) issue(t, b);
+        }
+    int it = 0;
+    bool ok = true;
+    for (uint64_t t = blockIdx.x; t < a.ntiles; t += step, ++it) {
+        const int b = it % kNB2;
+        const double2* const tile = tiles + (size_t)b * Tn;
+        const uint64_t tn = t + (uint64_t)(kNB2 - 1) * step;   // copied after this tile's first barrier
+        if (tid < 32) {
+            if (tid == 0 && tn < a.ntiles) oz::mbar_expect_tx(&full[(it + kNB2 - 1) % kNB2], Tn * 16u);
+            // outside parities of this tile
+            const uint64_t base = insert_zero_bits(t << a.L, a.hq_sorted, a.kh);
+            const uint32_t p0 = ((int)lane < a.nz) ? (uint32_t)(__popcll(base & a.zo[lane]) & 1) : 0u;
+            const uint32_t p1 = ((int)lane + 32 < a.nz) ? (uint32_t)(__popcll(base & a.zo[lane + 32]) & 1) : 0u;
+            const uint32_t px = ((int)lane < a.nxt) ? (uint32_t)(__popcll(base & a.xzo[lane]) & 1) : 0u;
+            const uint32_t b0 = __ballot_sync(0xffffffffu, p0), b1 = __ballot_sync(0xffffffffu, p1);
+            const uint32_t xb = __ballot_sync(0xffffffffu, px);
+            if (lane == 0) {
+                s_zbits[it & 1] = ((uint64_t)b1 << 32) | b0;
+                s_xbits[it & 1] = xb;
             }
         }
+        const bool arrived = oz::wait_or_abort(oz::smem_u32(&full[b]), (uint32_t)(it / kNB2) & 1u, a.spin_limit,
+                                               &abort_flag);
+        // the thread's round-0 amplitudes (rotated order): the tile's largest exponent
+        const uint32_t rot = tid & 7u;
+        double2 d[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) d[j] = tile[l0 | ((uint32_t)j ^ rot)];
+        uint32_t em = 0u;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) em = max(em, max(fx_exp(d[j].x), fx_exp(d[j].y)));
+        em = __reduce_max_sync(0xffffffffu, em);
+        if (lane == 0) s_wmax[it & 1][tid >> 5] = em;
+        if (__syncthreads_or(!arrived)) {
+            ok = false;
+            break;
+        }
+        // every thread is past the previous tile: its buffer takes tile tn
+        if (issuer && tn < a.ntiles) issue(tn, (it + kNB2 - 1) % kNB2);
+        uint32_t emax = 0u;
+#pragma unroll
+        for (int w = 0; w < kThr2 / 32; w += 4) {
+            const uint4 q = *reinterpret_cast<const uint4*>(&s_wmax[it & 1][w]);
+            emax = max(emax, max(max(q.x, q.y), max(q.z, q.w)));
+        }
+        const bool flush = emax < kFxFlush;
+        const uint32_t emx = flush ? 4095u : emax;
+        Fx v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            fx_limbs(d[j].x, emx, v[j].xh, v[j].xl);
+            fx_limbs(d[j].y, emx, v[j].yh, v[j].yl);
+        }
+        if (later_rounds) {
+            int4* const ti = reinterpret_cast<int4*>(tiles + (size_t)b * Tn);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) ti[l0 | ((uint32_t)j ^ rot)] = make_int4(v[j].xh, v[j].xl, v[j].yh, v[j].yl);
+        }
+        // v[i] holds amplitude l0 | (i ^ rot): round 0 works in that order
+        // (below: the count bytes permuted alike, and the terms' signs)
+        if (later_rounds) __syncthreads();
+        const double f2 = flush ? 0.0 : fx_pow2(emax - 53u);   // 2^(E - 1076)
+        const uint64_t zbits = tz ^ s_zbits[it & 1];
+        const uint32_t xflip = tx ^ s_xbits[it & 1];
+        if (a.nzg > 0) {
+            const double f1 = fx_pow2(emax + 5u);   // 2^(E - 1018): unit 2^58 of the folded sums
+#pragma unroll 1
+            for (int g = 0; g < a.nzg; ++g) {
+                uint64_t cg = s_cnt_in[g][tid] + (uint64_t)__popcll(zbits & a.zout[g]) * kOnes;
+                for (uint64_t bits = a.zmix[g]; bits; bits &= bits - 1) {
+                    const int m = __ffsll((long long)bits) - 1;
+                    cg += spread[a.zpz[m] ^ ((uint32_t)((zbits >> m) & 1ull) * 0xFFu)];
+                }
+                // byte i <- byte i ^ rot
+                uint32_t lo = (uint32_t)cg, hi = (uint32_t)(cg >> 32);
+                if (rot & 4u) {
+                    const uint32_t t2 = lo;
+                    lo = hi;
+                    hi = t2;
+                }
+                if (rot & 2u) {
+                    lo = __byte_perm(lo, 0u, 0x1032u);
+                    hi = __byte_perm(hi, 0u, 0x1032u);
+                }
+                if (rot & 1u) {
+                    lo = __byte_perm(lo, 0u, 0x2301u);
+                    hi = __byte_perm(hi, 0u, 0x2301u);
+                }
+                const int ngm = a.zg_end[g] - (g ? a.zg_end[g - 1] : 0);   // masks of group g
+                long long zt = 0;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    // |q|^2 at unit 2^56: h^2 terms plus the cross terms 2 h l / 2^28
+                    const long long ph = (long long)v[j].xh * v[j].xh + (long long)v[j].yh * v[j].yh;
+                    const long long pm = (long long)v[j].xh * v[j].xl + (long long)v[j].yh * v[j].yl;
+                    const uint32_t byte = ((j < 4 ? lo : hi) >> (8 * (j & 3))) & 0xFFu;
+                    zt += (long long)(ngm - 2 * (int)byte) * (ph + (pm >> 27));
+                }
+                long long z = zt >> 2;
+                z += __shfl_xor_sync(0xffffffffu, z, 1);
+                z += __shfl_xor_sync(0xffffffffu, z, 2);
+                if ((lane & 3u) == 0u) zs = __fma_rn(__dmul_rn(__dmul_rn((double)z, f1), a.zw[g]), f2, zs);
+            }
+        }
+#pragma unroll 1
+        for (int r = 0; r < 4; ++r) {
+            if (!((a.rmask >> r) & 1)) continue;
+            if (r > 0) {
+                const uint32_t lt = round_base(tid, r);
+                const int4* const ti = reinterpret_cast<const int4*>(tile);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int4 q = ti[lt | ((uint32_t)j << (3 * r))];
+                    v[j] = Fx{q.x, q.y, q.z, q.w};
+                }
+            }
+            round_plain<1>(a, r, v, acc);
+            round_plain<2>(a, r, v, acc);
+            round_plain<3>(a, r, v, acc);
+            round_plain<4>(a, r, v, acc);
+            round_plain<5>(a, r, v, acc);
+            round_plain<6>(a, r, v, acc);
+            round_plain<7>(a, r, v, acc);
+            round_xt<1>(a, r, rot, xflip, v, acc);
+            round_xt<2>(a, r, rot, xflip, v, acc);
+            round_xt<3>(a, r, rot, xflip, v, acc);
+            round_xt<4>(a, r, rot, xflip, v, acc);
+            round_xt<5>(a, r, rot, xflip, v, acc);
+            round_xt<6>(a, r, rot, xflip, v, acc);
+            round_xt<7>(a, r, rot, xflip, v, acc);
+        }
+        if (a.rmask != 0) {
+            long long x = acc.h0 + acc.h1 + (acc.m0 >> 28) + (acc.m1 >> 28);
+            acc = FxAcc{0, 0, 0, 0};
+            x += __shfl_xor_sync(0xffffffffu, x, 1);
+            x += __shfl_xor_sync(0xffffffffu, x, 2);
+            if ((lane & 3u) == 0u) xs = __fma_rn(__dmul_rn((double)x, fx_pow2(emax + 3u)), f2, xs);   // unit 2^56
+        }
+        // the buffer is refilled by bulk copies (async proxy) after the next
+        // tile's first barrier
+        asm volatile("fence.proxy.async.shared::cta;");
+    }
+    if (!ok) {
+        // copies still in flight land before the CTA exits (bounded waits)
+        if (tid == 0) {
+            atomicExch(a.status, 1u);
+            for (int k = 0; k < kNB2 - 1; ++k) {
+                const int i2 = it + k;
+                if (blockIdx.x + (uint64_t)i2 * step < a.ntiles)
+                    tc::mbar_wait(oz::smem_u32(&full[i2 % kNB2]), (uint32_t)(i2 / kNB2) & 1u, a.spin_limit);
+            }
+        }
+        return;
+    }
+    double s = 0.0, c = 0.0;
+    if (a.nzg > 0) {
+        const double r = block_reduce_d(zs, shd);
+        if (tid == 0) neumaier(s, c, r);
+    }
+    if (a.rmask != 0) {
+        const double r = block_reduce_d(xs, shd);
+        if (tid == 0) neumaier(s, c, r * a.wx);
     }
     if (tid == 0) a.partial[blockIdx.x] = make_double2(s, c);
 }
 
 // Native FP64 variants (baseline policy).
 __global__ void __launch_bounds__(kRThreads) k_probs_partial_f64(const __grid_constant__ ProbArgs<double2> a) {
-    __shared__ double shs[32], shc[32];
+    __shared__ double shs[32];
     const uint64_t bin = blockIdx.x / a.chunks, ch = blockIdx.x % a.chunks;
     uint64_t dep = 0;
     for (int j = 0; j < a.m; ++j) dep |= ((bin >> j) & 1ull) << a.q[j];
@@ -822,7 +1148,6 @@ __global__ void __launch_bounds__(kRThreads) k_probs_partial_f64(const __grid_co
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) neumaier(ts, tc, shs[w]);
         a.partial[blockIdx.x] = make_double2(ts, tc);
     }
-    (void)shc;
 }
 
 // Blocks of the probability reduction for m register qubits: about 8 blocks
@@ -1076,17 +1401,24 @@ bool plan_rounds(int n, int nterms, const uint64_t* xm, const double* cf,
 template <class S, bool NAT>
 double expect_rounds(qe_state* s, const std::vector<RoundLaunch>& rl, const uint64_t* xm, const uint64_t* zm,
                      const std::vector<double>& wv) {
-    using V = std::conditional_t<NAT, S, decltype(rview(S{}))>;
+    // complex128 (either arithmetic mode): the fixed-point kernel
+    constexpr bool kFx = sizeof(S) == 16;
+    const auto kern = [] {
+        if constexpr (kFx) return k_expect_fx;
+        else return k_expect_rounds<S>;
+    }();
     const int n = s->n;
-    const size_t smem = (size_t)kNB2 * (sizeof(V) << kT2);
-    QE_CUDA(cudaFuncSetAttribute(k_expect_rounds<S, NAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem = (size_t)kNB2 * (sizeof(S) << kT2);
+    QE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
-    QE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_expect_rounds<S, NAT>, kThr2, smem));
+    QE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThr2, smem));
     const uint64_t ntiles = 1ull << (n - kT2);
     const unsigned grid = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)num_sms() * std::max(occ, 1));
     char* scr = (char*)ensure_scratch(s, rl.size() * grid * sizeof(double2) + 64);
     double2* partial = (double2*)scr;
     double* dout = (double*)(scr + rl.size() * grid * sizeof(double2));
+    uint32_t* status = reinterpret_cast<uint32_t*>(dout + 1);   // fixed-point kernel: a copy wait ran out
+    if (kFx) QE_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), s->stream));
     auto pattern = [](uint32_t bits3) {   // bit j: parity of j & bits3
         uint32_t p = 0;
         for (uint32_t j = 0; j < 8; ++j) p |= (uint32_t)(__builtin_popcount(j & bits3) & 1) << j;
@@ -1122,6 +1454,8 @@ double expect_rounds(qe_state* s, const std::vector<RoundLaunch>& rl, const uint
                 a.zl[k] = to_local(zm[t]);
                 a.zo[k] = zm[t] & ~inside;
                 a.zpz[k] = (uint8_t)pattern(a.zl[k] & 7u);
+                uint64_t& cls = a.zl[k] == 0 ? a.zout[g] : a.zo[k] == 0 ? a.zin[g] : a.zmix[g];
+                cls |= 1ull << k;
                 ++k;
             }
             a.zg_end[g] = k;
@@ -1132,11 +1466,37 @@ double expect_rounds(qe_state* s, const std::vector<RoundLaunch>& rl, const uint
         for (const auto& tr : R.x) ++per[tr.second];
         a.rb[0] = 0;
         for (int r = 0; r < 4; ++r) a.rb[r + 1] = a.rb[r] + per[r];
+        auto xt_of = [&](const std::pair<int, int>& tr) { return (to_local(xm[tr.first]) >> (3 * tr.second)) & 7u; };
+        // X strings without Z bits: counted per round and pattern (fixed-point kernel)
+        std::vector<std::pair<int, int>> xs;
+        a.rmask = 0;
+        for (const auto& tr : R.x) {
+            const uint32_t xl = to_local(xm[tr.first]);
+            if ((xl >> (3 * tr.second) & 7u) == 0 || (xl & ~(7u << (3 * tr.second))) != 0)
+                fail(QE_ERR_STATE, "expectation term outside its round");
+            a.rmask |= 1 << tr.second;
+            if (kFx && zm[tr.first] == 0) ++a.xplain[tr.second][xt_of(tr)];
+            else xs.push_back(tr);
+        }
+        if (kFx) {
+            a.nxt = (int)xs.size();
+            for (int r = 0; r < 4; ++r) per[r] = 0;
+            for (const auto& tr : xs) ++per[tr.second];
+            for (int r = 0; r < 4; ++r) a.rb[r + 1] = a.rb[r] + per[r];
+        }
+        // within a round, by the pattern of X/Y bits in its triple
+        std::stable_sort(xs.begin(), xs.end(), [&](const std::pair<int, int>& p, const std::pair<int, int>& q) {
+            return p.second != q.second ? p.second < q.second : xt_of(p) < xt_of(q);
+        });
+        for (int r = 0; r < 4; ++r) {
+            for (int x = 0; x <= 8; ++x) a.xtb[r][x] = (uint8_t)a.rb[r];
+            for (int j = a.rb[r]; j < a.rb[r + 1]; ++j)
+                for (int x = (int)xt_of(xs[j]) + 1; x <= 8; ++x) a.xtb[r][x] = (uint8_t)(j + 1);
+        }
         for (int j = 0; j < a.nxt; ++j) {
-            const int t = R.x[j].first, r = R.x[j].second;
+            const int t = xs[j].first, r = xs[j].second;
             const uint32_t xl = to_local(xm[t]), zl = to_local(zm[t]);
             const uint32_t xt = (xl >> (3 * r)) & 7u;
-            if (xt == 0 || (xl & ~(7u << (3 * r))) != 0) fail(QE_ERR_STATE, "expectation term outside its round");
             const int ny = __builtin_popcountll(xm[t] & zm[t]) & 3;
             a.xw[j] = xt | (pattern((zl >> (3 * r)) & 7u) << 3) | ((uint32_t)(ny & 1) << 11) |
                       ((uint32_t)(ny == 1 || ny == 2) << 12) | ((uint32_t)(zm[t] != 0) << 13);
@@ -1145,8 +1505,10 @@ double expect_rounds(qe_state* s, const std::vector<RoundLaunch>& rl, const uint
         }
         a.wx = R.wx;
         a.partial = partial + i * grid;
-        Launch L(s, "expect_rounds", (double)dim(s) * amp_bytes(s));
-        k_expect_rounds<S, NAT><<<grid, kThr2, smem, s->stream>>>(a);
+        a.status = status;
+        a.spin_limit = 1ll << 20;   // polls of up to 1 us each
+        Launch L(s, kFx ? "expect_fx" : "expect_rounds", (double)dim(s) * amp_bytes(s));
+        kern<<<grid, kThr2, smem, s->stream>>>(a);
         QE_CUDA(cudaGetLastError());
     }
     {
@@ -1154,10 +1516,14 @@ double expect_rounds(qe_state* s, const std::vector<RoundLaunch>& rl, const uint
         k_sum_partials<<<1, kSumThreads, 0, s->stream>>>(partial, 1, (uint64_t)rl.size() * grid, nullptr, dout);
         QE_CUDA(cudaGetLastError());
     }
-    double out = 0.0;
-    QE_CUDA(cudaMemcpyAsync(&out, dout, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    struct {
+        double v;
+        uint32_t st;
+    } out{0.0, 0u};
+    QE_CUDA(cudaMemcpyAsync(&out, dout, kFx ? 12 : sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     QE_CUDA(cudaStreamSynchronize(s->stream));
-    return out;
+    if (out.st != 0) fail(QE_ERR_TIMEOUT, "an expectation tile copy wait ran out");
+    return out.v;
 }
 
 template <class S, bool NAT>
@@ -1251,14 +1617,15 @@ double expect_impl(qe_state* s, int nterms, const uint64_t* xm, const uint64_t* 
     }
     const int nwide = (int)((wide.size() + kXT - 1) / kXT);
     if (plans.empty() && nwide == 0) return 0.0;
-    // the register-round kernel when every term fits it, in no more
-    // launches, for the float-pair and complex64 paths (their per-pair cost
-    // is instruction issue, which it cuts by a third); the native FP64 path
-    // is bound by the FP64 pipe either way and measured no faster with it
-    if (const int sw = expect_kernel_switch(); sw != 1 && (sw == 2 || !NAT)) {
+    // the register-round kernel when every term fits it: always for
+    // complex128 (fixed point; the tile kernel's FP64 products are bound by
+    // the FP64 pipe), for complex64 when it needs no more launches (its
+    // per-pair cost is instruction issue, which it cuts by a third)
+    if (const int sw = expect_kernel_switch(); sw != 1) {
+        constexpr bool kFx = sizeof(S) == 16;
         std::vector<RoundLaunch> rl;
         if (plan_rounds(n, nterms, xm, cf, zchunks, rl) && !rl.empty() &&
-            (sw == 2 || rl.size() <= plans.size() + (size_t)nwide))
+            (sw == 2 || kFx || rl.size() <= plans.size() + (size_t)nwide))
             return expect_rounds<S, NAT>(s, rl, xm, zm, wv);
     }
     uint64_t max_grid = (uint64_t)num_sms() * 8;

@@ -491,7 +491,8 @@ def test_expectation_register_rounds(qe, dtype, arith, tol, n, nweights):
                 prof = st.profile_read()
         finally:
             os.environ.pop("QE_EXPECT_TILE", None)
-        assert ("expect_rounds" in prof) == (sw == "2"), prof
+        tag = "expect_fx" if dtype == "c128" else "expect_rounds"
+        assert (tag in prof) == (sw == "2"), prof
     bound = tol if dtype == "c128" else tol * float(np.sum(np.abs(cf)))
     for sw, e in got.items():
         assert abs(e - ref) < bound, (sw, e, ref)
@@ -499,20 +500,18 @@ def test_expectation_register_rounds(qe, dtype, arith, tol, n, nweights):
 
 @pytest.mark.parametrize("dtype,arith", [("c128", "fp64"), ("c128", "df64"), ("c64", None)])
 def test_expectation_rounds_chosen_for_tfim(qe, dtype, arith):
-    # TFIM at n = 24: the float-pair and complex64 paths take 3 launches of
-    # the register-round kernel (qubits [0, 12), then two layouts of six high
-    # qubits) instead of 4 tile ones; the FP64 path keeps the tile kernel;
-    # closed forms on |0..0> and |+..+>
+    # TFIM at n = 24: 3 launches of the register-round kernel (qubits
+    # [0, 12), then two layouts of six high qubits) instead of 4 tile ones,
+    # in fixed point for complex128 in both modes; closed forms on |0..0>
+    # and |+..+>
     n = 24
     xm, zm, cf = I.tfim_terms(n)
     with make(qe, n, dtype, arith=arith) as st:
         st.profile(True)
         e0 = st.expectation(xm, zm, cf)
         prof = st.profile_read()
-        if arith == "fp64":
-            assert "expect_rounds" not in prof and prof["expect_tile"][0] == 4, prof
-        else:
-            assert prof["expect_rounds"][0] == 3 and "expect_tile" not in prof, prof
+        tag = "expect_fx" if dtype == "c128" else "expect_rounds"
+        assert prof[tag][0] == 3 and "expect_tile" not in prof, prof
         for q in range(n):
             st.apply_gate([q], I.mat_h())
         e1 = st.expectation(xm, zm, cf)
@@ -531,8 +530,56 @@ def test_expectation_rounds_not_chosen_when_terms_do_not_fit(qe):
         st.profile(True)
         e = st.expectation(xm, zm, cf)
         prof = st.profile_read()
-    assert "expect_rounds" not in prof and "expect_tile" in prof
+    assert "expect_rounds" not in prof and "expect_fx" not in prof and "expect_tile" in prof
     assert abs(e - oracle.expectation(psi, xm, zm, cf)) < 1e-12
+
+
+def _scaled_blocks(psi, seed, lo=-60):
+    # every block of 256 amplitudes scaled by 2^k, k uniform in [lo, 0]; one
+    # block in eight zero: tiles whose components span many binades
+    rng = np.random.default_rng(seed)
+    out = psi.copy().reshape(-1, 256)
+    k = rng.integers(lo, 1, size=out.shape[0])
+    out *= (2.0 ** k.astype(np.float64))[:, None]
+    out[rng.random(out.shape[0]) < 0.125] = 0
+    return out.reshape(-1)
+
+
+@pytest.mark.parametrize("arith", ["fp64", "df64"])
+@pytest.mark.parametrize("scale", [0, 400, -400])
+def test_expectation_fixed_point_dynamic_range(qe, arith, scale):
+    # complex128 expectation in fixed point (the tile's largest component
+    # keeps its 53 bits, the others share its grid): states whose tiles span
+    # 60 binades and zero tiles, scaled by 2^scale (results by 2^(2 scale));
+    # against the oracle within 1e-13 of sum |c_t| ||psi||^2
+    n = 16
+    xm, zm, cf = _rounds_terms(n, 91, 2)
+    psi = _scaled_blocks(I.random_state(n, 92), 93) * 2.0 ** scale
+    ref = oracle.expectation(psi, xm, zm, cf)
+    with make(qe, n, "c128", psi=psi, arith=arith) as st:
+        st.profile(True)
+        e = st.expectation(xm, zm, cf)
+        prof = st.profile_read()
+    assert "expect_fx" in prof and "expect_tile" not in prof, prof
+    bound = 1e-13 * float(np.sum(np.abs(cf))) * float(np.vdot(psi, psi).real)
+    assert abs(e - ref) <= bound, (e, ref, bound)
+
+
+def test_expectation_fixed_point_underflow(qe):
+    # components below 2^-959: their products underflow FP64 and the fixed
+    # point takes such tiles as zero; tiles of ordinary size beside them are
+    # exact
+    n = 14
+    xm, zm, cf = I.tfim_terms(n)
+    psi = I.random_state(n, 94)
+    tiny = psi.copy()
+    tiny[: 1 << 12] *= 2.0 ** -1000
+    with make(qe, n, "c128", psi=tiny) as st:
+        e = st.expectation(xm, zm, cf)
+    ref = oracle.expectation(tiny, xm, zm, cf)
+    assert abs(e - ref) < 1e-13, (e, ref)
+    with make(qe, n, "c128", psi=psi * 2.0 ** -1000) as st:
+        assert st.expectation(xm, zm, cf) == 0.0
 
 
 def test_tfim_closed_forms(qe):
