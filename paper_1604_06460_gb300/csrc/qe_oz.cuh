@@ -67,12 +67,6 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t mbar, uint32_t phase, lon
     return false;
 }
 
-__device__ __forceinline__ long long mad_wide(int a, int b, long long c) {
-    long long d;
-    asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
-    return d;
-}
-
 // Bulk prefetch of `bytes` (a multiple of 16) at a 16-byte aligned global
 // address into L2.
 __device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
@@ -168,8 +162,10 @@ __device__ __forceinline__ long long combine_y(const uint32_t c[D + 1]) {
     // u4 2^24 + u5 2^16 carry the offsets 0x4B400000 (2^24 + 2^16) = 0x4B8B40 2^32,
     // taken off H: H = C_2 256 + C_3 - 0x4B8B40 (mod 2^32), and Y is exact mod 2^64
     const int H = (int)(u2 * 256u + u3 - (257u * 0x4B400000u + 0x4B8B40u));
-    long long Y = mad_wide((int)u5, 1 << 16, (long long)(c6 * 256 + c78));   // |C_6 256 + c78| < 2^31
-    Y = mad_wide((int)u4, 1 << 24, Y);
+    // C products (each one 32 x 32 + 64 multiply-add; the PTX mad.wide form
+    // measured two instructions)
+    long long Y = (long long)(int)u5 * (1 << 16) + (long long)(c6 * 256 + c78);   // |C_6 256 + c78| < 2^31
+    Y += (long long)(int)u4 * (1 << 24);
     return Y + ((long long)H << 32);
 }
 
