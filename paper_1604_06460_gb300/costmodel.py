@@ -113,7 +113,7 @@ def decision_cases(n, seed=1):
 # kernels that only the emulated QFT and addition launch (the simulated paths
 # run elementwise 1-2-qubit gates, controlled phases and permutations)
 _EMULATED = {"fft_pass", "fft_twiddle", "digitrev", "gate_tc_k5_c128", "gate_tc_k5_c128_df",
-             "add_slice", "add_cluster", "add_walk"}
+             "add_slice", "add_cluster", "add_walk", "add_bulk", "add_bulk_cluster"}
 
 
 def _path(prof):

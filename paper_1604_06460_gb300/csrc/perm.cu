@@ -123,19 +123,20 @@ __global__ void __launch_bounds__(256) k_add_walk(const __grid_constant__ WalkAr
     }
 }
 
-// One CTA per slice of 2^S contiguous amplitudes; rotation by c * 2^lo.
+// Chunks of 2^C contiguous amplitudes (C >= S: whole slices of 2^S) through
+// shared memory, one per CTA pass; each slice rotated by c * 2^lo.
 template <class S>
-__global__ void __launch_bounds__(512) k_add_slice(S* __restrict__ x, uint64_t nslices, int Sbits,
+__global__ void __launch_bounds__(512) k_add_slice(S* __restrict__ x, uint64_t nchunks, int Cbits, int Sbits,
                                                    uint64_t shift) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* buf = reinterpret_cast<S*>(smem_raw);
-    const uint32_t E = 1u << Sbits, mask = E - 1u;
+    const uint32_t E = 1u << Cbits, mask = (1u << Sbits) - 1u;
     const uint32_t sh = (uint32_t)shift;
-    for (uint64_t sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
-        S* base = x + (sl << Sbits);
+    for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        S* base = x + (ch << Cbits);
         for (uint32_t i = threadIdx.x; i < E; i += blockDim.x) buf[i] = base[i];
         __syncthreads();
-        for (uint32_t p = threadIdx.x; p < E; p += blockDim.x) base[p] = buf[(p - sh) & mask];
+        for (uint32_t p = threadIdx.x; p < E; p += blockDim.x) base[p] = buf[(p & ~mask) | ((p - sh) & mask)];
         __syncthreads();
     }
 }
@@ -172,7 +173,7 @@ __device__ uint32_t g_add_status;
 // and writes it back rotated by `shift` within the slice.
 template <class S>
 __global__ void __launch_bounds__(32) k_add_bulk(S* __restrict__ x, int Sbits, uint32_t shift, long long limit) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t abort_flag;
     cg::cluster_group cl = cg::this_cluster();
@@ -226,12 +227,14 @@ void add_impl(qe_state* s, int m, const int* qubits, uint64_t c) {
     const int cap_bits = (sizeof(S) >= 16) ? 12 : 13;      // 64 KB per CTA
     const int ccap_bits = (sizeof(S) >= 16) ? 13 : 14;     // 128 KB per CTA, 8 per cluster
     S* x = reinterpret_cast<S*>(s->d);
-    // bulk: parts of <= 128 KB per CTA (one CTA, or a cluster of eight), and
-    // rotation runs on 16-byte boundaries
+    // bulk: parts of 32 KB to 128 KB per CTA (one CTA, or a cluster of
+    // eight; smaller slices go through the chunked shared-memory kernel,
+    // measured faster below 32 KB), and rotation runs on 16-byte boundaries
     const int bulk_bits = (sizeof(S) >= 16) ? 13 : 14;
+    const int bulk_min = (sizeof(S) >= 16) ? 11 : 12;
     const uint64_t shift = c << lo;
     const int nblk = (contiguous && Sbits >= 3 && Sbits <= bulk_bits) ? 1 : 8;
-    const bool use_bulk = contiguous && lo < 5 && Sbits >= 4 && Sbits <= bulk_bits + 3 &&
+    const bool use_bulk = contiguous && lo < 5 && Sbits >= bulk_min && Sbits <= bulk_bits + 3 &&
                           ((shift * sizeof(S)) % 16 == 0) && ((((uint64_t)sizeof(S) << Sbits) / nblk) % 16 == 0);
     if (use_bulk) {
         Launch L(s, nblk == 1 ? "add_bulk" : "add_bulk_cluster", 2.0 * dim(s) * amp_bytes(s));
@@ -268,13 +271,15 @@ void add_impl(qe_state* s, int m, const int* qubits, uint64_t c) {
     Launch L(s, use_slice ? "add_slice" : use_cluster ? "add_cluster" : "add_walk",
              2.0 * dim(s) * amp_bytes(s));
     if (use_slice) {
-        const uint64_t nslices = 1ull << (n - Sbits);
-        size_t smem = sizeof(S) << Sbits;
+        // 32 KB chunks (2^11 complex128 or 2^12 complex64 amplitudes), or the slice
+        const int Cbits = std::min(n, std::max(Sbits, sizeof(S) >= 16 ? 11 : 12));
+        const uint64_t nchunks = 1ull << (n - Cbits);
+        size_t smem = sizeof(S) << Cbits;
         QE_CUDA(cudaFuncSetAttribute(k_add_slice<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int occ = 0;
         QE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_add_slice<S>, 512, smem));
-        uint64_t grid = std::min<uint64_t>(nslices, (uint64_t)num_sms() * std::max(occ, 1));
-        k_add_slice<S><<<(unsigned)grid, 512, smem, s->stream>>>(x, nslices, Sbits, c << lo);
+        uint64_t grid = std::min<uint64_t>(nchunks, (uint64_t)num_sms() * std::max(occ, 1));
+        k_add_slice<S><<<(unsigned)grid, 512, smem, s->stream>>>(x, nchunks, Cbits, Sbits, c << lo);
     } else if (use_cluster) {
         const uint64_t nslices = 1ull << (n - Sbits);
         size_t smem = sizeof(S) << (Sbits - 3);

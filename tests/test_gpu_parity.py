@@ -369,8 +369,8 @@ def test_qft_c64(qe):
 
 # --------------------------------------------------------- add constant
 @pytest.mark.parametrize("n,qubits,c", [
-    (12, list(range(0, 8)), 77),          # slice in shared memory
-    (12, list(range(2, 12)), 1000),       # slice of 2^12
+    (12, list(range(0, 8)), 77),          # chunks of 2^8-amplitude slices in shared memory
+    (12, list(range(2, 12)), 1000),       # slice of 2^12 (bulk copies)
     (18, list(range(0, 16)), 40503),      # cluster of 8 CTAs
     (17, list(range(1, 16)), 12345),      # cluster, lo = 1
     (14, list(range(6, 14)), 201),        # walk, coalesced columns
@@ -389,7 +389,7 @@ def test_add_const_bit_exact(qe, n, qubits, c):
 
 @pytest.mark.parametrize("n,qubits,c", [
     (12, list(range(0, 8)), 77),          # odd shift: 8-byte runs, shared-memory slice
-    (12, list(range(0, 8)), 78),          # even shift: bulk copies, one CTA
+    (14, list(range(0, 12)), 78),         # even shift: bulk copies, one CTA
     (18, list(range(0, 17)), 4097),       # odd shift, cluster through shared memory
     (18, list(range(0, 17)), 4098),       # even shift, bulk copies, cluster of eight
     (15, list(range(1, 13)), 5),          # lo = 1: the shift 10 is even
@@ -401,6 +401,34 @@ def test_add_const_c64_paths_bit_exact(qe, n, qubits, c):
         st.add_const(qubits, c)
         got = st.get()
     want = oracle.add_const(psi.astype(np.complex128), qubits, c).astype(np.complex64)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n,qubits,c", [
+    (14, [0], 1),                         # 2-amplitude slices, whole chunks of them
+    (14, [0, 1, 2, 3], 5),                # 16-amplitude slices
+    (14, [2, 3, 4], 5),                   # lo = 2: 32-amplitude slices, shift 20
+    (15, list(range(0, 10)), 1001),       # 2^10 slices (below the bulk threshold)
+    (11, [0, 1, 2, 3], 9),                # one chunk is the whole state (complex128)
+    (9, [0, 1], 3),                       # the state is smaller than a chunk
+])
+def test_add_const_small_slices_in_chunks(qe, dtype, n, qubits, c):
+    # registers at the bottom whose slices are far below a CTA's shared
+    # memory: many whole slices per chunk, bit-exact, on the chunked kernel
+    psi = I.random_state(n, 31 + c)
+    if dtype == "c64":
+        psi = psi.astype(np.complex64)
+    with make(qe, n, dtype, psi=psi) as st:
+        st.set_policy(qe.POLICY_EMULATE, 1)
+        st.profile(True)
+        st.add_const(qubits, c)
+        prof = st.profile_read()
+        got = st.get()
+    assert set(prof) & {"add_slice", "add_bulk"} == {"add_slice"}, prof
+    want = oracle.add_const(psi.astype(np.complex128), qubits, c)
+    if dtype == "c64":
+        want = want.astype(np.complex64)
     assert np.array_equal(got, want)
 
 
