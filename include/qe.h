@@ -160,12 +160,12 @@ int qe_apply_div(qe_state* s, int N, const int* qa, const int* qb, const int* qc
  * complex128 states, terms whose X/Y bits below qubit 12 lie in one of the
  * triples {0,1,2} .. {9,10,11} and whose X/Y bits above it number at most
  * three (every term of a nearest-neighbour Ising or Heisenberg model): in
- * fixed point: every component truncated once to a multiple of 2^(e - 54),
- * 2^e the power of two just above the largest component among the 4096
- * amplitudes read with it (tiles below 2^-959 flush to zero), products and
- * tile sums exact in integers, tile results combined in FP64 with
- * compensation.  Other terms and complex64 states: FP64 (FP64
- * mode) or double-float products, compensated sums.  *out receives the real
+ * fixed point: every component rounded once to the nearest multiple of
+ * 2^(e - 54), 2^e the power of two just above the largest component among
+ * the 4096 amplitudes read with it (tiles below 2^-959 flush to zero),
+ * products and tile sums exact in integers, tile results combined in FP64
+ * with compensation.  Other terms and complex64 states: FP64 (FP64 mode) or
+ * double-float products, compensated sums.  *out receives the real
  * value (0 for nterms = 0).  QE_ERR_ARG for nterms < 0, a mask naming a
  * qubit >= n or a non-finite coefficient; QE_ERR_TIMEOUT if a copy wait of
  * the fixed-point kernel ran out (bounded waits). */

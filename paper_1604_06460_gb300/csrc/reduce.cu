@@ -742,10 +742,11 @@ __global__ void __launch_bounds__(kThr2, 1) k_expect_rounds(const __grid_constan
 // are conflict-free as they stand.
 //
 // Fixed point.  With E the largest biased exponent of the tile's components,
-// component v becomes the integer q = v 2^(1076 - E), truncated toward zero
+// component v becomes the integer q = v 2^(1076 - E) rounded to the nearest
 // (|q| < 2^54; the largest component keeps its 53 significant bits, the
-// others lose at most half a unit of the 53-bit grid 2^(E - 1075)).  A tile
-// whose largest component is below 2^-959 is taken as zero (the products of
+// others lose at most a quarter unit of the 53-bit grid 2^(E - 1075);
+// rounding, not truncation, so the errors do not bias |v|^2 downwards).  A
+// tile whose largest component is below 2^-959 is taken as zero (the products of
 // such values underflow FP64 as well).  q is held as two limbs q = h 2^28 + l,
 // |h| < 2^26, |l| < 2^28, so the product of two components is three
 // 32 x 32 -> 64-bit integer multiply-adds: h h' at unit 2^56 and h l' + l h'
@@ -753,10 +754,10 @@ __global__ void __launch_bounds__(kThr2, 1) k_expect_rounds(const __grid_constan
 // chains each, positive and negative terms apart); the dropped l l' is below
 // 2^-52 of the largest product.  A launch has at most 24 X/Y terms, so a
 // thread's tile sums stay below 2^62.6.  At the end of a tile they are folded
-// into one int64 at unit 2^56 (truncating less than one unit), summed exactly
+// into one int64 at unit 2^56 (rounding to the nearest unit), summed exactly
 // over four lanes, and one lane in four adds the tile's value, scaled by
 // 2^(2 E - 2152), to its FP64 sum.  Z-only masks weigh |q|^2 (at unit 2^56,
-// truncated the same way) by the integer count of even minus odd parities:
+// rounded the same way) by the integer count of even minus odd parities:
 // masks inside the tile are counted once per launch, masks wholly outside it
 // once per tile by a population count, and only masks with bits on both
 // sides per amplitude.  The products thus run on the integer pipes, whose
@@ -768,13 +769,14 @@ constexpr uint32_t kFxFlush = 64;   // tiles whose largest biased exponent is be
 
 __device__ __forceinline__ uint32_t fx_exp(double v) { return ((uint32_t)__double2hiint(v) >> 20) & 0x7FFu; }
 
-// the limbs of q = trunc(v 2^(1076 - emx)), emx >= the exponent of v (and
-// emx >= 64, so zero and subnormal v give d = 63 and q = 0)
+// the limbs of q = v 2^(1076 - emx) rounded to the nearest integer (ties
+// away from zero), emx >= the exponent of v (and emx >= 64, so zero and
+// subnormal v give d = 63 and q = 0)
 __device__ __forceinline__ void fx_limbs(double v, uint32_t emx, int& h, int& l) {
     const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
-    const uint64_t m2 = ((((uint64_t)((hi & 0xFFFFFu) | 0x100000u)) << 32) | lo) << 1;   // 2 m, below 2^54
+    const uint64_t m4 = ((((uint64_t)((hi & 0xFFFFFu) | 0x100000u)) << 32) | lo) << 2;   // 4 m, below 2^55
     const uint32_t d = min(emx - ((hi >> 20) & 0x7FFu), 63u);
-    const uint64_t q2 = m2 >> d;
+    const uint64_t q2 = ((m4 >> d) + 1u) >> 1;
     const int s = (int)hi >> 31;
     h = ((int)(q2 >> 28) ^ s) - s;
     l = ((int)((uint32_t)q2 & 0xFFFFFFFu) ^ s) - s;
@@ -1047,9 +1049,9 @@ __global__ void __launch_bounds__(kThr2, 1) k_expect_fx(const __grid_constant__ 
                     const long long ph = (long long)v[j].xh * v[j].xh + (long long)v[j].yh * v[j].yh;
                     const long long pm = (long long)v[j].xh * v[j].xl + (long long)v[j].yh * v[j].yl;
                     const uint32_t byte = ((j < 4 ? lo : hi) >> (8 * (j & 3))) & 0xFFu;
-                    zt += (long long)(ngm - 2 * (int)byte) * (ph + (pm >> 27));
+                    zt += (long long)(ngm - 2 * (int)byte) * (ph + ((pm + (1ll << 26)) >> 27));
                 }
-                long long z = zt >> 2;
+                long long z = (zt + 2) >> 2;
                 z += __shfl_xor_sync(0xffffffffu, z, 1);
                 z += __shfl_xor_sync(0xffffffffu, z, 2);
                 if ((lane & 3u) == 0u) zs = __fma_rn(__dmul_rn(__dmul_rn((double)z, f1), a.zw[g]), f2, zs);
@@ -1083,7 +1085,7 @@ __global__ void __launch_bounds__(kThr2, 1) k_expect_fx(const __grid_constant__ 
             round_xt<7>(a, r, rot, xflip, v, acc);
         }
         if (a.rmask != 0) {
-            long long x = acc.h0 + acc.h1 + (acc.m0 >> 28) + (acc.m1 >> 28);
+            long long x = acc.h0 + acc.h1 + ((acc.m0 + acc.m1 + (1ll << 27)) >> 28);   // |m0 + m1| < 2^62.6
             acc = FxAcc{0, 0, 0, 0};
             x += __shfl_xor_sync(0xffffffffu, x, 1);
             x += __shfl_xor_sync(0xffffffffu, x, 2);

@@ -593,6 +593,22 @@ def test_expectation_fixed_point_dynamic_range(qe, arith, scale):
     assert abs(e - ref) <= bound, (e, ref, bound)
 
 
+def test_expectation_fixed_point_unbiased(qe):
+    # the limbs are rounded to the nearest grid point: an energy dominated by
+    # |a|^2 weights (sum_i Z_i) plus X terms stays within 1e-15 of the oracle
+    # at n = 22 (truncated limbs shrink every |a|^2 alike: ~2e-15 here)
+    n = 22
+    xm = [1 << q for q in range(n)] + [0] * n
+    zm = [0] * n + [1 << q for q in range(n)]
+    cf = [0.7] * n + [1.0] * n
+    xm, zm, cf = np.array(xm, dtype=np.uint64), np.array(zm, dtype=np.uint64), np.array(cf)
+    psi = I.random_state(n, 95)
+    ref = oracle.expectation(psi, xm, zm, cf)
+    with make(qe, n, "c128", psi=psi) as st:
+        e = st.expectation(xm, zm, cf)
+    assert abs(e - ref) < 1e-15, (e, ref, e - ref)
+
+
 def test_expectation_fixed_point_underflow(qe):
     # components below 2^-959: their products underflow FP64 and the fixed
     # point takes such tiles as zero; tiles of ordinary size beside them are
