@@ -1152,6 +1152,76 @@ __global__ void __launch_bounds__(kRThreads) k_probs_partial_f64(const __grid_co
     }
 }
 
+// Marginals of qubits that all lie below qubit 8: thread t of a 256-thread
+// block reads the amplitudes whose low 8 bits are t, so its bin is fixed and
+// the block reads a contiguous range (the bin-major kernels read each bin
+// with a stride); the block then sums its threads per bin.  Partials at
+// [bin * nblocks + block].  FP64 mode: FP64 products and sums (two
+// accumulators a thread); otherwise float-pair sums as in k_probs_partial.
+constexpr int kLowBits = 8;
+template <class S, bool NAT>
+__global__ void __launch_bounds__(1 << kLowBits) k_probs_low(const __grid_constant__ ProbArgs<S> a) {
+    constexpr uint32_t T = 1u << kLowBits;
+    __shared__ double ss[T], sc[T];
+    const uint32_t t = threadIdx.x;
+    uint32_t bin = 0;
+    for (int j = 0; j < a.m; ++j) bin |= ((t >> a.q[j]) & 1u) << j;
+    const uint64_t base = blockIdx.x * a.chunk_len + t;   // chunk_len: amplitudes a block, a multiple of 4 T
+    double s = 0.0, c = 0.0;
+    if constexpr (NAT) {
+        double s2 = 0.0, s3 = 0.0, s4 = 0.0;
+        for (uint64_t k = 0; k < a.chunk_len; k += 4 * T) {
+            const double2 v0 = reinterpret_cast<const double2*>(a.x)[base + k];
+            const double2 v1 = reinterpret_cast<const double2*>(a.x)[base + k + T];
+            const double2 v2 = reinterpret_cast<const double2*>(a.x)[base + k + 2 * T];
+            const double2 v3 = reinterpret_cast<const double2*>(a.x)[base + k + 3 * T];
+            s = __fma_rn(v0.x, v0.x, __fma_rn(v0.y, v0.y, s));
+            s2 = __fma_rn(v1.x, v1.x, __fma_rn(v1.y, v1.y, s2));
+            s3 = __fma_rn(v2.x, v2.x, __fma_rn(v2.y, v2.y, s3));
+            s4 = __fma_rn(v3.x, v3.x, __fma_rn(v3.y, v3.y, s4));
+        }
+        neumaier(s, c, s2);
+        neumaier(s, c, s3);
+        neumaier(s, c, s4);
+    } else {
+        Acc acc{0.f, 0.f};
+        for (uint64_t k = 0; k < a.chunk_len; k += 4 * T) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                float h, l;
+                abs2(rview(a.x[base + k + (uint64_t)u * T]), h, l);
+                acc_add(acc, h, l);
+            }
+        }
+        const df r = df_norm(acc.s, acc.e);
+        s = df2d(r.h, r.l);
+    }
+    ss[t] = s;
+    sc[t] = c;
+    __syncthreads();
+    if (t < (1u << a.m)) {
+        // the threads of bin t, in index order
+        double bs = 0.0, bc = 0.0;
+        for (uint32_t u = 0; u < T; ++u) {
+            uint32_t b = 0;
+            for (int j = 0; j < a.m; ++j) b |= ((u >> a.q[j]) & 1u) << j;
+            if (b != t) continue;
+            neumaier(bs, bc, ss[u]);
+            bc += sc[u];
+        }
+        a.partial[(uint64_t)t * gridDim.x + blockIdx.x] = make_double2(bs, bc);
+    }
+}
+
+// Blocks of the low-qubit marginal kernel: about 8 per SM, at least 2^14
+// amplitudes each (a power of two).
+uint64_t probs_low_blocks(const qe_state* s) {
+    if (s->n < 14) return 0;
+    uint64_t per = 1ull << 14;
+    while (((1ull << s->n) / per) > (uint64_t)num_sms() * 8) per <<= 1;
+    return (1ull << s->n) / per;
+}
+
 // Blocks of the probability reduction for m register qubits: about 8 blocks
 // per SM in total, at least 2^14 amplitudes per block.
 uint64_t probs_chunks(const qe_state* s, int m) {
@@ -1164,10 +1234,14 @@ uint64_t probs_chunks(const qe_state* s, int m) {
 template <class S>
 void probs_device(qe_state* s, int m, const int* qubits, double2* partial, double* dout);
 
+uint64_t probs_partials(const qe_state* s, int m) {
+    return (1ull << m) * std::max(probs_chunks(s, m), probs_low_blocks(s));
+}
+
 template <class S>
 void probs_impl(qe_state* s, int m, const int* qubits, double* host_out) {
     const uint64_t bins = 1ull << m;
-    const uint64_t nblocks = bins * probs_chunks(s, m);
+    const uint64_t nblocks = probs_partials(s, m);
     char* scr = (char*)ensure_scratch(s, nblocks * sizeof(double2) + bins * sizeof(double));
     double* dout = (double*)(scr + nblocks * sizeof(double2));
     probs_device<S>(s, m, qubits, (double2*)scr, dout);
@@ -1190,6 +1264,26 @@ void probs_device(qe_state* s, int m, const int* qubits, double2* partial, doubl
     std::sort(tmp, tmp + m);
     for (int j = 0; j < m; ++j) a.q_sorted[j] = (uint8_t)tmp[j];
     const uint64_t bins = 1ull << m;
+    bool low = m >= 1 && probs_low_blocks(s) > 0;
+    for (int j = 0; j < m; ++j) low &= qubits[j] < kLowBits;
+    if (low) {
+        const uint64_t nb = probs_low_blocks(s);
+        a.chunk_len = (1ull << s->n) / nb;
+        a.partial = partial;
+        {
+            Launch L(s, "probs_low", (double)dim(s) * amp_bytes(s));
+            if (std::is_same<S, double2>::value && c128_f64(s))
+                k_probs_low<S, true><<<(unsigned)nb, 1 << kLowBits, 0, s->stream>>>(a);
+            else
+                k_probs_low<S, false><<<(unsigned)nb, 1 << kLowBits, 0, s->stream>>>(a);
+            QE_CUDA(cudaGetLastError());
+        }
+        Launch L(s, "sum_partials", 0.0, false);
+        const unsigned g2 = (unsigned)std::min<uint64_t>(bins, 4096);
+        k_sum_partials<<<g2, kSumThreads, 0, s->stream>>>(a.partial, bins, nb, nullptr, dout);
+        QE_CUDA(cudaGetLastError());
+        return;
+    }
     a.per_bin = 1ull << (s->n - m);
     const uint64_t chunks = probs_chunks(s, m);
     a.chunks = chunks;
@@ -1738,7 +1832,7 @@ double reduce_norm2(qe_state* s) {
     return out;
 }
 
-uint64_t probs_partials_needed(const qe_state* s, int m) { return (1ull << m) * probs_chunks(s, m); }
+uint64_t probs_partials_needed(const qe_state* s, int m) { return probs_partials(s, m); }
 
 void reduce_probs_device(qe_state* s, int m, const int* qubits, double2* partial, double* dout) {
     if (s->dtype == QE_C128) probs_device<double2>(s, m, qubits, partial, dout);

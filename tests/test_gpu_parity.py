@@ -685,6 +685,24 @@ def test_probs(qe, qubits, arith):
     assert abs(nrm - 1) < 1e-13
 
 
+@pytest.mark.parametrize("dtype,arith", [("c128", "fp64"), ("c128", "df64"), ("c64", None)])
+@pytest.mark.parametrize("qubits", [[0], [0, 1, 2], [7, 0, 3], list(range(8)), [2, 9]])
+def test_probs_low_qubits_contiguous_reads(qe, dtype, arith, qubits):
+    # qubits all below 8 at n = 16: the kernel whose threads each own one bin
+    # (contiguous reads); a register reaching qubit 9 keeps the bin-major one
+    n = 16
+    psi = I.random_state(n, 18)
+    if dtype == "c64":
+        psi = psi.astype(np.complex64)
+    with make(qe, n, dtype, psi=psi, arith=arith) as st:
+        st.profile(True)
+        p = st.probs(qubits)
+        prof = st.profile_read()
+    assert ("probs_low" in prof) == (max(qubits) < 8), prof
+    ref = oracle.probs(psi.astype(np.complex128), qubits)
+    assert np.max(np.abs(p - ref)) < (1e-13 if dtype == "c128" else 1e-6)
+
+
 def test_probs_ghz(qe):
     n = 9
     with make(qe, n) as st:
