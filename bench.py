@@ -1081,8 +1081,8 @@ def bench_config4(qe, I, n=33):
     register (emulated permutation vs multi-controlled-NOT ripple) and the QFT
     on it (digit passes vs 136 gates).  The learned cost model is trained on
     timing sweeps at the sizes of configurations 1-3 (gate passes of the
-    30-qubit complex128 and 32-qubit complex64 states, subroutines on 24- and
-    26-qubit states) and scored, with the analytic rule, on held-out
+    30-qubit complex128 and 32-qubit complex64 states, subroutines on 24-, 26-
+    and 28-qubit states) and scored, with the analytic rule, on held-out
     emulate-or-simulate decisions at n = 30 and on this configuration's two
     subroutines: regret = time of the chosen paths / time of the best - 1."""
     import torch
@@ -1090,13 +1090,13 @@ def bench_config4(qe, I, n=33):
     t0 = time.perf_counter()
     Xg, yg = costmodel.sweep_gate_passes([30], dtypes=("c128",), seed=0)
     Xc, yc = costmodel.sweep_gate_passes([32], dtypes=("c64",), seed=0)
-    Xs, ys = costmodel.sweep_subroutines([24, 26], dtypes=("c128",), seed=0)
+    Xs, ys = costmodel.sweep_subroutines([24, 26, 28], dtypes=("c128",), seed=0)
     X = np.concatenate([Xg, Xc, Xs])
     y = np.concatenate([yg, yc, ys])
     model, loss = costmodel.train(X, y, epochs=4000, lr=3e-3, seed=0)
     out = {"cost_model": {"samples": int(len(y)), "train_loss": loss, "sweep_and_train_s": time.perf_counter() - t0,
                           "sweeps": "gate passes k=1..5 at n=30 (c128) and n=32 (c64); QFTs and additions at "
-                                    "n=24, 26 (c128)"}}
+                                    "n=24, 26, 28 (c128)"}}
     t0 = time.perf_counter()
     res, regret = costmodel.evaluate_decisions(30, costmodel.decision_cases(30), model)
     out["decisions_n30"] = {"cases": len(res), "regret": regret,
@@ -1120,7 +1120,7 @@ def bench_config4(qe, I, n=33):
                 e1.synchronize()
                 results[f"add_{reg_lo}_{label}"] = e0.elapsed_time(e1)
                 # bit-exact check on a slice: both paths from the same input
-                results[f"add_{reg_lo}_{label}_sample"] = st.get(12345 << 17, 1024).copy()
+                results[f"add_{reg_lo}_{label}_sample"] = st.get(min(12345 << 17, (1 << n) - 1024), 1024).copy()
         for label, pol in (("emulated", qe.POLICY_EMULATE), ("simulated", qe.POLICY_SIMULATE)):
             st.init_random(9)
             st.set_policy(pol, 1)
