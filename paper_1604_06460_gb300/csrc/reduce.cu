@@ -529,6 +529,7 @@ struct RoundArgs {
     int rmask;                // bit r: round r has X/Y terms
     uint32_t* status;         // raised when a copy wait ran out
     long long spin_limit;
+    int stall_test;           // failure-path test: block 0's first tile is announced but never copied
 };
 
 template <int EB>
@@ -952,7 +953,7 @@ __global__ void __launch_bounds__(kThr2, 1) k_expect_fx(const __grid_constant__ 
     if (issuer)
         for (int b = 0; b < kNB2 - 1; ++b) {
             const uint64_t t = blockIdx.x + (uint64_t)b * step;
-            if (t < a.ntiles) issue(t, b);
+            if (t < a.ntiles && !(a.stall_test && blockIdx.x == 0 && b == 0)) issue(t, b);
         }
     int it = 0;
     bool ok = true;
@@ -1603,6 +1604,13 @@ double expect_rounds(qe_state* s, const std::vector<RoundLaunch>& rl, const uint
         a.partial = partial + i * grid;
         a.status = status;
         a.spin_limit = 1ll << 20;   // polls of up to 1 us each
+        // Failure-path test (QE_TEST_STALL_EXPECT=1, fixed-point kernel): block
+        // 0 announces its first tile's bytes but copies none, so its wait runs
+        // out after a short limit, the block drains its other copies and
+        // leaves, and the host reports QE_ERR_TIMEOUT with the context intact.
+        const char* stall = std::getenv("QE_TEST_STALL_EXPECT");
+        a.stall_test = (kFx && stall != nullptr && stall[0] == '1') ? 1 : 0;
+        if (a.stall_test) a.spin_limit = 1ll << 12;
         Launch L(s, kFx ? "expect_fx" : "expect_rounds", (double)dim(s) * amp_bytes(s));
         kern<<<grid, kThr2, smem, s->stream>>>(a);
         QE_CUDA(cudaGetLastError());

@@ -609,6 +609,23 @@ def test_expectation_fixed_point_unbiased(qe):
     assert abs(e - ref) < 1e-15, (e, ref, e - ref)
 
 
+def test_expectation_fixed_point_copy_wait_times_out(qe, monkeypatch):
+    # block 0's first tile is announced but never copied: its bounded wait
+    # runs out, the launch reports QE_ERR_TIMEOUT, and the state still works
+    from paper_1604_06460_gb300.qe import QEError
+    n = 16
+    xm, zm, cf = I.tfim_terms(n)
+    psi = I.random_state(n, 96)
+    ref = oracle.expectation(psi, xm, zm, cf)
+    with make(qe, n, "c128", psi=psi) as st:
+        monkeypatch.setenv("QE_TEST_STALL_EXPECT", "1")
+        with pytest.raises(QEError) as err:
+            st.expectation(xm, zm, cf)
+        assert err.value.status == -4 and "QE_ERR_TIMEOUT" in str(err.value)
+        monkeypatch.delenv("QE_TEST_STALL_EXPECT")
+        assert abs(st.expectation(xm, zm, cf) - ref) < 1e-12
+
+
 def test_expectation_fixed_point_underflow(qe):
     # components below 2^-959: their products underflow FP64 and the fixed
     # point takes such tiles as zero; tiles of ordinary size beside them are
