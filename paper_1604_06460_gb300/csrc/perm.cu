@@ -24,6 +24,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "qe_arith.cuh"
 #include "qe_internal.h"
@@ -172,7 +173,8 @@ __device__ uint32_t g_add_status;
 // CTA `rank` holds the contiguous part [rank E, rank E + E), E = 2^S / nblk,
 // and writes it back rotated by `shift` within the slice.
 template <class S>
-__global__ void __launch_bounds__(32) k_add_bulk(S* __restrict__ x, int Sbits, uint32_t shift, long long limit) {
+__global__ void __launch_bounds__(32) k_add_bulk(S* __restrict__ x, int Sbits, uint32_t shift, long long limit,
+                                                 int stall_test) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t abort_flag;
@@ -192,8 +194,10 @@ __global__ void __launch_bounds__(32) k_add_bulk(S* __restrict__ x, int Sbits, u
         const uint32_t bytes = E * (uint32_t)sizeof(S);
         oz::mbar_expect_tx(&bar, bytes);
         const char* src = reinterpret_cast<const char*>(base + (uint64_t)rank * E);
-        for (uint32_t off = 0; off < bytes; off += kPiece)
-            oz::bulk_g2s(sm + off, src + off, min(kPiece, bytes - off), &bar);
+        // (failure-path test: block 0 announces its part but copies none)
+        if (!(stall_test && blockIdx.x == 0))
+            for (uint32_t off = 0; off < bytes; off += kPiece)
+                oz::bulk_g2s(sm + off, src + off, min(kPiece, bytes - off), &bar);
     }
     const bool ok = oz::wait_or_abort(oz::smem_u32(&bar), 0u, limit, &abort_flag);
     // every CTA of the cluster holds its part before any part is written back
@@ -257,8 +261,13 @@ void add_impl(qe_state* s, int m, const int* qubits, uint64_t c) {
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        const long long limit = 1ll << 20;   // polls of up to 1 us each
-        QE_CUDA(cudaLaunchKernelEx(&cfg, k_add_bulk<S>, x, Sbits, (uint32_t)shift, limit));
+        // Failure-path test (QE_TEST_STALL_ADD=1): block 0's copy wait runs out
+        // after a short limit (its cluster waits for it at the barrier), the
+        // host reports QE_ERR_TIMEOUT; the state's contents are then undefined.
+        const char* stall = std::getenv("QE_TEST_STALL_ADD");
+        const int stall_test = (stall != nullptr && stall[0] == '1') ? 1 : 0;
+        const long long limit = stall_test ? (1ll << 12) : (1ll << 20);   // polls of up to 1 us each
+        QE_CUDA(cudaLaunchKernelEx(&cfg, k_add_bulk<S>, x, Sbits, (uint32_t)shift, limit, stall_test));
         QE_CUDA(cudaGetLastError());
         uint32_t st = 0;
         QE_CUDA(cudaMemcpyAsync(&st, st_addr, sizeof(uint32_t), cudaMemcpyDeviceToHost, s->stream));

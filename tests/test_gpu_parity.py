@@ -432,6 +432,31 @@ def test_add_const_small_slices_in_chunks(qe, dtype, n, qubits, c):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("n,qubits", [(14, list(range(0, 12))), (18, list(range(0, 16)))])
+def test_add_const_bulk_copy_wait_times_out(qe, monkeypatch, n, qubits):
+    # one CTA (2^12-amplitude slices) and clusters of eight (2^16): block 0
+    # announces its part but copies none; QE_ERR_TIMEOUT, then a fresh state
+    # on the same context adds bit-exactly
+    from paper_1604_06460_gb300.qe import QEError
+    psi = I.random_state(n, 97)
+    c = 1234
+    with make(qe, n, psi=psi) as st:
+        st.set_policy(qe.POLICY_EMULATE, 1)
+        monkeypatch.setenv("QE_TEST_STALL_ADD", "1")
+        with pytest.raises(QEError) as err:
+            st.add_const(qubits, c)
+            st.flush()
+        assert err.value.status == -4 and "QE_ERR_TIMEOUT" in str(err.value)
+        monkeypatch.delenv("QE_TEST_STALL_ADD")
+        st.set(psi)
+        st.profile(True)
+        st.add_const(qubits, c)
+        prof = st.profile_read()
+        got = st.get()
+    assert "add_bulk" in prof or "add_bulk_cluster" in prof, prof
+    assert np.array_equal(got, oracle.add_const(psi, qubits, c))
+
+
 def test_add_const_simulated_bit_exact(qe):
     n, qubits, c = 12, list(range(2, 10)), 173
     psi = I.random_state(n, 5)
